@@ -1,0 +1,284 @@
+"""Plain FP64 CPU oracle of the thermal pseudopotential D2Q9 LB step.
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, obviously correct
+reference written from the equations of Li & Luo (arXiv:1405.2232):
+Eq. (1) with the forcing term of Ref. [21], Eqs. (2)/(4) for the force,
+the pseudopotential of Sec. II A, Eq. (7) and Eqs. (24)-(25) for the
+temperature distribution.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+it.  It shares no code with the CUDA library and never imports it.
+
+All arrays are float64 numpy arrays.  Populations use the layout
+``f[i, y, x]`` (nine planes, row-major), holding the PRE-collision values at
+the current time.
+
+Parity status of each function (what pins it, see tests/test_oracle_pins.py):
+  feq, forcing_term, correction_term  -- exact moment identities
+  p_eos / critical_point             -- vdW closed form, published CS critical
+                                        point, hard-sphere virial coefficients
+  force (Eq. 2/4)                    -- closed form on a sinusoid, Taylor limit
+  step                               -- conservation, uniform state,
+                                        translation, G and c_v invariance,
+                                        Chapman-Enskog drift rate (Eq. 23)
+                                        and steady states (Eq. 23 / A11),
+                                        brute-force per-site recomputation
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lb_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EOS_CS, EOS_VDW, EOS_IDEAL = 0, 1, 2
+THERMAL_EQ7, THERMAL_EQ24 = 0, 1
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_PSI_DOMAIN = 0, 1, 4, 5
+
+
+class OracleParams(ctypes.Structure):
+    """Mirror of the oracle's own ``or_params`` struct."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("tau_f", ctypes.c_double),
+        ("tau_g", ctypes.c_double),
+        ("G", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("eos", ctypes.c_int32),
+        ("a", ctypes.c_double),
+        ("b", ctypes.c_double),
+        ("R", ctypes.c_double),
+        ("cv", ctypes.c_double),
+        ("thermal", ctypes.c_int32),
+        ("psi_uses_local_T", ctypes.c_int32),
+        ("T_psi", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off, OpenMP on)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def build_variant(source_text: str, tag: str) -> str:
+    """Compile a modified copy of the oracle source (used by the mutation tests,
+    which plant a mistake in the oracle and check that a pin catches it)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_BUILD, f"variant_{tag}.c")
+    lib = os.path.join(_BUILD, f"libvariant_{tag}.so")
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                    "-fPIC", "-shared", src, "-o", lib, "-lm"], check=True)
+    return lib
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+class using:
+    """Context manager: route every oracle call to another build of the source."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self._saved = _lib
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    P = ctypes.POINTER(OracleParams)
+    lib.or_p_eos.argtypes = [P, ctypes.c_double, ctypes.c_double]
+    lib.or_p_eos.restype = ctypes.c_double
+    lib.or_psi_sq.argtypes = [P, ctypes.c_double, ctypes.c_double]
+    lib.or_psi_sq.restype = ctypes.c_double
+    lib.or_feq.argtypes = [ctypes.c_double] * 3 + [dp]
+    lib.or_forcing_term.argtypes = [ctypes.c_double] * 5 + [dp]
+    lib.or_correction_term.argtypes = [ctypes.c_double] * 5 + [dp]
+    lib.or_step.argtypes = [P, dp, dp, dp, dp, ctypes.c_int]
+    lib.or_step.restype = ctypes.c_int
+    lib.or_moments.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
+    lib.or_moments.restype = ctypes.c_int
+    lib.or_init_equilibrium.argtypes = [P, dp, dp, dp, dp]
+    lib.or_init_equilibrium.restype = ctypes.c_int
+    lib.or_step_sites.argtypes = [P, dp, dp, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_int64), dp, dp]
+    lib.or_step_sites.restype = ctypes.c_int
+    lib.or_totals.argtypes = [P, dp, dp, dp]
+    lib.or_totals.restype = ctypes.c_int
+    lib.or_residual.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int64]
+    lib.or_residual.restype = ctypes.c_double
+    lib.or_critical_point.argtypes = [P, dp, dp]
+    lib.or_critical_point.restype = ctypes.c_int
+    lib.or_num_threads_available.restype = ctypes.c_int
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def params(nx, ny, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0, eos=EOS_CS, a=1.0, b=4.0,
+           R=1.0, cv=1.0, thermal=THERMAL_EQ24, psi_uses_local_T=1, T_psi=0.0):
+    """Build the oracle's parameter struct (names follow the paper)."""
+    return OracleParams(int(nx), int(ny), float(tau_f), float(tau_g), float(G),
+                        float(beta), int(eos), float(a), float(b), float(R),
+                        float(cv), int(thermal), int(psi_uses_local_T), float(T_psi))
+
+
+def p_eos(P, rho, T):
+    return _load().or_p_eos(ctypes.byref(P), float(rho), float(T))
+
+
+def psi_sq(P, rho, T):
+    return _load().or_psi_sq(ctypes.byref(P), float(rho), float(T))
+
+
+def feq(rho, ux, uy):
+    out = np.zeros(9)
+    _load().or_feq(float(rho), float(ux), float(uy), _ptr(out))
+    return out
+
+
+def forcing_term(tau_f, ux, uy, Fx, Fy):
+    out = np.zeros(9)
+    _load().or_forcing_term(float(tau_f), float(ux), float(uy), float(Fx), float(Fy),
+                            _ptr(out))
+    return out
+
+
+def correction_term(tau_g, cv, T, Fx, Fy):
+    out = np.zeros(9)
+    _load().or_correction_term(float(tau_g), float(cv), float(T), float(Fx), float(Fy),
+                               _ptr(out))
+    return out
+
+
+def init_equilibrium(P, rho0, T0):
+    """f = f^eq(rho0, 0), g = c_v T0 f^eq(rho0, 0): arrays [9, ny, nx]."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    assert rho0.shape == (P.ny, P.nx) and T0.shape == (P.ny, P.nx)
+    f = np.zeros((9, P.ny, P.nx))
+    g = np.zeros((9, P.ny, P.nx))
+    rc = _load().or_init_equilibrium(ctypes.byref(P), _ptr(rho0), _ptr(T0), _ptr(f), _ptr(g))
+    if rc:
+        raise ValueError(f"or_init_equilibrium failed: {rc}")
+    return f, g
+
+
+def step(P, f, g, n=1, threads=1, check=True):
+    """Advance the pre-collision state (f, g) by n steps; returns (f, g, status)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    fn = np.empty_like(f)
+    gn = np.empty_like(g)
+    lib = _load()
+    worst = OK
+    for _ in range(int(n)):
+        rc = lib.or_step(ctypes.byref(P), _ptr(f), _ptr(g), _ptr(fn), _ptr(gn), int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        g, gn = gn, g
+    if check and worst:
+        raise FloatingPointError(f"oracle step reported status {worst}")
+    return f, g, worst
+
+
+def moments(P, f, g):
+    """(rho, ux, uy, T, Fx, Fy) of the pre-collision state, each [ny, nx]."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    outs = [np.zeros((P.ny, P.nx)) for _ in range(6)]
+    rc = _load().or_moments(ctypes.byref(P), _ptr(f), _ptr(g), *[_ptr(o) for o in outs])
+    if rc == ERR_ARG:
+        raise ValueError("or_moments: invalid parameters")
+    return tuple(outs)
+
+
+def step_sites(P, f, g, sites):
+    """State at t+1 at the given flat site indices; returns (f, g) as [n, 9]."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    of = np.zeros((len(sites), 9))
+    og = np.zeros((len(sites), 9))
+    rc = _load().or_step_sites(ctypes.byref(P), _ptr(f), _ptr(g), len(sites),
+                               sites.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               _ptr(of), _ptr(og))
+    if rc == ERR_ARG:
+        raise ValueError("or_step_sites: invalid arguments")
+    return of, og
+
+
+def totals(P, f, g):
+    """[mass, energy, px, py] with compensated summation."""
+    out = np.zeros(4)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _load().or_totals(ctypes.byref(P), _ptr(f), _ptr(g), _ptr(out))
+    return out
+
+
+def residual(rho0, T0, rho1, T1, K):
+    """max over {rho, T} of ||phi1 - phi0||_2 / (K ||phi1||_2)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (rho0, T0, rho1, T1)]
+    return _load().or_residual(arrs[0].size, *[_ptr(a) for a in arrs], int(K))
+
+
+def critical_point(P):
+    """(T_c, rho_c) of the EOS in P, from dp/drho = d2p/drho2 = 0."""
+    Tc = ctypes.c_double()
+    rc_ = ctypes.c_double()
+    rc = _load().or_critical_point(ctypes.byref(P), ctypes.byref(Tc), ctypes.byref(rc_))
+    if rc:
+        raise ValueError("no critical point for this EOS")
+    return Tc.value, rc_.value
+
+
+def threads_available():
+    return _load().or_num_threads_available()

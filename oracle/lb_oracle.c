@@ -1,0 +1,533 @@
+/*
+ * lb_oracle.c -- plain FP64 CPU oracle of the D2Q9 double-distribution
+ * thermal pseudopotential lattice Boltzmann step of Li & Luo,
+ * "Effect of the forcing term in the pseudopotential lattice Boltzmann
+ * modeling of thermal flows" (arXiv:1405.2232).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, obviously correct reference
+ * the GPU path is checked against.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark load it.  It shares no code, header,
+ * table or constant with the CUDA library, and it includes nothing of it.
+ *
+ * State convention: the arrays hold the PRE-collision populations f_i(x,t)
+ * and g_i(x,t) in structure-of-arrays order, index  i*ny*nx + y*nx + x,
+ * on a periodic nx-by-ny lattice.  One step applies, at every site, the
+ * collision of Eq. (1) (density) and Eq. (7) or Eq. (24) (temperature) and
+ * then streams the post-collision value to x + e_i, giving f_i(x,t+1).
+ *
+ * The order of operations below follows the paper's formulas as printed;
+ * nothing is blocked, fused or reordered beyond them.
+ *
+ * Readings of passages where the paper is silent (each is listed in the
+ * design notes of the repository):
+ *   - lattice numbering and weights (Sec. II A names D2Q9 but lists neither):
+ *     e0=(0,0); e1..e4=(1,0),(0,1),(-1,0),(0,-1);
+ *     e5..e8=(1,1),(-1,1),(-1,-1),(1,-1); omega = 4/9, 1/9, 1/36.
+ *   - the forcing term F_i of Eq. (1) is "the scheme of Ref. [21]", read as
+ *     Guo, Zheng & Shi (2002):
+ *       F_i = (1 - 1/(2 tau_f)) omega_i [ (e_i - u)/cs^2 + (e_i.u) e_i/cs^4 ] . F
+ *     with the velocity u = (sum_i e_i f_i + F/2) / rho used in f^eq, g^eq and F_i.
+ *   - temperature T = sum_i g_i / (rho c_v), which follows from g^eq = c_v T f^eq.
+ *   - psi of Sec. II A is sqrt(2 (p_EOS - rho cs^2) / (G c^2)) with c = 1;
+ *     the mixed force Eq. (4) with beta = 0 only needs psi^2, which may be
+ *     negative (the single-phase test of Sec. III).
+ *   - the pair sums of Eq. (2)/(4) are written as antisymmetric differences
+ *     (east minus west, ...), which is the same sum grouped in pairs.
+ *   - Carnahan-Starling EOS (not in the paper; used by the workloads):
+ *     p = rho R T (1 + eta + eta^2 - eta^3) / (1 - eta)^3 - a rho^2, eta = b rho / 4.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* status codes of the oracle (its own numbering) */
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_NONFINITE 4
+#define OR_ERR_PSI_DOMAIN 5
+
+#define OR_EOS_CS 0
+#define OR_EOS_VDW 1
+#define OR_EOS_IDEAL 2
+
+#define OR_THERMAL_EQ7 0
+#define OR_THERMAL_EQ24 1
+
+typedef struct or_params {
+    int32_t nx, ny;
+    double tau_f, tau_g; /* relaxation times of Eq. (1) and Eq. (7)         */
+    double G, beta;      /* interaction strength and mixing of Eq. (2)/(4)  */
+    int32_t eos;         /* OR_EOS_*                                        */
+    double a, b, R;      /* EOS constants                                   */
+    double cv;           /* specific heat at constant volume, g^eq = cv T f^eq */
+    int32_t thermal;     /* OR_THERMAL_EQ7 or OR_THERMAL_EQ24               */
+    int32_t psi_uses_local_T; /* 1: psi(rho, T(x,t)); 0: psi(rho, T_psi)    */
+    double T_psi;
+} or_params;
+
+/* D2Q9 lattice (reading of Sec. II A, see header) */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double OMEGA[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                                1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0; /* c_s^2 = c^2/3 with c = 1 (Sec. II A) */
+
+static int wrap(int v, int n) { return ((v % n) + n) % n; }
+
+/* ---------------------------------------------------------------------- */
+/* Equations of state.  vdW and ideal: Sec. III.  Carnahan-Starling: see
+ * header (not in the paper).                                               */
+double or_p_eos(const or_params* P, double rho, double T)
+{
+    if (P->eos == OR_EOS_IDEAL) {
+        return rho * P->R * T;
+    }
+    if (P->eos == OR_EOS_VDW) {
+        return rho * P->R * T / (1.0 - P->b * rho) - P->a * rho * rho;
+    }
+    /* Carnahan-Starling */
+    double eta = P->b * rho / 4.0;
+    double num = 1.0 + eta + eta * eta - eta * eta * eta;
+    double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);
+    return rho * P->R * T * num / den - P->a * rho * rho;
+}
+
+/* psi^2 = 2 (p_EOS - rho cs^2) / (G c^2), c = 1  (Sec. II A, after Eq. 3) */
+double or_psi_sq(const or_params* P, double rho, double T)
+{
+    double T_eos = P->psi_uses_local_T ? T : P->T_psi;
+    return 2.0 * (or_p_eos(P, rho, T_eos) - rho * CS2) / P->G;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Equilibrium of Sec. II A (after Eq. 1):
+ * f_i^eq = rho w_i [1 + (e_i.u)/cs^2 + 0.5 (e_i.u)^2/cs^4 - 0.5 |u|^2/cs^2] */
+void or_feq(double rho, double ux, double uy, double feq[9])
+{
+    double usq = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        feq[i] = rho * OMEGA[i] *
+                 (1.0 + eu / CS2 + 0.5 * eu * eu / (CS2 * CS2) - 0.5 * usq / CS2);
+    }
+}
+
+/* Forcing term F_i of Eq. (1), scheme of Ref. [21] (Guo et al.):
+ * F_i = (1 - 1/(2 tau_f)) w_i [ (e_i - u).F / cs^2 + (e_i.u)(e_i.F) / cs^4 ] */
+void or_forcing_term(double tau_f, double ux, double uy, double Fx, double Fy,
+                     double Fi[9])
+{
+    double pre = 1.0 - 1.0 / (2.0 * tau_f);
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        double eF = EX[i] * Fx + EY[i] * Fy;
+        double emuF = (EX[i] - ux) * Fx + (EY[i] - uy) * Fy;
+        Fi[i] = pre * OMEGA[i] * (emuF / CS2 + eu * eF / (CS2 * CS2));
+    }
+}
+
+/* Correction term of Eq. (25):
+ * C_i = (1 - 1/(2 tau_g)) w_i c_v T (e_i.F) / cs^2 */
+void or_correction_term(double tau_g, double cv, double T, double Fx, double Fy,
+                        double Ci[9])
+{
+    double pre = 1.0 - 1.0 / (2.0 * tau_g);
+    for (int i = 0; i < 9; ++i) {
+        double eF = EX[i] * Fx + EY[i] * Fy;
+        Ci[i] = pre * OMEGA[i] * cv * T * eF / CS2;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Density and temperature at every site from the pre-collision
+ * populations:  rho = sum_i f_i,  rho c_v T = sum_i g_i.  Then psi^2 and,
+ * when beta != 0, psi (which needs psi^2 >= 0).                            */
+static int macroscopic_fields(const or_params* P, const double* f, const double* g,
+                              double* rho, double* T, double* psi, double* psi2,
+                              int nthreads)
+{
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    int err = OR_OK;
+    (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static) reduction(max : err)
+    for (int64_t s = 0; s < N; ++s) {
+        double r = 0.0, e = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            r += f[i * N + s];
+            e += g[i * N + s];
+        }
+        rho[s] = r;
+        T[s] = e / (r * P->cv);
+        psi2[s] = or_psi_sq(P, r, T[s]);
+        psi[s] = 0.0;
+        if (!isfinite(r) || !isfinite(T[s])) {
+            if (err < OR_ERR_NONFINITE) err = OR_ERR_NONFINITE;
+        }
+        if (P->beta != 0.0) {
+            if (psi2[s] < 0.0) {
+                if (err < OR_ERR_PSI_DOMAIN) err = OR_ERR_PSI_DOMAIN;
+                psi[s] = NAN;
+            } else {
+                psi[s] = sqrt(psi2[s]);
+            }
+        }
+    }
+    return err;
+}
+
+/* Pseudopotential force at (x, y), Eq. (4) (Eq. (2) when beta = 1):
+ * F = -G [ beta psi(x) sum_i w ψ(x+e_i) e_i + (1-beta)/2 sum_i w ψ^2(x+e_i) e_i ]
+ * with w(1) = 1/3 on the axes and w(2) = 1/12 on the diagonals.  Each sum is
+ * grouped into the pairs of opposite directions.                           */
+static void force_at(const or_params* P, const double* psi, const double* psi2,
+                     int x, int y, double* Fx, double* Fy)
+{
+    const int nx = P->nx, ny = P->ny;
+    const double w1 = 1.0 / 3.0, w2 = 1.0 / 12.0;
+    int xe = wrap(x + 1, nx), xw = wrap(x - 1, nx);
+    int yn = wrap(y + 1, ny), ys = wrap(y - 1, ny);
+    int64_t E = (int64_t)y * nx + xe, W = (int64_t)y * nx + xw;
+    int64_t N_ = (int64_t)yn * nx + x, S = (int64_t)ys * nx + x;
+    int64_t NE = (int64_t)yn * nx + xe, NW = (int64_t)yn * nx + xw;
+    int64_t SW = (int64_t)ys * nx + xw, SE = (int64_t)ys * nx + xe;
+    int64_t C = (int64_t)y * nx + x;
+
+    double fx = 0.0, fy = 0.0;
+    if (P->beta != 0.0) {
+        double s1x = w1 * (psi[E] - psi[W]) + w2 * ((psi[NE] - psi[SW]) + (psi[SE] - psi[NW]));
+        double s1y = w1 * (psi[N_] - psi[S]) + w2 * ((psi[NE] - psi[SW]) + (psi[NW] - psi[SE]));
+        fx += P->beta * psi[C] * s1x;
+        fy += P->beta * psi[C] * s1y;
+    }
+    if (P->beta != 1.0) {
+        double s2x = w1 * (psi2[E] - psi2[W]) + w2 * ((psi2[NE] - psi2[SW]) + (psi2[SE] - psi2[NW]));
+        double s2y = w1 * (psi2[N_] - psi2[S]) + w2 * ((psi2[NE] - psi2[SW]) + (psi2[NW] - psi2[SE]));
+        fx += 0.5 * (1.0 - P->beta) * s2x;
+        fy += 0.5 * (1.0 - P->beta) * s2y;
+    }
+    *Fx = -P->G * fx;
+    *Fy = -P->G * fy;
+}
+
+/* Collision of one site: Eq. (1) with F_i for f, and Eq. (7) (or Eq. (24)
+ * with C_i of Eq. (25)) for g.  Writes post-collision values fs, gs and the
+ * macroscopic velocity.                                                     */
+static void collide_site(const or_params* P, const double fl[9], const double gl[9],
+                         double rho, double T, double Fx, double Fy,
+                         double fs[9], double gs[9], double* ux_out, double* uy_out)
+{
+    double mx = 0.0, my = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        mx += EX[i] * fl[i];
+        my += EY[i] * fl[i];
+    }
+    double ux = (mx + 0.5 * Fx) / rho;
+    double uy = (my + 0.5 * Fy) / rho;
+
+    double feq[9], Fi[9], Ci[9];
+    or_feq(rho, ux, uy, feq);
+    or_forcing_term(P->tau_f, ux, uy, Fx, Fy, Fi);
+    or_correction_term(P->tau_g, P->cv, T, Fx, Fy, Ci);
+
+    for (int i = 0; i < 9; ++i) {
+        fs[i] = fl[i] - (1.0 / P->tau_f) * (fl[i] - feq[i]) + Fi[i];
+        double geq = P->cv * T * feq[i];
+        gs[i] = gl[i] - (1.0 / P->tau_g) * (gl[i] - geq);
+        if (P->thermal == OR_THERMAL_EQ24) gs[i] += Ci[i];
+    }
+    if (ux_out) *ux_out = ux;
+    if (uy_out) *uy_out = uy;
+}
+
+static int check_params(const or_params* P)
+{
+    if (!P || P->nx < 3 || P->ny < 3) return OR_ERR_ARG;
+    if (!(P->tau_f > 0.5) || !(P->tau_g > 0.5) || P->G == 0.0 || !(P->cv > 0.0))
+        return OR_ERR_ARG;
+    if (P->eos < 0 || P->eos > 2 || P->thermal < 0 || P->thermal > 1) return OR_ERR_ARG;
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* One full time step, t -> t+1.  f, g: pre-collision state at t; fn, gn
+ * receive the pre-collision state at t+1 (streaming: f_i(x+e_i) <- f*_i(x)).
+ * Returns OR_OK, or the worst error seen (the step is still completed).    */
+int or_step(const or_params* P, const double* f, const double* g, double* fn,
+            double* gn, int nthreads)
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* T = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    if (!rho || !T || !psi || !psi2) {
+        free(rho); free(T); free(psi); free(psi2);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    err = macroscopic_fields(P, f, g, rho, T, psi, psi2, nthreads);
+
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = g[i * N + s];
+            }
+            force_at(P, psi, psi2, x, y, &Fx, &Fy);
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, NULL, NULL);
+            for (int i = 0; i < 9; ++i) {
+                int64_t d = (int64_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+                fn[i * N + d] = fs[i];
+                gn[i * N + d] = gs[i];
+            }
+        }
+    }
+    free(rho); free(T); free(psi); free(psi2);
+    return err;
+}
+
+/* Macroscopic fields of the pre-collision state at t: rho, u (including the
+ * half-force term of the Guo scheme), T, and the force F.  Any output may be
+ * NULL.                                                                     */
+int or_moments(const or_params* P, const double* f, const double* g, double* rho_out,
+               double* ux_out, double* uy_out, double* T_out, double* Fx_out,
+               double* Fy_out)
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* T = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    if (!rho || !T || !psi || !psi2) {
+        free(rho); free(T); free(psi); free(psi2);
+        return OR_ERR_ARG;
+    }
+    err = macroscopic_fields(P, f, g, rho, T, psi, psi2, 1);
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int64_t s = (int64_t)y * nx + x;
+            double Fx, Fy, mx = 0.0, my = 0.0;
+            force_at(P, psi, psi2, x, y, &Fx, &Fy);
+            for (int i = 0; i < 9; ++i) {
+                mx += EX[i] * f[i * N + s];
+                my += EY[i] * f[i * N + s];
+            }
+            if (rho_out) rho_out[s] = rho[s];
+            if (T_out) T_out[s] = T[s];
+            if (ux_out) ux_out[s] = (mx + 0.5 * Fx) / rho[s];
+            if (uy_out) uy_out[s] = (my + 0.5 * Fy) / rho[s];
+            if (Fx_out) Fx_out[s] = Fx;
+            if (Fy_out) Fy_out[s] = Fy;
+        }
+    }
+    free(rho); free(T); free(psi); free(psi2);
+    return err;
+}
+
+/* Initial state: f = f^eq(rho0, u = 0), g = c_v T0 f^eq(rho0, 0). */
+int or_init_equilibrium(const or_params* P, const double* rho0, const double* T0,
+                        double* f, double* g)
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int64_t N = (int64_t)P->nx * P->ny;
+    for (int64_t s = 0; s < N; ++s) {
+        double feq[9];
+        or_feq(rho0[s], 0.0, 0.0, feq);
+        for (int i = 0; i < 9; ++i) {
+            f[i * N + s] = feq[i];
+            g[i * N + s] = P->cv * T0[s] * feq[i];
+        }
+    }
+    return OR_OK;
+}
+
+/* The state at t+1 at a list of sites only, from the full state at t.
+ * Site x at t+1 receives f*_i(x - e_i), so the collisions of the nine source
+ * sites are computed, each with the force from the psi values around it.
+ * out_f, out_g: [n_sites][9].  Used to check a large lattice at sampled
+ * sites without a full step.                                               */
+int or_step_sites(const or_params* P, const double* f, const double* g, int64_t n_sites,
+                  const int64_t* sites, double* out_f, double* out_g)
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    for (int64_t k = 0; k < n_sites; ++k) {
+        int64_t d = sites[k];
+        if (d < 0 || d >= N) return OR_ERR_ARG;
+        int xd = (int)(d % nx), yd = (int)(d / nx);
+        for (int i = 0; i < 9; ++i) {
+            int xs = wrap(xd - EX[i], nx), ys = wrap(yd - EY[i], ny);
+            /* psi, psi^2, rho, T on the 3x3 block around the source site,
+             * stored in a local 3x3 lattice so force_at can be reused.    */
+            or_params L = *P;
+            L.nx = 3;
+            L.ny = 3;
+            double rho9[9], T9[9], psi9[9], psi29[9];
+            for (int by = 0; by < 3; ++by) {
+                for (int bx = 0; bx < 3; ++bx) {
+                    int64_t s = (int64_t)wrap(ys + by - 1, ny) * nx + wrap(xs + bx - 1, nx);
+                    double r = 0.0, e = 0.0;
+                    for (int j = 0; j < 9; ++j) {
+                        r += f[j * N + s];
+                        e += g[j * N + s];
+                    }
+                    int b = by * 3 + bx;
+                    rho9[b] = r;
+                    T9[b] = e / (r * P->cv);
+                    psi29[b] = or_psi_sq(P, r, T9[b]);
+                    psi9[b] = 0.0;
+                    if (P->beta != 0.0) {
+                        if (psi29[b] < 0.0) {
+                            err = OR_ERR_PSI_DOMAIN;
+                            psi9[b] = NAN;
+                        } else {
+                            psi9[b] = sqrt(psi29[b]);
+                        }
+                    }
+                }
+            }
+            double Fx, Fy, fl[9], gl[9], fs[9], gs[9];
+            force_at(&L, psi9, psi29, 1, 1, &Fx, &Fy);
+            int64_t s = (int64_t)ys * nx + xs;
+            for (int j = 0; j < 9; ++j) {
+                fl[j] = f[j * N + s];
+                gl[j] = g[j * N + s];
+            }
+            collide_site(P, fl, gl, rho9[4], T9[4], Fx, Fy, fs, gs, NULL, NULL);
+            out_f[k * 9 + i] = fs[i];
+            out_g[k * 9 + i] = gs[i];
+        }
+    }
+    return err;
+}
+
+/* Neumaier-compensated sum: the accurate reference for the totals. */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum* a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+/* Conserved totals of the pre-collision state: mass sum rho, energy
+ * sum rho c_v T (= sum of all g_i), momentum sum rho u (with the half-force
+ * term), out[0..3] = mass, energy, px, py.                                  */
+int or_totals(const or_params* P, const double* f, const double* g, double out[4])
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int64_t N = (int64_t)P->nx * P->ny;
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* rho = (double*)malloc(sizeof(double) * N);
+    if (!ux || !uy || !rho) {
+        free(ux); free(uy); free(rho);
+        return OR_ERR_ARG;
+    }
+    err = or_moments(P, f, g, rho, ux, uy, NULL, NULL, NULL);
+    nsum m = {0, 0}, e = {0, 0}, px = {0, 0}, py = {0, 0};
+    for (int64_t s = 0; s < N; ++s) {
+        for (int i = 0; i < 9; ++i) {
+            nsum_add(&m, f[i * N + s]);
+            nsum_add(&e, g[i * N + s]);
+        }
+        nsum_add(&px, rho[s] * ux[s]);
+        nsum_add(&py, rho[s] * uy[s]);
+    }
+    out[0] = m.s + m.c;
+    out[1] = e.s + e.c;
+    out[2] = px.s + px.c;
+    out[3] = py.s + py.c;
+    free(ux); free(uy); free(rho);
+    return err;
+}
+
+/* Steady-state residual between two density/temperature snapshots taken
+ * K steps apart:  r = max over phi in {rho, T} of ||phi1 - phi0||_2 / (K ||phi1||_2). */
+double or_residual(int64_t n, const double* rho0, const double* T0, const double* rho1,
+                   const double* T1, int64_t K)
+{
+    nsum dr = {0, 0}, nr = {0, 0}, dT = {0, 0}, nT = {0, 0};
+    for (int64_t s = 0; s < n; ++s) {
+        nsum_add(&dr, (rho1[s] - rho0[s]) * (rho1[s] - rho0[s]));
+        nsum_add(&nr, rho1[s] * rho1[s]);
+        nsum_add(&dT, (T1[s] - T0[s]) * (T1[s] - T0[s]));
+        nsum_add(&nT, T1[s] * T1[s]);
+    }
+    double r_rho = sqrt(dr.s + dr.c) / ((double)K * sqrt(nr.s + nr.c));
+    double r_T = sqrt(dT.s + dT.c) / ((double)K * sqrt(nT.s + nT.c));
+    return r_rho > r_T ? r_rho : r_T;
+}
+
+/* Critical point of the EOS: the (rho_c, T_c) where dp/drho = d2p/drho2 = 0.
+ * Found by bisection on T of  min_rho dp/drho(rho, T) = 0, the inner minimum
+ * by golden-section search.  Derivatives are central differences.           */
+static double dp_drho(const or_params* P, double rho, double T)
+{
+    double h = 1e-6 * (rho > 1e-3 ? rho : 1e-3);
+    return (or_p_eos(P, rho + h, T) - or_p_eos(P, rho - h, T)) / (2.0 * h);
+}
+
+static double min_dp_drho(const or_params* P, double T, double lo, double hi, double* arg)
+{
+    const double gr = 0.5 * (sqrt(5.0) - 1.0);
+    double a = lo, b = hi;
+    double c = b - gr * (b - a), d = a + gr * (b - a);
+    for (int it = 0; it < 200; ++it) {
+        if (dp_drho(P, c, T) < dp_drho(P, d, T)) b = d;
+        else a = c;
+        c = b - gr * (b - a);
+        d = a + gr * (b - a);
+    }
+    *arg = 0.5 * (a + b);
+    return dp_drho(P, *arg, T);
+}
+
+int or_critical_point(const or_params* P, double* Tc, double* rhoc)
+{
+    if (!P || P->eos == OR_EOS_IDEAL) return OR_ERR_ARG;
+    /* rho range inside the EOS's domain: vdW needs b rho < 1, CS eta < 1 */
+    double hi = (P->eos == OR_EOS_VDW) ? 0.99 / P->b : 3.96 / P->b;
+    double lo = 1e-4 * hi;
+    double Tlo = 1e-6, Thi = 10.0 * P->a / (P->b * P->R);
+    double arg = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        double Tm = 0.5 * (Tlo + Thi);
+        if (min_dp_drho(P, Tm, lo, hi, &arg) < 0.0) Tlo = Tm;
+        else Thi = Tm;
+    }
+    *Tc = 0.5 * (Tlo + Thi);
+    min_dp_drho(P, *Tc, lo, hi, &arg);
+    *rhoc = arg;
+    return OR_OK;
+}
+
+int or_num_threads_available(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs for the thermal pseudopotential LB workloads.
+
+This module holds only the input recipes (initial density and temperature
+fields, parameter draws).  It contains none of the method's arithmetic, so
+both the CUDA path and the CPU oracle can be fed from it.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), a
+counter-based generator: the value for site index s under seed k is
+SplitMix64(SplitMix64(k) XOR s), mapped to a 53-bit double in [0, 1).
+The same seed therefore gives the same field on every machine.
+
+Workload recipes (all periodic D2Q9 lattices, Carnahan-Starling EOS with
+a = 1, b = 4, R = 1, G = -1):
+
+* ``slab_64``      64 x 64, T = 0.85 T_c, liquid slab x in [nx/2-16, nx/2+16)
+                   at rho_l = 0.35 in vapour rho_g = 0.03, noise +-1e-3 (seed 1)
+* ``droplet_512``  512 x 512, droplet radius 64 at rho_l in rho_g, T linear
+                   in x from 0.80 T_c to 0.90 T_c
+* ``spinodal_4096`` 4096 x 4096, T = 0.75 T_c, rho = 0.12 + noise +-0.01 (seed 3)
+* ``batched_sweep`` 256 domains, side L ~ U{64..512}, T/T_c ~ U[0.6, 0.95],
+                   G ~ U[-1.2, -0.8], tau_f ~ U[0.6, 1.2], droplet or slab
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+#: Critical temperature and density of the Carnahan-Starling EOS with
+#: a = 1, b = 4, R = 1 (the point where dp/drho = d2p/drho2 = 0; the tests
+#: check these constants against an independent high-precision solve).
+CS_TC = 0.09432870313855984
+CS_RHOC = 0.130443
+
+RHO_LIQUID = 0.35
+RHO_GAS = 0.03
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """One SplitMix64 output for each 64-bit state in x (vectorised)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, index: np.ndarray) -> np.ndarray:
+    """Counter-based U[0, 1) doubles: SplitMix64(SplitMix64(seed) ^ index) >> 11."""
+    key = splitmix64(np.array([seed], dtype=np.uint64))[0]
+    z = splitmix64(np.asarray(index, dtype=np.uint64) ^ key)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def site_noise(seed: int, nx: int, ny: int, amplitude: float) -> np.ndarray:
+    """Noise U[-amplitude, amplitude] on an ny x nx lattice, site s = y*nx + x."""
+    idx = np.arange(nx * ny, dtype=np.uint64)
+    return (amplitude * (2.0 * uniform01(seed, idx) - 1.0)).reshape(ny, nx)
+
+
+def slab_fields(nx, ny, T_over_Tc=0.85, width=32, rho_l=RHO_LIQUID, rho_g=RHO_GAS,
+                noise=1e-3, seed=1, Tc=CS_TC):
+    """Flat liquid slab x in [nx/2 - width/2, nx/2 + width/2) plus noise; uniform T."""
+    x = np.arange(nx)
+    liquid = (x >= nx // 2 - width // 2) & (x < nx // 2 + width // 2)
+    rho = np.where(liquid[None, :], rho_l, rho_g) * np.ones((ny, 1))
+    if noise:
+        rho = rho + site_noise(seed, nx, ny, noise)
+    T = np.full((ny, nx), T_over_Tc * Tc)
+    return np.ascontiguousarray(rho), T
+
+
+def droplet_fields(nx, ny, radius, T_lo=0.80, T_hi=0.90, rho_l=RHO_LIQUID,
+                   rho_g=RHO_GAS, Tc=CS_TC, noise=0.0, seed=2):
+    """Sharp droplet centred at (nx/2, ny/2); T linear in x from T_lo to T_hi (x T_c).
+
+    The linear profile is taken literally on the periodic lattice, so T jumps
+    at the x seam.
+    """
+    y, x = np.mgrid[0:ny, 0:nx]
+    r2 = (x - nx / 2 + 0.5) ** 2 + (y - ny / 2 + 0.5) ** 2
+    rho = np.where(r2 < radius * radius, rho_l, rho_g).astype(np.float64)
+    if noise:
+        rho = rho + site_noise(seed, nx, ny, noise)
+    T = Tc * (T_lo + (T_hi - T_lo) * x / (nx - 1))
+    return np.ascontiguousarray(rho), np.ascontiguousarray(T.astype(np.float64))
+
+
+def spinodal_fields(nx, ny, T_over_Tc=0.75, rho_mean=0.12, noise=0.01, seed=3, Tc=CS_TC):
+    """Uniform density rho_mean plus seeded noise, uniform T: spinodal decomposition."""
+    rho = rho_mean + site_noise(seed, nx, ny, noise)
+    T = np.full((ny, nx), T_over_Tc * Tc)
+    return np.ascontiguousarray(rho), T
+
+
+def uniform_fields(nx, ny, rho, T):
+    return np.full((ny, nx), float(rho)), np.full((ny, nx), float(T))
+
+
+def sinusoid_fields(nx, ny, rho0, T0, eps, mode=1, axis=0):
+    """rho = rho0 (1 + eps sin(k x)) with k = 2 pi mode / nx (axis 0 = x); uniform T."""
+    if axis == 0:
+        k = 2.0 * np.pi * mode / nx
+        prof = np.sin(k * np.arange(nx))[None, :] * np.ones((ny, 1))
+    else:
+        k = 2.0 * np.pi * mode / ny
+        prof = np.sin(k * np.arange(ny))[:, None] * np.ones((1, nx))
+    rho = rho0 * (1.0 + eps * prof)
+    return np.ascontiguousarray(rho), np.full((ny, nx), float(T0))
+
+
+@dataclasses.dataclass
+class Domain:
+    """One domain of the batched parameter sweep."""
+
+    L: int
+    T_over_Tc: float
+    G: float
+    tau_f: float
+    tau_g: float
+    kind: str           # "droplet" or "slab"
+    size: float         # droplet radius or slab width
+    rho: np.ndarray
+    T: np.ndarray
+
+
+def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_TC,
+                  fixed_L=None):
+    """Parameter sweep of independent periodic square domains.
+
+    Per domain d (stream index 16 d + k of the counter-based generator):
+    side L ~ U{L_min..L_max}, T/T_c ~ U[0.6, 0.95], G ~ U[-1.2, -0.8],
+    tau_f ~ U[0.6, 1.2], tau_g fixed; droplet (radius U[L/8, L/4]) or slab
+    (width U[L/4, L/2]) from a fair coin.
+    """
+    out = []
+    for d in range(n_domains):
+        u = uniform01(seed, np.arange(16 * d, 16 * d + 8, dtype=np.uint64))
+        L = int(fixed_L) if fixed_L else int(L_min + min(int(u[0] * (L_max - L_min + 1)),
+                                                         L_max - L_min))
+        T_over = 0.6 + 0.35 * u[1]
+        G = -1.2 + 0.4 * u[2]
+        tau_f = 0.6 + 0.6 * u[3]
+        if u[4] < 0.5:
+            kind = "droplet"
+            size = L / 8 + (L / 4 - L / 8) * u[5]
+            rho, _ = droplet_fields(L, L, size)
+        else:
+            kind = "slab"
+            size = L / 4 + (L / 2 - L / 4) * u[5]
+            w = max(2, 2 * int(size / 2))
+            rho, _ = slab_fields(L, L, width=w, noise=0.0)
+        T = np.full((L, L), T_over * Tc)
+        out.append(Domain(L, float(T_over), float(G), float(tau_f), float(tau_g), kind,
+                          float(size), rho, T))
+    return out
