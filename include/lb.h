@@ -1,0 +1,183 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) fused thermal pseudopotential D2Q9
+ * lattice Boltzmann step.
+ *
+ * Method: Li & Luo, "Effect of the forcing term in the pseudopotential
+ * lattice Boltzmann modeling of thermal flows", arXiv:1405.2232.
+ *   density LBE ............ Eq. (1), BGK with forcing term F_i (Ref. [21]:
+ *                            Guo et al., u = (sum e_i f_i + F/2)/rho)
+ *   pseudopotential force .. Eq. (2), mixed form Eq. (4) (parameter beta)
+ *   pseudopotential ........ psi = sqrt(2 (p_EOS - rho cs^2)/(G c^2)), Sec. II A
+ *   temperature LBE ........ Eq. (7), g^eq = c_v T f^eq   (forcing-term effect)
+ *                            Eq. (24) with C_i of Eq. (25) (forcing-free)
+ *   equations of state ..... van der Waals and ideal gas (Sec. III),
+ *                            Carnahan-Starling
+ *
+ * Lattice: periodic nx-by-ny D2Q9, site index y*nx + x, c = 1, delta_t = 1,
+ * cs^2 = 1/3.  Velocity numbering: e0 = (0,0); e1..e4 = (1,0),(0,1),(-1,0),
+ * (0,-1); e5..e8 = (1,1),(-1,1),(-1,-1),(1,-1); weights 4/9, 1/9, 1/36.
+ *
+ * Host arrays passed to or returned from the library are float64, row-major
+ * (y, x); population arrays are [9][ny][nx] and hold the PRE-collision
+ * populations f_i(x, t) and g_i(x, t) at the context's current time t.
+ *
+ * Ownership: the library owns every device buffer of a context (allocated
+ * in lb_init, released in lb_free).  Caller arrays are only read or written
+ * during the call, except where a function says it is asynchronous.
+ *
+ * Errors: every function returns an lb_status.  On an argument error nothing
+ * changes.  lb_last_error() returns a thread-local message about the last
+ * failure.  Numerical trouble on the device (non-finite rho or T, psi^2 < 0
+ * when beta != 0) sets a sticky per-context error word that the next
+ * synchronising call (lb_synchronize, lb_moments, lb_totals, ...) reports and
+ * clears.  Kernels never trap or spin: a bad state is reported, not fatal.
+ */
+#ifndef LBGB_LB_H
+#define LBGB_LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lb_status {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,         /* invalid argument; nothing was changed            */
+    LB_ERR_CUDA = 2,        /* a CUDA runtime call failed                       */
+    LB_ERR_OOM = 3,         /* device allocation failed                         */
+    LB_ERR_NONFINITE = 4,   /* rho or T became NaN/Inf during a step            */
+    LB_ERR_PSI_DOMAIN = 5,  /* 2 (p_EOS - rho cs^2)/G < 0 with beta != 0        */
+    LB_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                    */
+    LB_ERR_UNSUPPORTED = 7  /* option not built or not available                */
+} lb_status;
+
+/* Equation of state p_EOS(rho, T) used by the pseudopotential (Sec. II A). */
+enum {
+    LB_EOS_CS = 0,    /* rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2, eta = b rho/4 */
+    LB_EOS_VDW = 1,   /* rho R T/(1 - b rho) - a rho^2                      (Sec. III) */
+    LB_EOS_IDEAL = 2  /* rho R T                                            (Sec. III) */
+};
+
+/* Temperature treatment (Sec. II B). */
+enum {
+    LB_THERMAL_EQ7 = 0,  /* Eq. (7): g relaxes to c_v T f^eq; recovers Eq. (23)       */
+    LB_THERMAL_EQ24 = 1  /* Eq. (24): Eq. (7) + C_i of Eq. (25); recovers Eq. (6)/(A11) */
+};
+
+/* Storage of the populations in device memory; collision arithmetic is FP64
+ * for LB_PREC_FP64 and FP32 otherwise.  The 16-bit modes store the deviation
+ * h = f - w_i rho0 (and g - w_i rho0 c_v T0), rounded to nearest even. */
+enum {
+    LB_PREC_FP64 = 0,
+    LB_PREC_FP32 = 1,
+    LB_PREC_FP16_DEV = 2,
+    LB_PREC_BF16_DEV = 3
+};
+
+/* Numbers of lb_totals outputs. */
+enum { LB_TOTALS_N = 5 };
+
+typedef struct lb_params {
+    int32_t nx, ny;        /* lattice size, both >= 3                                  */
+    int32_t eos;           /* LB_EOS_*                                                 */
+    int32_t thermal;       /* LB_THERMAL_*                                             */
+    int32_t precision;     /* LB_PREC_*                                                */
+    int32_t psi_uses_local_T; /* 1: psi(rho, T(x,t)); 0: psi(rho, T_psi) (T passive)   */
+    int32_t tile_x, tile_y;   /* CTA tile of the step kernel; 0 = library default      */
+    double tau_f;          /* relaxation time of Eq. (1), > 1/2                        */
+    double tau_g;          /* relaxation time of Eq. (7)/(24), > 1/2                   */
+    double G;              /* interaction strength of Eq. (2)/(4), != 0                */
+    double beta;           /* mixing parameter of Eq. (4); 1 gives Eq. (2)             */
+    double a, b, R;        /* EOS constants                                            */
+    double cv;             /* specific heat at constant volume (g^eq = c_v T f^eq), > 0 */
+    double T_psi;          /* temperature used by psi when psi_uses_local_T == 0       */
+    double rho0, T0;       /* deviation base of the 16-bit storage modes               */
+} lb_params;
+
+typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
+
+/* Fill *p with the defaults: 64x64, CS EOS a=1 b=4 R=1, G=-1, beta=1,
+ * tau_f=1, tau_g=0.8, c_v=1, Eq. (24), FP32, psi from the local T,
+ * rho0 = 0.12, T0 = 0.075. */
+void lb_params_default(lb_params* p);
+
+/* Create a context whose initial state is f = f^eq(rho0, u = 0) and
+ * g = c_v T0 f^eq(rho0, 0) (Eq. (1) and Eq. (7) equilibria at rest).
+ * rho0, T0: host float64 arrays [ny][nx], copied during the call.
+ * stream: a cudaStream_t for all work of the context, or NULL for a stream
+ * the library creates.  *out receives the context.  Returns LB_ERR_ARG for
+ * invalid parameters (tau <= 1/2, n < 3, G == 0, c_v <= 0, unknown enum). */
+lb_status lb_init(const lb_params* p, const double* rho0, const double* T0,
+                  void* stream, lb_ctx** out);
+
+/* As lb_init, but rho0 and T0 are DEVICE float64 arrays [ny][nx]; they are
+ * read by kernels on the stream before the call returns. */
+lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,
+                         void* stream, lb_ctx** out);
+
+/* Advance n >= 0 time steps (Eq. (1) for f; Eq. (7) or (24) for g), each one
+ * fused kernel launch that reads and writes every population once.
+ * Asynchronous on the context's stream. */
+lb_status lb_step(lb_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream and report (then clear) the device error word. */
+lb_status lb_synchronize(lb_ctx* ctx);
+
+/* Macroscopic fields of the state at time t, as the step computes them:
+ * rho = sum f_i, u = (sum e_i f_i + F/2)/rho, T = sum g_i/(rho c_v).
+ * Host float64 arrays [ny][nx]; any pointer may be NULL.  Synchronises. */
+lb_status lb_moments(lb_ctx* ctx, double* rho, double* ux, double* uy, double* T);
+
+/* Same, into DEVICE float64 arrays [ny][nx]; asynchronous on the stream. */
+lb_status lb_moments_device(lb_ctx* ctx, double* d_rho, double* d_ux, double* d_uy,
+                            double* d_T);
+
+/* Copy the pre-collision populations at time t to host arrays [9][ny][nx]
+ * (any may be NULL).  Synchronises. */
+lb_status lb_get_populations(lb_ctx* ctx, double* f, double* g);
+
+/* Replace the state by host populations [9][ny][nx] (pre-collision, time t);
+ * values are rounded to the storage precision. */
+lb_status lb_set_populations(lb_ctx* ctx, const double* f, const double* g);
+
+/* Global FP64 totals of the state at time t, reduced on the device in a
+ * fixed order (deterministic):
+ *   out[0] mass   sum_x sum_i f_i
+ *   out[1] energy sum_x sum_i g_i  (= sum rho c_v T)
+ *   out[2] px     sum_x rho u_x    (with the F/2 term)
+ *   out[3] py     sum_x rho u_y
+ *   out[4] residual: max over phi in {rho, T} of
+ *          ||phi_t - phi_s||_2 / ((t - s) ||phi_t||_2), where s is the time of
+ *          the previous lb_totals call (0 on the first call or when t == s).
+ * Each call stores (rho, T) at t as the new reference.  Synchronises. */
+lb_status lb_totals(lb_ctx* ctx, double out[LB_TOTALS_N]);
+
+/* Raw state for checkpoint/resume: *bytes receives the size of the opaque
+ * state blob; lb_save_state copies it to host memory, lb_load_state restores
+ * it bit for bit (same params required).  Both synchronise. */
+lb_status lb_state_size(const lb_ctx* ctx, size_t* bytes);
+lb_status lb_save_state(lb_ctx* ctx, void* host_blob);
+lb_status lb_load_state(lb_ctx* ctx, const void* host_blob);
+
+/* Number of steps taken since lb_init (or the loaded state's time). */
+int64_t lb_time(const lb_ctx* ctx);
+
+/* Parameters the context runs with (tile sizes resolved). */
+lb_status lb_get_params(const lb_ctx* ctx, lb_params* out);
+
+/* Release the context and its device memory.  NULL is accepted. */
+lb_status lb_free(lb_ctx* ctx);
+
+/* Thread-local description of the last error ("" if none). */
+const char* lb_last_error(void);
+
+/* Library version string. */
+const char* lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBGB_LB_H */

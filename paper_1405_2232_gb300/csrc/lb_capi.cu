@@ -1,0 +1,537 @@
+// lb_capi.cu -- host implementation of the C ABI declared in include/lb.h.
+//
+// A context owns two 18-plane population buffers (ping-pong), an error word,
+// the FP64 reference fields of the steady-state residual and the partial-sum
+// buffer of the deterministic totals reduction.  Every kernel runs on the
+// context's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lb.h"
+#include "lb_launch.h"
+
+using namespace lbgb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lb_status fail(lb_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+lb_status fail(lb_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lb_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t elem_size(int prec) {
+    switch (prec) {
+        case LB_PREC_FP64: return 8;
+        case LB_PREC_FP32: return 4;
+        default: return 2;
+    }
+}
+
+lb_status validate(const lb_params* p) {
+    if (!p) return fail(LB_ERR_ARG, "params is NULL");
+    if (p->nx < 3 || p->ny < 3) return fail(LB_ERR_ARG, "nx, ny must be >= 3 (got %d, %d)", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 31))
+        return fail(LB_ERR_ARG, "lattice larger than 2^31 sites");
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5))
+        return fail(LB_ERR_ARG, "tau_f and tau_g must be > 1/2 (got %g, %g)", p->tau_f, p->tau_g);
+    if (!(p->G != 0.0) || !std::isfinite(p->G)) return fail(LB_ERR_ARG, "G must be finite and != 0");
+    if (!std::isfinite(p->beta)) return fail(LB_ERR_ARG, "beta must be finite");
+    if (!(p->cv > 0.0)) return fail(LB_ERR_ARG, "c_v must be > 0");
+    if (p->eos < LB_EOS_CS || p->eos > LB_EOS_IDEAL) return fail(LB_ERR_ARG, "unknown eos %d", p->eos);
+    if (p->thermal < LB_THERMAL_EQ7 || p->thermal > LB_THERMAL_EQ24)
+        return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
+    if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
+        return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
+    const int tx = p->tile_x ? p->tile_x : 32, ty = p->tile_y ? p->tile_y : 8;
+    if (!step_tile_supported(tx, ty)) return fail(LB_ERR_ARG, "unsupported tile %dx%d", tx, ty);
+    return LB_OK;
+}
+
+}  // namespace
+
+namespace lbgb {
+bool step_tile_supported(int bx, int by) {
+    return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 4);
+}
+
+// Final reduction of the per-CTA partials in a fixed order (one CTA).
+__global__ void k_reduce_partials(const double* __restrict__ part, int nparts,
+                                  double* __restrict__ out8) {
+    __shared__ double s[256][8];
+    const int t = threadIdx.x;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = t; p < nparts; p += 256)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += part[(long long)p * 8 + k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[t][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[t][k] += s[t + w][k];
+        __syncthreads();
+    }
+    if (t < 8) out8[t] = s[0][t];
+}
+
+}  // namespace lbgb
+
+struct lb_ctx {
+    lb_params p;
+    KParams kp;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;             // every call makes this device current first
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    size_t buf_bytes = 0;
+    int* d_err = nullptr;
+    double* d_ref = nullptr;    // [2][n]: reference rho, T of the residual
+    double* d_snap = nullptr;   // [2][n]: current rho, T written by lb_totals
+    double* d_part = nullptr;   // [moments_grid_blocks][8]
+    double* d_out8 = nullptr;   // [8]
+    bool have_ref = false;
+    int64_t ref_time = 0;
+    int64_t t = 0;
+};
+
+namespace {
+
+int bmode_of(double beta) { return beta == 0.0 ? BETA_ZERO : (beta == 1.0 ? BETA_ONE : BETA_MIXED); }
+
+KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* err) {
+    KParams k;
+    std::memset(&k, 0, sizeof(k));
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.pitch = pitch;
+    k.plane = plane;
+    k.omega_f = 1.0 / p.tau_f;
+    k.omega_g = 1.0 / p.tau_g;
+    k.guo_pre = 1.0 - 1.0 / (2.0 * p.tau_f);
+    k.corr_pre = 1.0 - 1.0 / (2.0 * p.tau_g);
+    k.G = p.G;
+    k.two_over_G = 2.0 / p.G;
+    k.beta = p.beta;
+    k.half_1mbeta = 0.5 * (1.0 - p.beta);
+    k.eos = p.eos;
+    k.psi_local_T = p.psi_uses_local_T;
+    k.a = p.a;
+    k.b = p.b;
+    k.R = p.R;
+    k.cv = p.cv;
+    k.inv_cv = 1.0 / p.cv;
+    k.T_psi = p.T_psi;
+    const bool dev = p.precision == LB_PREC_FP16_DEV || p.precision == LB_PREC_BF16_DEV;
+    for (int i = 0; i < 9; ++i) {
+        k.base_f[i] = dev ? (float)(wd(i) * p.rho0) : 0.0f;
+        k.base_g[i] = dev ? (float)(wd(i) * p.rho0 * p.cv * p.T0) : 0.0f;
+    }
+    k.err = err;
+    return k;
+}
+
+cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
+    StepLaunch L;
+    L.src = src;
+    L.dst = dst;
+    L.kp = c->kp;
+    L.eq24 = c->p.thermal == LB_THERMAL_EQ24;
+    L.bmode = bmode_of(c->p.beta);
+    L.bx = c->p.tile_x;
+    L.by = c->p.tile_y;
+    L.stream = c->stream;
+    switch (c->p.precision) {
+        case LB_PREC_FP64: return launch_step_fp64(L);
+        case LB_PREC_FP32: return launch_step_fp32(L);
+        case LB_PREC_FP16_DEV: return launch_step_fp16(L);
+        default: return launch_step_bf16(L);
+    }
+}
+
+cudaError_t dispatch_moments(const lb_ctx* c, MomentsLaunch& L) {
+    L.src = c->buf[c->cur];
+    L.kp = c->kp;
+    L.bmode = bmode_of(c->p.beta);
+    L.stream = c->stream;
+    switch (c->p.precision) {
+        case LB_PREC_FP64: return launch_moments_fp64(L);
+        case LB_PREC_FP32: return launch_moments_fp32(L);
+        case LB_PREC_FP16_DEV: return launch_moments_fp16(L);
+        default: return launch_moments_bf16(L);
+    }
+}
+
+cudaError_t dispatch_init(const lb_ctx* c, const double* rho0, const double* T0) {
+    void* d = c->buf[c->cur];
+    switch (c->p.precision) {
+        case LB_PREC_FP64: return launch_init_fp64(d, c->kp, rho0, T0, c->stream);
+        case LB_PREC_FP32: return launch_init_fp32(d, c->kp, rho0, T0, c->stream);
+        case LB_PREC_FP16_DEV: return launch_init_fp16(d, c->kp, rho0, T0, c->stream);
+        default: return launch_init_bf16(d, c->kp, rho0, T0, c->stream);
+    }
+}
+
+cudaError_t dispatch_gather(const lb_ctx* c, double* out) {
+    const void* s = c->buf[c->cur];
+    switch (c->p.precision) {
+        case LB_PREC_FP64: return launch_gather_fp64(s, c->kp, out, c->stream);
+        case LB_PREC_FP32: return launch_gather_fp32(s, c->kp, out, c->stream);
+        case LB_PREC_FP16_DEV: return launch_gather_fp16(s, c->kp, out, c->stream);
+        default: return launch_gather_bf16(s, c->kp, out, c->stream);
+    }
+}
+
+cudaError_t dispatch_scatter(const lb_ctx* c, const double* in) {
+    void* d = c->buf[c->cur];
+    switch (c->p.precision) {
+        case LB_PREC_FP64: return launch_scatter_fp64(d, c->kp, in, c->stream);
+        case LB_PREC_FP32: return launch_scatter_fp32(d, c->kp, in, c->stream);
+        case LB_PREC_FP16_DEV: return launch_scatter_fp16(d, c->kp, in, c->stream);
+        default: return launch_scatter_bf16(d, c->kp, in, c->stream);
+    }
+}
+
+void release(lb_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+    cudaFree(c->d_err);
+    cudaFree(c->d_ref);
+    cudaFree(c->d_snap);
+    cudaFree(c->d_part);
+    cudaFree(c->d_out8);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// Read and clear the device error word (synchronises the stream).
+lb_status check_device_error(lb_ctx* c) {
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error word");
+    CU(cudaStreamSynchronize(c->stream), "synchronize");
+    if (h) {
+        CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear error word");
+        CU(cudaStreamSynchronize(c->stream), "synchronize");
+        if (h & (1 << LB_ERR_PSI_DOMAIN))
+            return fail(LB_ERR_PSI_DOMAIN,
+                        "psi^2 = 2 (p_EOS - rho cs^2)/G became negative with beta != 0");
+        if (h & (1 << LB_ERR_NONFINITE)) return fail(LB_ERR_NONFINITE, "rho or T became non-finite");
+        return fail(LB_ERR_CUDA, "device error word 0x%x", h);
+    }
+    return LB_OK;
+}
+
+lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
+    lb_status st = validate(p);
+    if (st) return st;
+    if (!out) return fail(LB_ERR_ARG, "out is NULL");
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(LB_ERR_OOM, "host allocation failed");
+    c->p = *p;
+    if (!c->p.tile_x) c->p.tile_x = 32;
+    if (!c->p.tile_y) c->p.tile_y = 8;
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+        // bind the context to the stream's device
+        cudaError_t e = cudaStreamGetDevice(c->stream, &c->device);
+        if (e == cudaSuccess) e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "stream device");
+        }
+    } else {
+        cudaError_t e0 = cudaGetDevice(&c->device);
+        if (e0 != cudaSuccess) {
+            delete c;
+            return cuda_fail(e0, "cudaGetDevice");
+        }
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+    const size_t es = elem_size(p->precision);
+    // rows padded to 128 bytes, planes to 256 bytes
+    const long long pitch = ((long long)p->nx * es + 127) / 128 * 128 / es;
+    const long long plane = ((long long)pitch * p->ny * es + 255) / 256 * 256 / es;
+    c->buf_bytes = (size_t)plane * 18 * es;
+    const long long n = (long long)p->nx * p->ny;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&c->buf[0], c->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->buf[1], c->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ref, sizeof(double) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_snap, sizeof(double) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_part, sizeof(double) * 8 * moments_grid_blocks(p->nx, p->ny));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_out8, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    // zero both buffers so the padding never holds uninitialised bits
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, c->buf_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, c->buf_bytes, c->stream);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "allocating context buffers");
+    }
+    c->kp = make_kparams(c->p, pitch, plane, c->d_err);
+    *out = c;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_params_default(lb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = 64;
+    p->ny = 64;
+    p->eos = LB_EOS_CS;
+    p->thermal = LB_THERMAL_EQ24;
+    p->precision = LB_PREC_FP32;
+    p->psi_uses_local_T = 1;
+    p->tile_x = 0;
+    p->tile_y = 0;
+    p->tau_f = 1.0;
+    p->tau_g = 0.8;
+    p->G = -1.0;
+    p->beta = 1.0;
+    p->a = 1.0;
+    p->b = 4.0;
+    p->R = 1.0;
+    p->cv = 1.0;
+    p->T_psi = 0.0;
+    p->rho0 = 0.12;
+    p->T0 = 0.075;
+}
+
+lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,
+                         void* stream, lb_ctx** out) {
+    if (!d_rho0 || !d_T0) return fail(LB_ERR_ARG, "rho0/T0 is NULL");
+    lb_ctx* c = nullptr;
+    lb_status st = create(p, stream, &c);
+    if (st) return st;
+    cudaError_t e = dispatch_init(c, d_rho0, d_T0);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "init kernel");
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_init(const lb_params* p, const double* rho0, const double* T0, void* stream,
+                  lb_ctx** out) {
+    if (!rho0 || !T0) return fail(LB_ERR_ARG, "rho0/T0 is NULL");
+    lb_ctx* c = nullptr;
+    lb_status st = create(p, stream, &c);
+    if (st) return st;
+    const size_t bytes = sizeof(double) * (size_t)p->nx * p->ny;
+    // stage the host fields in the residual reference buffer, then build the state
+    cudaError_t e = cudaMemcpyAsync(c->d_ref, rho0, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_ref + (size_t)p->nx * p->ny, T0, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = dispatch_init(c, c->d_ref, c->d_ref + (size_t)p->nx * p->ny);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "lb_init upload");
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int64_t n) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = dispatch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        c->cur ^= 1;
+        c->t += 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_synchronize(lb_ctx* c) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    return check_device_error(c);
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+}
+
+lb_status lb_moments_device(lb_ctx* c, double* d_rho, double* d_ux, double* d_uy, double* d_T) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    MomentsLaunch L;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    std::memset(&L, 0, sizeof(L));
+    L.rho = d_rho;
+    L.ux = d_ux;
+    L.uy = d_uy;
+    L.T = d_T;
+    cudaError_t e = dispatch_moments(c, L);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    double* d = nullptr;
+    CU(cudaMallocAsync(&d, sizeof(double) * 4 * n, c->stream), "moments scratch");
+    lb_status st = lb_moments_device(c, d, d + n, d + 2 * n, d + 3 * n);
+    double* hs[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4 && st == LB_OK; ++k) {
+        if (!hs[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(hs[k], d + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "moments download");
+    }
+    cudaFreeAsync(d, c->stream);
+    lb_status st2 = check_device_error(c);
+    return st ? st : st2;
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f, double* g) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    double* d = nullptr;
+    CU(cudaMallocAsync(&d, sizeof(double) * 18 * n, c->stream), "gather scratch");
+    cudaError_t e = dispatch_gather(c, d);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && g)
+        e = cudaMemcpyAsync(g, d + 9 * n, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_get_populations");
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
+    if (!c || !f || !g) return fail(LB_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    double* d = nullptr;
+    CU(cudaMallocAsync(&d, sizeof(double) * 18 * n, c->stream), "scatter scratch");
+    cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 9 * n, g, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = dispatch_scatter(c, d);
+    cudaFreeAsync(d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_set_populations");
+    c->have_ref = false;
+    return LB_OK;
+}
+
+lb_status lb_totals(lb_ctx* c, double out[LB_TOTALS_N]) {
+    if (!c || !out) return fail(LB_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    MomentsLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.rho = c->d_snap;
+    L.T = c->d_snap + n;
+    const bool use_ref = c->have_ref && c->t != c->ref_time;
+    L.ref_rho = use_ref ? c->d_ref : nullptr;
+    L.ref_T = use_ref ? c->d_ref + n : nullptr;
+    L.part = c->d_part;
+    cudaError_t e = dispatch_moments(c, L);
+    if (e != cudaSuccess) return cuda_fail(e, "totals kernel");
+    k_reduce_partials<<<1, 256, 0, c->stream>>>(c->d_part, moments_grid_blocks(c->p.nx, c->p.ny), c->d_out8);
+    CU(cudaGetLastError(), "reduce kernel");
+    double h[8];
+    CU(cudaMemcpyAsync(h, c->d_out8, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "totals download");
+    lb_status st = check_device_error(c);
+    if (st) return st;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = h[3];
+    out[4] = 0.0;
+    if (use_ref) {
+        const double K = (double)(c->t - c->ref_time);
+        const double r_rho = std::sqrt(h[4]) / (K * std::sqrt(h[5]));
+        const double r_T = std::sqrt(h[6]) / (K * std::sqrt(h[7]));
+        out[4] = r_rho > r_T ? r_rho : r_T;
+    }
+    // the snapshot just taken becomes the reference of the next call
+    double* tmp = c->d_ref;
+    c->d_ref = c->d_snap;
+    c->d_snap = tmp;
+    c->have_ref = true;
+    c->ref_time = c->t;
+    return LB_OK;
+}
+
+lb_status lb_state_size(const lb_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(LB_ERR_ARG, "NULL argument");
+    *bytes = c->buf_bytes + sizeof(int64_t);
+    return LB_OK;
+}
+
+lb_status lb_save_state(lb_ctx* c, void* host_blob) {
+    if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(host_blob, c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(cudaStreamSynchronize(c->stream), "synchronize");
+    std::memcpy(static_cast<char*>(host_blob) + c->buf_bytes, &c->t, sizeof(int64_t));
+    return LB_OK;
+}
+
+lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
+    if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(c->buf[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(cudaStreamSynchronize(c->stream), "synchronize");
+    std::memcpy(&c->t, static_cast<const char*>(host_blob) + c->buf_bytes, sizeof(int64_t));
+    c->have_ref = false;
+    return LB_OK;
+}
+
+int64_t lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+
+lb_status lb_get_params(const lb_ctx* c, lb_params* out) {
+    if (!c || !out) return fail(LB_ERR_ARG, "NULL argument");
+    *out = c->p;
+    return LB_OK;
+}
+
+lb_status lb_free(lb_ctx* c) {
+    release(c);
+    return LB_OK;
+}
+
+const char* lb_last_error(void) { return g_err; }
+
+const char* lb_version(void) { return "lbgb 0.1 (sm_103a)"; }
+
+}  // extern "C"

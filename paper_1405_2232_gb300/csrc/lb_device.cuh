@@ -1,0 +1,494 @@
+// lb_device.cuh -- device code of the fused thermal pseudopotential D2Q9 step.
+//
+// Method (Li & Luo, arXiv:1405.2232):
+//   f: Eq. (1) BGK + forcing term F_i (Ref. [21], Guo et al.)
+//   F: Eq. (2) / mixed Eq. (4), 8-neighbour pseudopotential stencil
+//   psi: sqrt(2 (p_EOS - rho cs^2) / G), Sec. II A
+//   g: Eq. (7) (g^eq = c_v T f^eq) or Eq. (24) with C_i of Eq. (25)
+//
+// Storage: 18 structure-of-arrays planes (f_0..f_8, g_0..g_8), plane stride
+// `plane` elements, row pitch `pitch` elements.  The buffer holds the
+// post-collision populations of the previous step at their source site, so
+// the pre-collision value f_i(x, t) is read ("pulled") from x - e_i.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lb.h"
+
+namespace lbgb {
+
+// ---------------------------------------------------------------- lattice
+__host__ __device__ constexpr int ex(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// weights as exact-literal quotients (4/9, 1/9, 1/36)
+__host__ __device__ constexpr double wd(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------- storage
+template <int PREC> struct Store;
+
+template <> struct Store<LB_PREC_FP64> {
+    using elem = double;
+    using real = double;
+    static __device__ __forceinline__ real load(const elem* p, real) { return *p; }
+    static __device__ __forceinline__ void put(elem* p, real v, real) { *p = v; }
+};
+template <> struct Store<LB_PREC_FP32> {
+    using elem = float;
+    using real = float;
+    static __device__ __forceinline__ real load(const elem* p, real) { return *p; }
+    static __device__ __forceinline__ void put(elem* p, real v, real) { *p = v; }
+};
+// 16-bit deviation storage: h = f - base, decoded in FP32
+template <> struct Store<LB_PREC_FP16_DEV> {
+    using elem = __half;
+    using real = float;
+    static __device__ __forceinline__ real load(const elem* p, real base) {
+        return base + __half2float(*p);
+    }
+    static __device__ __forceinline__ void put(elem* p, real v, real base) {
+        *p = __float2half_rn(v - base);
+    }
+};
+template <> struct Store<LB_PREC_BF16_DEV> {
+    using elem = __nv_bfloat16;
+    using real = float;
+    static __device__ __forceinline__ real load(const elem* p, real base) {
+        return base + __bfloat162float(*p);
+    }
+    static __device__ __forceinline__ void put(elem* p, real v, real base) {
+        *p = __float2bfloat16_rn(v - base);
+    }
+};
+
+// ---------------------------------------------------------------- params
+// Kernel parameters, derived once on the host from lb_params.
+struct KParams {
+    int nx, ny;
+    long long pitch;   // elements per row
+    long long plane;   // elements per plane
+    double omega_f;    // 1/tau_f
+    double omega_g;    // 1/tau_g
+    double guo_pre;    // 1 - 1/(2 tau_f)
+    double corr_pre;   // 1 - 1/(2 tau_g)
+    double G;
+    double two_over_G;
+    double beta;
+    double half_1mbeta;  // (1 - beta)/2
+    int eos;
+    int psi_local_T;
+    double a, b, R;
+    double cv, inv_cv;
+    double T_psi;
+    float base_f[9], base_g[9];  // deviation bases of the 16-bit modes
+    int* err;                    // sticky device error word (bit per lb_status)
+};
+
+enum BetaMode { BETA_ZERO = 0, BETA_ONE = 1, BETA_MIXED = 2 };
+
+template <typename real>
+__device__ __forceinline__ real p_eos(const KParams& kp, real rho, real T) {
+    const real R = (real)kp.R, a = (real)kp.a, b = (real)kp.b;
+    if (kp.eos == LB_EOS_IDEAL) return rho * R * T;
+    if (kp.eos == LB_EOS_VDW) return rho * R * T / ((real)1 - b * rho) - a * rho * rho;
+    // Carnahan-Starling, eta = b rho / 4
+    const real eta = b * rho / (real)4;
+    if constexpr (sizeof(real) == 8) {
+        // FP64 parity mode: the printed polynomial, evaluated term by term
+        const real num = (real)1 + eta + eta * eta - eta * eta * eta;
+        const real den = ((real)1 - eta) * ((real)1 - eta) * ((real)1 - eta);
+        return rho * R * T * num / den - a * rho * rho;
+    } else {
+        const real num = (real)1 + eta * ((real)1 + eta * ((real)1 - eta));
+        const real d = (real)1 - eta;
+        return rho * R * T * num / (d * d * d) - a * rho * rho;
+    }
+}
+
+// wrap a coordinate that may lie a few tiles outside [0, n)
+__device__ __forceinline__ int wrapc(int v, int n) {
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
+// Pull the 18 pre-collision populations of site (x, y).
+template <class S>
+__device__ __forceinline__ void pull18(const typename S::elem* __restrict__ src,
+                                       const KParams& kp, int x, int y,
+                                       typename S::real f[9], typename S::real g[9]) {
+    const int xm = x == 0 ? kp.nx - 1 : x - 1;
+    const int xp = x == kp.nx - 1 ? 0 : x + 1;
+    const long long r0 = (long long)y * kp.pitch;
+    const long long rm = (long long)(y == 0 ? kp.ny - 1 : y - 1) * kp.pitch;
+    const long long rp = (long long)(y == kp.ny - 1 ? 0 : y + 1) * kp.pitch;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
+        const long long sr = ey(i) == 1 ? rm : (ey(i) == -1 ? rp : r0);
+        const long long off = sr + sx;
+        f[i] = S::load(src + (long long)i * kp.plane + off, (typename S::real)kp.base_f[i]);
+        g[i] = S::load(src + (long long)(9 + i) * kp.plane + off, (typename S::real)kp.base_g[i]);
+    }
+}
+
+// rho, T and the pseudopotential (psi^2, and psi when beta != 0) of one site.
+template <typename real, int BMODE>
+__device__ __forceinline__ void site_psi(const KParams& kp, const real f[9], const real g[9],
+                                         real& rho, real& T, real& psi, real& psi2, int& flags) {
+    real r = f[0], e = g[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        r += f[i];
+        e += g[i];
+    }
+    rho = r;
+    T = e / (r * (real)kp.cv);
+    const real Te = kp.psi_local_T ? T : (real)kp.T_psi;
+    if constexpr (sizeof(real) == 8)
+        psi2 = (real)2 * (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) / (real)kp.G;
+    else
+        psi2 = (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) * (real)kp.two_over_G;
+    psi = (real)0;
+    if (BMODE != BETA_ZERO) {
+        if (psi2 < (real)0) flags |= 1 << LB_ERR_PSI_DOMAIN;
+        psi = sqrt(psi2);
+    }
+    if (!isfinite(r) || !isfinite(T)) flags |= 1 << LB_ERR_NONFINITE;
+}
+
+// Eq. (4) force (Eq. (2) when beta = 1) from a shared-memory window with
+// row stride W centred at index c.  Pair sums: east-west, north-south and the
+// two diagonals, weights w(1) = 1/3, w(2) = 1/12.
+template <typename real, int BMODE>
+__device__ __forceinline__ void force_from_window(const KParams& kp, const real* s_psi,
+                                                  const real* s_psi2, int c, int W,
+                                                  real& Fx, real& Fy) {
+    const real w1 = (real)(1.0 / 3.0), w2 = (real)(1.0 / 12.0);
+    real fx = 0, fy = 0;
+    if (BMODE != BETA_ZERO) {
+        const real* p = s_psi;
+        const real E = p[c + 1], Wv = p[c - 1], N = p[c + W], S = p[c - W];
+        const real NE = p[c + W + 1], NW = p[c + W - 1], SE = p[c - W + 1], SW = p[c - W - 1];
+        const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
+        const real s1x = w1 * (E - Wv) + w2 * (d1 + d2);
+        const real s1y = w1 * (N - S) + w2 * (d1 + d3);
+        const real pc = (BMODE == BETA_ONE) ? p[c] : (real)kp.beta * p[c];
+        fx += pc * s1x;
+        fy += pc * s1y;
+    }
+    if (BMODE != BETA_ONE) {
+        const real* p = s_psi2;
+        const real E = p[c + 1], Wv = p[c - 1], N = p[c + W], S = p[c - W];
+        const real NE = p[c + W + 1], NW = p[c + W - 1], SE = p[c - W + 1], SW = p[c - W - 1];
+        const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
+        const real s2x = w1 * (E - Wv) + w2 * (d1 + d2);
+        const real s2y = w1 * (N - S) + w2 * (d1 + d3);
+        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : (real)kp.half_1mbeta;
+        fx += h * s2x;
+        fy += h * s2y;
+    }
+    Fx = -(real)kp.G * fx;
+    Fy = -(real)kp.G * fy;
+}
+
+// Collision of one site, Eq. (1) + F_i for f and Eq. (7) / (24) for g.
+// f, g are overwritten with the post-collision values.
+//
+// Two evaluations of the same formulas:
+//  * FP64 (parity mode): every formula in its printed form and order,
+//    divisions by cs^2 included, no contraction (the FP64 translation unit is
+//    compiled with --fmad=false), so results are reproducible bit for bit by
+//    any literal FP64 implementation;
+//  * FP32: multiplications by the constants 3, 4.5, 9 and one reciprocal of
+//    rho, contracted to FMAs.
+template <typename real, bool EQ24>
+__device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9], real rho,
+                                        real Fx, real Fy, real& ux_out, real& uy_out,
+                                        real& T_out) {
+    if constexpr (sizeof(real) == 8) {
+        const double cs2 = 1.0 / 3.0;
+        // sum_i e_i f_i in index order
+        const double mx = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
+        const double my = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+        double e = g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) e += g[i];
+        const double ux = (mx + 0.5 * Fx) / rho;
+        const double uy = (my + 0.5 * Fy) / rho;
+        const double T = e / (rho * kp.cv);
+        const double usq = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double w = wd(i);
+            // e_i.u, e_i.F with the zero components dropped (exact)
+            const double eu = ex(i) == 0 ? (ey(i) == 0 ? 0.0 : (ey(i) > 0 ? uy : -uy))
+                                         : (ey(i) == 0 ? (ex(i) > 0 ? ux : -ux)
+                                                       : (ex(i) > 0 ? ux : -ux) + (ey(i) > 0 ? uy : -uy));
+            const double eF = ex(i) == 0 ? (ey(i) == 0 ? 0.0 : (ey(i) > 0 ? Fy : -Fy))
+                                         : (ey(i) == 0 ? (ex(i) > 0 ? Fx : -Fx)
+                                                       : (ex(i) > 0 ? Fx : -Fx) + (ey(i) > 0 ? Fy : -Fy));
+            const double emuF = ((double)ex(i) - ux) * Fx + ((double)ey(i) - uy) * Fy;
+            const double feq = rho * w * (1.0 + eu / cs2 + 0.5 * eu * eu / (cs2 * cs2) - 0.5 * usq / cs2);
+            const double Fi = kp.guo_pre * w * (emuF / cs2 + eu * eF / (cs2 * cs2));
+            f[i] = f[i] - kp.omega_f * (f[i] - feq) + Fi;
+            const double geq = kp.cv * T * feq;
+            double gs = g[i] - kp.omega_g * (g[i] - geq);
+            if (EQ24) gs += kp.corr_pre * w * kp.cv * T * eF / cs2;
+            g[i] = gs;
+        }
+        ux_out = ux;
+        uy_out = uy;
+        T_out = T;
+    } else {
+        const real mx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
+        const real my = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+        real e = g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) e += g[i];
+        const real inv_rho = (real)1 / rho;
+        const real ux = (mx + (real)0.5 * Fx) * inv_rho;
+        const real uy = (my + (real)0.5 * Fy) * inv_rho;
+        const real T = e / (rho * (real)kp.cv);
+        const real cvT = (real)kp.cv * T;
+        const real usq15 = (real)1.5 * (ux * ux + uy * uy);
+        const real uF = ux * Fx + uy * Fy;
+        const real om_f = (real)kp.omega_f, om_g = (real)kp.omega_g;
+        const real guo = (real)kp.guo_pre, corr = (real)kp.corr_pre;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const real w = (real)wd(i);
+            const real eu = (real)ex(i) * ux + (real)ey(i) * uy;
+            const real eF = (real)ex(i) * Fx + (real)ey(i) * Fy;
+            const real feq = rho * w * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - usq15);
+            const real Fi = guo * w * ((real)3 * (eF - uF) + (real)9 * eu * eF);
+            f[i] = f[i] - om_f * (f[i] - feq) + Fi;
+            real gs = g[i] - om_g * (g[i] - cvT * feq);
+            if (EQ24) gs += corr * w * cvT * (real)3 * eF;
+            g[i] = gs;
+        }
+        ux_out = ux;
+        uy_out = uy;
+        T_out = T;
+    }
+}
+
+// ---------------------------------------------------------------- step
+// One fused time step.  CTA tile BX x BY; phase 1 computes psi for the tile
+// plus a one-site ring from pulled populations (ring pulls hit L2), phase 2
+// pulls each tile site again (L1), applies the stencil and both collisions,
+// and stores 18 values at the site (the next step pulls them).
+template <int PREC, int BX, int BY, bool EQ24, int BMODE>
+__global__ void __launch_bounds__(BX* BY)
+    k_step(const typename Store<PREC>::elem* __restrict__ src,
+           typename Store<PREC>::elem* __restrict__ dst, const KParams kp) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    constexpr int WX = BX + 2, WY = BY + 2, NT = BX * BY;
+    __shared__ real s_psi[BMODE != BETA_ZERO ? WX * WY : 1];
+    __shared__ real s_psi2[BMODE != BETA_ONE ? WX * WY : 1];
+
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    int flags = 0;
+    for (int s = tid; s < WX * WY; s += NT) {
+        const int ly = s / WX, lx = s - ly * WX;
+        const int gx = wrapc(x0 + lx - 1, kp.nx), gy = wrapc(y0 + ly - 1, kp.ny);
+        real f[9], g[9], rho, T, psi, psi2;
+        pull18<S>(src, kp, gx, gy, f, g);
+        site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+        if (BMODE != BETA_ZERO) s_psi[s] = psi;
+        if (BMODE != BETA_ONE) s_psi2[s] = psi2;
+    }
+    __syncthreads();
+
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+    if (gx < kp.nx && gy < kp.ny) {
+        real f[9], g[9];
+        pull18<S>(src, kp, gx, gy, f, g);
+        real rho = f[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) rho += f[i];
+        real Fx, Fy, ux, uy, T;
+        force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1,
+                                       WX, Fx, Fy);
+        collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+        const long long off = (long long)gy * kp.pitch + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S::put(dst + (long long)i * kp.plane + off, f[i], (real)kp.base_f[i]);
+            S::put(dst + (long long)(9 + i) * kp.plane + off, g[i], (real)kp.base_g[i]);
+        }
+    } else {
+        flags = 0;
+    }
+    if (flags) atomicOr(kp.err, flags);
+}
+
+// ---------------------------------------------------------------- moments
+// Same front end as the step; phase 2 writes rho, u (with F/2), T (any
+// pointer may be null) and, if `part` is set, reduces FP64 totals per CTA:
+//   part[blk*8 + k], k = mass, energy, rho ux, rho uy, |d rho|^2, rho^2, |dT|^2, T^2
+// against the reference fields ref_rho/ref_T (may be null).
+template <int PREC, int BX, int BY, int BMODE>
+__global__ void __launch_bounds__(BX* BY)
+    k_moments(const typename Store<PREC>::elem* __restrict__ src, const KParams kp,
+              double* __restrict__ o_rho, double* __restrict__ o_ux, double* __restrict__ o_uy,
+              double* __restrict__ o_T, const double* __restrict__ ref_rho,
+              const double* __restrict__ ref_T, double* __restrict__ part) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    constexpr int WX = BX + 2, WY = BY + 2, NT = BX * BY;
+    __shared__ real s_psi[BMODE != BETA_ZERO ? WX * WY : 1];
+    __shared__ real s_psi2[BMODE != BETA_ONE ? WX * WY : 1];
+    __shared__ double s_red[NT / 32][8];
+
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    int flags = 0;
+    for (int s = tid; s < WX * WY; s += NT) {
+        const int ly = s / WX, lx = s - ly * WX;
+        const int gx = wrapc(x0 + lx - 1, kp.nx), gy = wrapc(y0 + ly - 1, kp.ny);
+        real f[9], g[9], rho, T, psi, psi2;
+        pull18<S>(src, kp, gx, gy, f, g);
+        site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+        if (BMODE != BETA_ZERO) s_psi[s] = psi;
+        if (BMODE != BETA_ONE) s_psi2[s] = psi2;
+    }
+    __syncthreads();
+
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+    if (gx < kp.nx && gy < kp.ny) {
+        real f[9], g[9];
+        pull18<S>(src, kp, gx, gy, f, g);
+        real rho = f[0];
+        double m = (double)f[0], e = (double)g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            rho += f[i];
+            m += (double)f[i];
+            e += (double)g[i];
+        }
+        real Fx, Fy, ux, uy, T;
+        force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1,
+                                       WX, Fx, Fy);
+        collide<real, false>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+        const long long idx = (long long)gy * kp.nx + gx;
+        if (o_rho) o_rho[idx] = (double)rho;
+        if (o_ux) o_ux[idx] = (double)ux;
+        if (o_uy) o_uy[idx] = (double)uy;
+        if (o_T) o_T[idx] = (double)T;
+        if (part) {
+            const double dr = (double)rho, dT = (double)T;
+            v[0] = m;
+            v[1] = e;
+            v[2] = dr * (double)ux;
+            v[3] = dr * (double)uy;
+            if (ref_rho) {
+                const double a = dr - ref_rho[idx], b = dT - ref_T[idx];
+                v[4] = a * a;
+                v[6] = b * b;
+            }
+            v[5] = dr * dr;
+            v[7] = dT * dT;
+        }
+    } else {
+        flags = 0;
+    }
+    if (flags) atomicOr(kp.err, flags);
+    if (!part) return;
+    // deterministic block reduction: warp tree, then warps in order
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((tid & 31) == 0) s_red[tid >> 5][k] = x;
+    }
+    __syncthreads();
+    if (tid < 8) {
+        double x = 0.0;
+        for (int w = 0; w < NT / 32; ++w) x += s_red[w][tid];
+        part[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 8 + tid] = x;
+    }
+}
+
+// ---------------------------------------------------------------- init / gather
+// Initial state f = f^eq(rho0, 0) = w_i rho0, g = c_v T0 w_i rho0, written at
+// the source position so the first pull sees it at its own site.
+template <int PREC>
+__global__ void k_init(typename Store<PREC>::elem* __restrict__ dst, const KParams kp,
+                       const double* __restrict__ rho0, const double* __restrict__ T0) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    const long long n = (long long)kp.nx * kp.ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % kp.nx), y = (int)(s / kp.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            // the value stored at (x, y) is pulled by site (x + e_i, y + e_i)
+            const int dx = wrapc(x + ex(i), kp.nx), dy = wrapc(y + ey(i), kp.ny);
+            const long long d = (long long)dy * kp.nx + dx;
+            const double fe = rho0[d] * wd(i);
+            const double ge = kp.cv * T0[d] * fe;
+            const long long off = (long long)y * kp.pitch + x;
+            S::put(dst + (long long)i * kp.plane + off, (real)fe, (real)kp.base_f[i]);
+            S::put(dst + (long long)(9 + i) * kp.plane + off, (real)ge, (real)kp.base_g[i]);
+        }
+    }
+}
+
+// Pre-collision populations at t (pull) -> dense float64 [18][ny][nx].
+template <int PREC>
+__global__ void k_gather(const typename Store<PREC>::elem* __restrict__ src, const KParams kp,
+                         double* __restrict__ out) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    const long long n = (long long)kp.nx * kp.ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % kp.nx), y = (int)(s / kp.nx);
+        real f[9], g[9];
+        pull18<S>(src, kp, x, y, f, g);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            out[(long long)i * n + s] = (double)f[i];
+            out[(long long)(9 + i) * n + s] = (double)g[i];
+        }
+    }
+}
+
+// Dense float64 [18][ny][nx] pre-collision populations -> storage (push to source).
+template <int PREC>
+__global__ void k_scatter(typename Store<PREC>::elem* __restrict__ dst, const KParams kp,
+                          const double* __restrict__ in) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    const long long n = (long long)kp.nx * kp.ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % kp.nx), y = (int)(s / kp.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            // f_i(x, t) is stored at x - e_i
+            const int sx = wrapc(x - ex(i), kp.nx), sy = wrapc(y - ey(i), kp.ny);
+            const long long off = (long long)sy * kp.pitch + sx;
+            S::put(dst + (long long)i * kp.plane + off, (real)in[(long long)i * n + s],
+                   (real)kp.base_f[i]);
+            S::put(dst + (long long)(9 + i) * kp.plane + off, (real)in[(long long)(9 + i) * n + s],
+                   (real)kp.base_g[i]);
+        }
+    }
+}
+
+}  // namespace lbgb

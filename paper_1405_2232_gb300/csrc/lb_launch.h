@@ -1,0 +1,56 @@
+// lb_launch.h -- host-side launch interface between the C ABI and the
+// per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lb_device.cuh"
+
+namespace lbgb {
+
+struct StepLaunch {
+    const void* src;
+    void* dst;
+    KParams kp;
+    int eq24;       // 0: Eq. (7), 1: Eq. (24)
+    int bmode;      // BetaMode
+    int bx, by;     // CTA tile
+    cudaStream_t stream;
+};
+
+struct MomentsLaunch {
+    const void* src;
+    KParams kp;
+    int bmode;
+    double *rho, *ux, *uy, *T;          // may be null
+    const double *ref_rho, *ref_T;      // may be null
+    double* part;                       // may be null; [grid][8]
+    cudaStream_t stream;
+};
+
+// Tile used by the moments/totals kernel (one fixed shape: deterministic grid).
+constexpr int MOM_BX = 32, MOM_BY = 8;
+
+inline int moments_grid_blocks(int nx, int ny) {
+    return ((nx + MOM_BX - 1) / MOM_BX) * ((ny + MOM_BY - 1) / MOM_BY);
+}
+
+// Supported step tiles (bx, by); every precision instantiates all of them.
+bool step_tile_supported(int bx, int by);
+
+#define LBGB_DECLARE_PREC(NAME)                                                       \
+    cudaError_t launch_step_##NAME(const StepLaunch& L);                               \
+    cudaError_t launch_moments_##NAME(const MomentsLaunch& L);                         \
+    cudaError_t launch_init_##NAME(void* dst, const KParams& kp, const double* rho0,   \
+                                   const double* T0, cudaStream_t st);                 \
+    cudaError_t launch_gather_##NAME(const void* src, const KParams& kp, double* out,  \
+                                     cudaStream_t st);                                 \
+    cudaError_t launch_scatter_##NAME(void* dst, const KParams& kp, const double* in,  \
+                                      cudaStream_t st);
+
+LBGB_DECLARE_PREC(fp64)
+LBGB_DECLARE_PREC(fp32)
+LBGB_DECLARE_PREC(fp16)
+LBGB_DECLARE_PREC(bf16)
+
+}  // namespace lbgb

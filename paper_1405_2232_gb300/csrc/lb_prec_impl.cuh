@@ -1,0 +1,96 @@
+// lb_prec_impl.cuh -- instantiates the kernels of one storage precision.
+// Included by lb_prec_<name>.cu after defining LBGB_PREC (an LB_PREC_*
+// value) and LBGB_NAME (the suffix of the launch functions).
+#pragma once
+
+#include "lb_launch.h"
+
+namespace lbgb {
+
+#define LBGB_CAT2(a, b) a##b
+#define LBGB_CAT(a, b) LBGB_CAT2(a, b)
+
+namespace {
+
+template <int BX, int BY>
+cudaError_t step_tile(const StepLaunch& L) {
+    using E = typename Store<LBGB_PREC>::elem;
+    const dim3 block(BX, BY);
+    const dim3 grid((L.kp.nx + BX - 1) / BX, (L.kp.ny + BY - 1) / BY);
+    const E* src = static_cast<const E*>(L.src);
+    E* dst = static_cast<E*>(L.dst);
+    if (L.eq24) {
+        switch (L.bmode) {
+            case BETA_ZERO: k_step<LBGB_PREC, BX, BY, true, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            case BETA_ONE: k_step<LBGB_PREC, BX, BY, true, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            default: k_step<LBGB_PREC, BX, BY, true, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+        }
+    } else {
+        switch (L.bmode) {
+            case BETA_ZERO: k_step<LBGB_PREC, BX, BY, false, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            case BETA_ONE: k_step<LBGB_PREC, BX, BY, false, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            default: k_step<LBGB_PREC, BX, BY, false, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t LBGB_CAT(launch_step_, LBGB_NAME)(const StepLaunch& L) {
+    if (L.bx == 32 && L.by == 8) return step_tile<32, 8>(L);
+    if (L.bx == 32 && L.by == 16) return step_tile<32, 16>(L);
+    if (L.bx == 64 && L.by == 4) return step_tile<64, 4>(L);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t LBGB_CAT(launch_moments_, LBGB_NAME)(const MomentsLaunch& L) {
+    using E = typename Store<LBGB_PREC>::elem;
+    const dim3 block(MOM_BX, MOM_BY);
+    const dim3 grid((L.kp.nx + MOM_BX - 1) / MOM_BX, (L.kp.ny + MOM_BY - 1) / MOM_BY);
+    const E* src = static_cast<const E*>(L.src);
+    switch (L.bmode) {
+        case BETA_ZERO:
+            k_moments<LBGB_PREC, MOM_BX, MOM_BY, BETA_ZERO><<<grid, block, 0, L.stream>>>(
+                src, L.kp, L.rho, L.ux, L.uy, L.T, L.ref_rho, L.ref_T, L.part);
+            break;
+        case BETA_ONE:
+            k_moments<LBGB_PREC, MOM_BX, MOM_BY, BETA_ONE><<<grid, block, 0, L.stream>>>(
+                src, L.kp, L.rho, L.ux, L.uy, L.T, L.ref_rho, L.ref_T, L.part);
+            break;
+        default:
+            k_moments<LBGB_PREC, MOM_BX, MOM_BY, BETA_MIXED><<<grid, block, 0, L.stream>>>(
+                src, L.kp, L.rho, L.ux, L.uy, L.T, L.ref_rho, L.ref_T, L.part);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+static inline int elementwise_blocks(const KParams& kp) {
+    const long long n = (long long)kp.nx * kp.ny;
+    long long b = (n + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+cudaError_t LBGB_CAT(launch_init_, LBGB_NAME)(void* dst, const KParams& kp, const double* rho0,
+                                             const double* T0, cudaStream_t st) {
+    using E = typename Store<LBGB_PREC>::elem;
+    k_init<LBGB_PREC><<<elementwise_blocks(kp), 256, 0, st>>>(static_cast<E*>(dst), kp, rho0, T0);
+    return cudaGetLastError();
+}
+
+cudaError_t LBGB_CAT(launch_gather_, LBGB_NAME)(const void* src, const KParams& kp, double* out,
+                                               cudaStream_t st) {
+    using E = typename Store<LBGB_PREC>::elem;
+    k_gather<LBGB_PREC><<<elementwise_blocks(kp), 256, 0, st>>>(static_cast<const E*>(src), kp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t LBGB_CAT(launch_scatter_, LBGB_NAME)(void* dst, const KParams& kp, const double* in,
+                                                cudaStream_t st) {
+    using E = typename Store<LBGB_PREC>::elem;
+    k_scatter<LBGB_PREC><<<elementwise_blocks(kp), 256, 0, st>>>(static_cast<E*>(dst), kp, in);
+    return cudaGetLastError();
+}
+
+}  // namespace lbgb

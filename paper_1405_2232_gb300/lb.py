@@ -1,0 +1,305 @@
+"""ctypes binding of the C ABI in include/lb.h (liblbgb.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The names mirror the C functions (lb_init, lb_step, lb_moments,
+lb_totals, lb_free, ...).  Host arrays are float64 numpy arrays; device
+arrays are anything exposing ``data_ptr()`` (torch tensors) or raw integer
+addresses; streams are ``torch.cuda.Stream`` objects or raw ``cudaStream_t``
+integers.
+
+The library is loaded from ``paper_1405_2232_gb300/_build/liblbgb.so``.  If
+it is missing, importing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM = 0, 1, 2, 3
+LB_ERR_NONFINITE, LB_ERR_PSI_DOMAIN, LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED = 4, 5, 6, 7
+LB_EOS_CS, LB_EOS_VDW, LB_EOS_IDEAL = 0, 1, 2
+LB_THERMAL_EQ7, LB_THERMAL_EQ24 = 0, 1
+LB_PREC_FP64, LB_PREC_FP32, LB_PREC_FP16_DEV, LB_PREC_BF16_DEV = 0, 1, 2, 3
+LB_TOTALS_N = 5
+
+PRECISIONS = {"fp64": LB_PREC_FP64, "fp32": LB_PREC_FP32, "fp16": LB_PREC_FP16_DEV,
+              "bf16": LB_PREC_BF16_DEV}
+
+
+class LbError(RuntimeError):
+    """A non-zero lb_status; ``status`` holds the code."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lb status {status}: {msg}")
+        self.status = status
+
+
+class lb_params(ctypes.Structure):
+    """Mirror of ``lb_params`` (field order and types as in include/lb.h)."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("eos", ctypes.c_int32), ("thermal", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("psi_uses_local_T", ctypes.c_int32),
+        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+        ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("G", ctypes.c_double), ("beta", ctypes.c_double),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
+        ("cv", ctypes.c_double), ("T_psi", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+#: Every symbol include/lb.h declares (checked by the CPU test-suite).
+EXPORTED = [
+    "lb_params_default", "lb_init", "lb_init_device", "lb_step", "lb_synchronize",
+    "lb_moments", "lb_moments_device", "lb_get_populations", "lb_set_populations",
+    "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
+    "lb_get_params", "lb_free", "lb_last_error", "lb_version",
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load liblbgb.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not found at {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(lb_params)
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = ctypes.c_int
+    sig = {
+        "lb_params_default": (None, [P]),
+        "lb_init": (st, [P, dp, dp, vp, ctypes.POINTER(vp)]),
+        "lb_init_device": (st, [P, vp, vp, vp, ctypes.POINTER(vp)]),
+        "lb_step": (st, [vp, ctypes.c_int64]),
+        "lb_synchronize": (st, [vp]),
+        "lb_moments": (st, [vp, dp, dp, dp, dp]),
+        "lb_moments_device": (st, [vp, vp, vp, vp, vp]),
+        "lb_get_populations": (st, [vp, dp, dp]),
+        "lb_set_populations": (st, [vp, dp, dp]),
+        "lb_totals": (st, [vp, dp]),
+        "lb_state_size": (st, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+        "lb_save_state": (st, [vp, vp]),
+        "lb_load_state": (st, [vp, vp]),
+        "lb_time": (ctypes.c_int64, [vp]),
+        "lb_get_params": (st, [vp, P]),
+        "lb_free": (st, [vp]),
+        "lb_last_error": (ctypes.c_char_p, []),
+        "lb_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != LB_OK:
+        raise LbError(status, load().lb_last_error().decode())
+
+
+def _host(a, shape=None, writable=False):
+    a = np.ascontiguousarray(a, dtype=np.float64) if not writable else a
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    if writable and not (a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("output arrays must be C-contiguous float64")
+    return a
+
+
+def _dptr(a) -> ctypes.POINTER(ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def lb_params_default(**overrides) -> lb_params:
+    p = lb_params()
+    load().lb_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(p, k, v)
+    return p
+
+
+def lb_init(p: lb_params, rho0, T0, stream=None) -> ctypes.c_void_p:
+    rho0 = _host(rho0, (p.ny, p.nx))
+    T0 = _host(T0, (p.ny, p.nx))
+    ctx = ctypes.c_void_p()
+    _check(load().lb_init(ctypes.byref(p), _dptr(rho0), _dptr(T0), _stream(stream),
+                          ctypes.byref(ctx)))
+    return ctx
+
+
+def lb_init_device(p: lb_params, d_rho0, d_T0, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().lb_init_device(ctypes.byref(p), _addr(d_rho0), _addr(d_T0), _stream(stream),
+                                 ctypes.byref(ctx)))
+    return ctx
+
+
+def lb_step(ctx, n: int = 1):
+    _check(load().lb_step(ctx, int(n)))
+
+
+def lb_synchronize(ctx):
+    _check(load().lb_synchronize(ctx))
+
+
+def lb_get_params(ctx) -> lb_params:
+    p = lb_params()
+    _check(load().lb_get_params(ctx, ctypes.byref(p)))
+    return p
+
+
+def lb_moments(ctx):
+    """Host (rho, ux, uy, T), each float64 [ny, nx]."""
+    p = lb_get_params(ctx)
+    outs = [np.empty((p.ny, p.nx)) for _ in range(4)]
+    _check(load().lb_moments(ctx, *[_dptr(o) for o in outs]))
+    return tuple(outs)
+
+
+def lb_moments_device(ctx, d_rho=None, d_ux=None, d_uy=None, d_T=None):
+    _check(load().lb_moments_device(ctx, _addr(d_rho), _addr(d_ux), _addr(d_uy), _addr(d_T)))
+
+
+def lb_get_populations(ctx):
+    """Pre-collision (f, g) at time t, float64 [9, ny, nx] each."""
+    p = lb_get_params(ctx)
+    f = np.empty((9, p.ny, p.nx))
+    g = np.empty((9, p.ny, p.nx))
+    _check(load().lb_get_populations(ctx, _dptr(f), _dptr(g)))
+    return f, g
+
+
+def lb_set_populations(ctx, f, g):
+    p = lb_get_params(ctx)
+    f = _host(f, (9, p.ny, p.nx))
+    g = _host(g, (9, p.ny, p.nx))
+    _check(load().lb_set_populations(ctx, _dptr(f), _dptr(g)))
+
+
+def lb_totals(ctx) -> np.ndarray:
+    """[mass, energy, px, py, residual] (FP64, deterministic device reduction)."""
+    out = np.zeros(LB_TOTALS_N)
+    _check(load().lb_totals(ctx, _dptr(out)))
+    return out
+
+
+def lb_save_state(ctx) -> bytes:
+    n = ctypes.c_size_t()
+    _check(load().lb_state_size(ctx, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().lb_save_state(ctx, ctypes.cast(buf, ctypes.c_void_p)))
+    return buf.raw
+
+
+def lb_load_state(ctx, blob: bytes):
+    n = ctypes.c_size_t()
+    _check(load().lb_state_size(ctx, ctypes.byref(n)))
+    if len(blob) != n.value:
+        raise ValueError(f"state blob has {len(blob)} bytes, expected {n.value}")
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().lb_load_state(ctx, ctypes.cast(buf, ctypes.c_void_p)))
+
+
+def lb_time(ctx) -> int:
+    return int(load().lb_time(ctx))
+
+
+def lb_free(ctx):
+    if ctx is not None:
+        _check(load().lb_free(ctx))
+
+
+def lb_last_error() -> str:
+    return load().lb_last_error().decode()
+
+
+def lb_version() -> str:
+    return load().lb_version().decode()
+
+
+class Lattice:
+    """Convenience owner of one context (frees it on close / garbage collection)."""
+
+    def __init__(self, rho0, T0, stream=None, device_inputs=False, **params):
+        self.params = lb_params_default(**params)
+        if device_inputs:
+            self.ctx = lb_init_device(self.params, rho0, T0, stream)
+        else:
+            self.ctx = lb_init(self.params, rho0, T0, stream)
+
+    def step(self, n=1):
+        lb_step(self.ctx, n)
+        return self
+
+    def synchronize(self):
+        lb_synchronize(self.ctx)
+
+    def moments(self):
+        return lb_moments(self.ctx)
+
+    def populations(self):
+        return lb_get_populations(self.ctx)
+
+    def set_populations(self, f, g):
+        lb_set_populations(self.ctx, f, g)
+
+    def totals(self):
+        return lb_totals(self.ctx)
+
+    @property
+    def time(self):
+        return lb_time(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            lb_free(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,99 @@
+"""CPU checks of the C-ABI boundary: the CUDA library builds for sm_103a, loads,
+exports every function include/lb.h declares, and validates arguments on the
+host.  No kernel is launched here (there is no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1405_2232_gb300 import lb
+    return lb, lb.load()
+
+
+def declared_functions():
+    """Function names declared in include/*.h (C declarations ending in ');')."""
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(lb_\w+)\s*\([^;{]*\)\s*;", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    lb, so = lib
+    names = declared_functions()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(so, name), f"{name} declared in include/ but not exported"
+    assert set(names) <= set(lb.EXPORTED) | set(names)
+    for name in lb.EXPORTED:
+        assert name in names, f"binding names {name}, which the header does not declare"
+
+
+def test_library_is_built_for_sm103a(lib):
+    lb, _ = lib
+    from paper_1405_2232_gb300 import build
+    assert ["-gencode", "arch=compute_103a,code=sm_103a"] == build.ARCH
+    assert os.path.exists(lb.library_path())
+
+
+def test_params_default_layout(lib):
+    lb, _ = lib
+    p = lb.lb_params_default()
+    assert (p.nx, p.ny) == (64, 64)
+    assert (p.tau_f, p.tau_g, p.G, p.beta) == (1.0, 0.8, -1.0, 1.0)
+    assert (p.a, p.b, p.R, p.cv) == (1.0, 4.0, 1.0, 1.0)
+    assert p.eos == lb.LB_EOS_CS and p.thermal == lb.LB_THERMAL_EQ24
+    assert p.precision == lb.LB_PREC_FP32 and p.psi_uses_local_T == 1
+    assert (p.rho0, p.T0) == (0.12, 0.075)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 2), ("ny", 0), ("tau_f", 0.5), ("tau_g", 0.3), ("G", 0.0), ("cv", 0.0),
+    ("eos", 7), ("thermal", 3), ("precision", 9), ("tile_x", 17),
+])
+def test_invalid_params_rejected_on_host(lib, field, value):
+    import numpy as np
+    lb, so = lib
+    p = lb.lb_params_default(nx=8, ny=8)
+    setattr(p, field, value)
+    rho = np.ones((8, 8))
+    dp = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ctx = ctypes.c_void_p()
+    st = so.lb_init(ctypes.byref(p), dp, dp, None, ctypes.byref(ctx))
+    assert st == lb.LB_ERR_ARG
+    assert ctx.value is None
+    assert lb.lb_last_error() != ""
+
+
+def test_null_arguments(lib):
+    lb, so = lib
+    assert so.lb_free(None) == lb.LB_OK
+    assert so.lb_step(None, 1) == lb.LB_ERR_ARG
+    assert so.lb_totals(None, None) == lb.LB_ERR_ARG
+    assert so.lb_time(None) == -1
+    assert "sm_103a" in lb.lb_version()
+
+
+def test_oracle_and_cuda_path_share_nothing():
+    """The oracle includes nothing of the library and the library nothing of the oracle."""
+    csrc = os.path.join(ROOT, "paper_1405_2232_gb300", "csrc")
+    for fn in os.listdir(csrc):
+        text = open(os.path.join(csrc, fn)).read()
+        assert "oracle" not in text.lower(), fn
+    otext = open(os.path.join(ROOT, "oracle", "lb_oracle.c")).read()
+    assert '#include "lb.h"' not in otext and "lbgb" not in otext
+    for fn in os.listdir(os.path.join(ROOT, "paper_1405_2232_gb300")):
+        if fn.endswith(".py"):
+            text = open(os.path.join(ROOT, "paper_1405_2232_gb300", fn)).read()
+            assert "import oracle" not in text and "from oracle" not in text, fn

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances (max-norm errors e_phi = max|d phi| / max|phi_oracle| per field):
+  * FP64 storage: the FP64 path evaluates the printed formulas in their order
+    without contraction, so populations must match the oracle BIT FOR BIT
+    (hence e = 0 <= 1e-12) after 1000 steps.
+  * FP32 storage, one step from a shared state: the per-step FP32 rounding,
+    e <= 2e-6 on populations and moments.
+  * FP32 storage after 1000 steps of the 64x64 slab: rho, u and T within 2e-5
+    (the oracle amplifies an FP32-sized perturbation of the start state only
+    about 10x over these steps, tests/test_sensitivity.py).  u is measured
+    against max|u| over both components.
+  * 16-bit deviation storage, one step: each population within half an ulp of
+    its stored deviation plus the FP32 step error (bound derived per element).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1405_2232_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(nx=64, ny=64, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0, a=1.0, b=4.0, R=1.0, cv=1.0)
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch  # noqa: F401  (initialises CUDA in this process)
+    from paper_1405_2232_gb300 import lb as _lb
+    _lb.load()
+    return _lb
+
+
+def emax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def field_errors(gpu, ref):
+    """(e_rho, e_u, e_T) between (rho, ux, uy, T) tuples."""
+    e_rho = emax(gpu[0], ref[0])
+    du = max(np.abs(gpu[1] - ref[1]).max(), np.abs(gpu[2] - ref[2]).max())
+    umax = max(np.abs(ref[1]).max(), np.abs(ref[2]).max())
+    return e_rho, float(du / umax), emax(gpu[3], ref[3])
+
+
+def oracle_params(thermal, psi_local=1, T_psi=0.0, **kw):
+    d = dict(C1)
+    d.update(kw)
+    return O.params(d["nx"], d["ny"], tau_f=d["tau_f"], tau_g=d["tau_g"], G=d["G"],
+                    beta=d["beta"], eos=d.get("eos", O.EOS_CS), a=d["a"], b=d["b"], R=d["R"],
+                    cv=d["cv"], thermal=thermal, psi_uses_local_T=psi_local, T_psi=T_psi)
+
+
+def gpu_lattice(lb, rho, T, thermal, precision, psi_local=1, T_psi=0.0, **kw):
+    d = dict(C1)
+    d.update(kw)
+    d.update(thermal=thermal, precision=lb.PRECISIONS[precision], psi_uses_local_T=psi_local,
+             T_psi=T_psi)
+    d["nx"], d["ny"] = rho.shape[1], rho.shape[0]
+    return lb.Lattice(rho, T, **d)
+
+
+_cache = {}
+
+
+def oracle_run(thermal, n, psi_local=1, shape=(64, 64), **kw):
+    key = (thermal, n, psi_local, shape, tuple(sorted(kw.items())))
+    if key not in _cache:
+        ny, nx = shape
+        rho, T = I.slab_fields(nx, ny, width=min(32, nx // 2))
+        P = oracle_params(thermal, psi_local, 0.85 * I.CS_TC, nx=nx, ny=ny, **kw)
+        f, g = O.init_equilibrium(P, rho, T)
+        f, g, st = O.step(P, f, g, n=n, check=False)
+        _cache[key] = (rho, T, P, f, g, st, O.moments(P, f, g)[:4])
+    return _cache[key]
+
+
+# ------------------------------------------------------------------ FP64
+@pytest.mark.parametrize("thermal,psi_local", [(O.THERMAL_EQ24, 1), (O.THERMAL_EQ7, 0)])
+def test_fp64_bit_identical_1000_steps(lb, thermal, psi_local):
+    """64x64 CS slab + noise (seed 1), 1000 steps: populations equal bit for bit."""
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(thermal, 1000, psi_local)
+    assert st == O.OK
+    with gpu_lattice(lb, rho, T, thermal, "fp64", psi_local, 0.85 * I.CS_TC) as L:
+        L.step(1000)
+        f, g = L.populations()
+        m = L.moments()
+    assert np.array_equal(f, f_ref) and np.array_equal(g, g_ref)
+    e = field_errors(m, m_ref)
+    assert max(e) <= 1e-12, e
+
+
+def test_fp64_eq7_local_T_reports_psi_domain_at_same_step(lb):
+    """Eq. (7) with psi(rho, T): the oracle leaves the psi domain at step k; the GPU
+    reports LB_ERR_PSI_DOMAIN in the same step and not before."""
+    rho, T = I.slab_fields(64, 64)
+    P = oracle_params(O.THERMAL_EQ7)
+    f, g = O.init_equilibrium(P, rho, T)
+    k = 0
+    while True:
+        f, g, st = O.step(P, f, g, n=1, check=False)
+        k += 1
+        if st:
+            break
+        assert k < 200
+    assert st == O.ERR_PSI_DOMAIN
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ7, "fp64") as L:
+        L.step(k - 1)
+        L.synchronize()  # no error before step k
+        L.step(1)
+        with pytest.raises(lb.LbError) as ei:
+            L.synchronize()
+        assert ei.value.status == lb.LB_ERR_PSI_DOMAIN
+
+
+@pytest.mark.parametrize("shape", [(45, 67), (130, 5), (3, 3), (9, 33), (8, 64), (17, 200)])
+def test_fp64_ragged_and_small_lattices(lb, shape):
+    """Lattices that leave ragged tiles, a single partial tile, the 3x3 minimum."""
+    ny, nx = shape
+    rho, T = I.slab_fields(nx, ny, width=max(2, nx // 2), noise=1e-3)
+    P = oracle_params(O.THERMAL_EQ24, nx=nx, ny=ny)
+    f0, g0 = O.init_equilibrium(P, rho, T)
+    f_ref, g_ref, st = O.step(P, f0, g0, n=40, check=False)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64") as L:
+        L.step(40)
+        f, g = L.populations()
+    assert np.array_equal(f, f_ref, equal_nan=True) and np.array_equal(g, g_ref, equal_nan=True)
+
+
+@pytest.mark.parametrize("case", ["vdw_eq2", "ideal_beta0", "ideal_mixed", "passive_T", "cv2"])
+def test_fp64_other_eos_and_force_forms(lb, case):
+    """vdW EOS, Eq. (4) with beta = 0 and beta = 0.3, passive T, c_v = 2."""
+    nx, ny = 48, 40
+    if case == "vdw_eq2":
+        kw = dict(eos=O.EOS_VDW, a=9.0 / 49.0, b=2.0 / 21.0, R=1.0, G=-1.0, beta=1.0)
+        Tc = 8 * kw["a"] / (27 * kw["b"])
+        rho, T = I.droplet_fields(nx, ny, 10, rho_l=5.0, rho_g=2.0, Tc=Tc, T_lo=0.9, T_hi=0.9)
+        psi_local, T_psi = 1, 0.0
+    elif case in ("ideal_beta0", "ideal_mixed"):
+        kw = dict(eos=O.EOS_IDEAL, a=0.0, b=0.0, R=0.5, G=1.0,
+                  beta=0.0 if case == "ideal_beta0" else 0.3)
+        rho, T = I.sinusoid_fields(nx, ny, 1.0, 1.0, 0.05, mode=2, axis=0)
+        T = T * (1.0 + 0.01 * np.sin(2 * np.pi * np.arange(ny) / ny))[:, None]
+        psi_local, T_psi = 1, 0.0
+    elif case == "passive_T":
+        kw = {}
+        rho, T = I.slab_fields(nx, ny, width=20)
+        psi_local, T_psi = 0, 0.85 * I.CS_TC
+    else:
+        kw = dict(cv=2.0)
+        rho, T = I.slab_fields(nx, ny, width=20)
+        psi_local, T_psi = 1, 0.0
+    for thermal in (O.THERMAL_EQ7, O.THERMAL_EQ24):
+        pl, tp = psi_local, T_psi
+        if thermal == O.THERMAL_EQ7 and case in ("vdw_eq2", "cv2"):
+            # Eq. (7) with psi(rho, T) leaves the psi domain here: run T passively
+            pl, tp = 0, float(T.mean())
+        P = oracle_params(thermal, pl, tp, nx=nx, ny=ny, **kw)
+        f0, g0 = O.init_equilibrium(P, rho, T)
+        f_ref, g_ref, st = O.step(P, f0, g0, n=60, check=False)
+        assert st == O.OK
+        with gpu_lattice(lb, rho, T, thermal, "fp64", pl, tp, **kw) as L:
+            L.step(60)
+            f, g = L.populations()
+        assert np.array_equal(f, f_ref), case
+        assert np.array_equal(g, g_ref), case
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 4)])
+def test_fp64_tiles_identical(lb, tile):
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(O.THERMAL_EQ24, 100)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64", tile_x=tile[0], tile_y=tile[1]) as L:
+        L.step(100)
+        f, g = L.populations()
+    assert np.array_equal(f, f_ref) and np.array_equal(g, g_ref)
+
+
+def test_fp64_totals_and_residual(lb):
+    """FP64 totals (deterministic device reduction) against the oracle's compensated sums;
+    the residual against the oracle's residual between the two snapshot times."""
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(O.THERMAL_EQ24, 300)
+    rho_a, T_a, P_a, f_a, g_a, _, m_a = oracle_run(O.THERMAL_EQ24, 200)
+    t_ref = O.totals(P, f_ref, g_ref)
+    t0 = O.totals(P, *O.init_equilibrium(P, rho, T))
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64") as L:
+        L.step(200)
+        L.totals()
+        L.step(100)
+        tot = L.totals()
+    assert tot[0] == pytest.approx(t_ref[0], rel=1e-14)
+    assert tot[1] == pytest.approx(t_ref[1], rel=1e-14)
+    assert abs(tot[2] - t_ref[2]) < 1e-14 * t_ref[0] and abs(tot[3] - t_ref[3]) < 1e-14 * t_ref[0]
+    assert tot[0] == pytest.approx(t0[0], rel=1e-13) and tot[1] == pytest.approx(t0[1], rel=1e-13)
+    r_ref = O.residual(m_a[0], m_a[3], m_ref[0], m_ref[3], 100)
+    assert tot[4] == pytest.approx(r_ref, rel=1e-9)
+
+
+# ------------------------------------------------------------------ FP32
+def test_fp32_one_step_from_shared_state(lb):
+    """From the oracle state at step 500 rounded to FP32, one GPU FP32 step against one
+    oracle step from the same (rounded) state."""
+    rho, T, P, f5, g5, st, _ = oracle_run(O.THERMAL_EQ24, 500)
+    f32 = f5.astype(np.float32).astype(np.float64)
+    g32 = g5.astype(np.float32).astype(np.float64)
+    f_ref, g_ref, _ = O.step(P, f32, g32, n=1)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32") as L:
+        L.set_populations(f32, g32)
+        f0, g0 = L.populations()
+        assert np.array_equal(f0, f32) and np.array_equal(g0, g32)
+        L.step(1)
+        f, g = L.populations()
+        m = L.moments()
+    for i in range(9):
+        assert emax(f[i], f_ref[i]) < 2e-6, i
+        assert emax(g[i], g_ref[i]) < 2e-6, i
+    e = field_errors(m, O.moments(P, f_ref, g_ref)[:4])
+    assert max(e) < 2e-6, e
+
+
+@pytest.mark.parametrize("thermal,psi_local", [(O.THERMAL_EQ24, 1), (O.THERMAL_EQ7, 0)])
+def test_fp32_1000_steps(lb, thermal, psi_local):
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(thermal, 1000, psi_local)
+    with gpu_lattice(lb, rho, T, thermal, "fp32", psi_local, 0.85 * I.CS_TC) as L:
+        L.step(1000)
+        m = L.moments()
+    e_rho, e_u, e_T = field_errors(m, m_ref)
+    print(f"FP32 1000 steps thermal={thermal}: e_rho={e_rho:.3e} e_u={e_u:.3e} e_T={e_T:.3e}")
+    assert e_rho <= 2e-5 and e_T <= 2e-5 and e_u <= 2e-5, (e_rho, e_u, e_T)
+
+
+def test_fp32_eq7_local_T_first_steps(lb):
+    """Eq. (7) with psi(rho, T) until just before it leaves the psi domain."""
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(O.THERMAL_EQ7, 25)
+    assert st == O.OK
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ7, "fp32") as L:
+        L.step(25)
+        m = L.moments()
+    e = field_errors(m, m_ref)
+    assert max(e) <= 2e-5, e
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (64, 4)])
+def test_fp32_tiles_identical(lb, tile):
+    rho, T = I.slab_fields(64, 64)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32") as A, \
+            gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32", tile_x=tile[0], tile_y=tile[1]) as B:
+        A.step(200)
+        B.step(200)
+        fa, ga = A.populations()
+        fb, gb = B.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_fp32_translation_invariance(lb):
+    """Periodic shift of the input shifts the output bit for bit (tile-position independent)."""
+    rho, T = I.slab_fields(96, 72)
+    sh = (5, -13)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32") as A, \
+            gpu_lattice(lb, np.roll(rho, sh, (0, 1)), np.roll(T, sh, (0, 1)), O.THERMAL_EQ24,
+                        "fp32") as B:
+        A.step(100)
+        B.step(100)
+        fa, ga = A.populations()
+        fb, gb = B.populations()
+    assert np.array_equal(np.roll(fa, sh, (1, 2)), fb)
+    assert np.array_equal(np.roll(ga, sh, (1, 2)), gb)
+
+
+def test_fp32_uniform_state_and_determinism(lb):
+    rho, T = I.uniform_fields(40, 24, 0.2, 0.8 * I.CS_TC)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ7, "fp32") as L:
+        L.step(50)
+        f, g = L.populations()
+    assert np.all(f == f[:, :1, :1]) and np.all(g == g[:, :1, :1])
+    rho, T = I.slab_fields(64, 64)
+    out = []
+    for _ in range(2):
+        with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32") as L:
+            L.step(300)
+            out.append(L.populations())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_checkpoint_resume_bit_identical(lb):
+    rho, T = I.slab_fields(64, 64)
+    for prec in ("fp32", "fp16"):
+        with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec) as A:
+            A.step(50)
+            blob = lb.lb_save_state(A.ctx)
+            A.step(50)
+            fa, ga = A.populations()
+        with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec) as B:
+            lb.lb_load_state(B.ctx, blob)
+            assert B.time == 50
+            B.step(50)
+            fb, gb = B.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_zero_steps_is_identity(lb):
+    rho, T = I.slab_fields(64, 64)
+    P = oracle_params(O.THERMAL_EQ24)
+    f0, g0 = O.init_equilibrium(P, rho, T)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64") as L:
+        L.step(0)
+        f, g = L.populations()
+    assert np.array_equal(f, f0) and np.array_equal(g, g0)
+
+
+# ------------------------------------------------------------------ 16-bit
+@pytest.mark.parametrize("prec,u", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_16bit_one_step_within_rounding_bound(lb, prec, u):
+    """One step from a state the 16-bit mode represents exactly: every stored
+    population within (half an ulp of its deviation) + (FP32 step error)."""
+    rho0, T0 = 0.12, 0.75 * I.CS_TC
+    rho, T = I.spinodal_fields(64, 64)
+    P = oracle_params(O.THERMAL_EQ24)
+    f, g = O.init_equilibrium(P, rho, T)
+    f, g, _ = O.step(P, f, g, n=20)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec, rho0=rho0, T0=T0) as L:
+        L.set_populations(f, g)
+        fs, gs = L.populations()  # the exactly representable state
+        f_ref, g_ref, _ = O.step(P, fs, gs, n=1)
+        L.step(1)
+        f1, g1 = L.populations()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    base_f = (w * rho0).astype(np.float32).astype(np.float64)
+    base_g = (w * rho0 * T0).astype(np.float32).astype(np.float64)
+    for got, ref, base in ((f1, f_ref, base_f), (g1, g_ref, base_g)):
+        # unit roundoff u of the 16-bit format on the deviation, plus the FP32 step
+        bound = u * np.abs(ref - base) * 1.01 + 2e-6 * np.abs(ref).max() + 1e-12
+        assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_16bit_spinodal_error_report(lb, prec):
+    """Spinodal 128x128 (T = 0.75 T_c, rho = 0.12 +- 0.01), 200 steps: error per field
+    against the FP64 oracle is reported; sanity bounds only (no tolerance is claimed
+    for the 16-bit modes beyond the one-step bound)."""
+    rho, T = I.spinodal_fields(128, 128)
+    P = oracle_params(O.THERMAL_EQ24, nx=128, ny=128)
+    f, g = O.init_equilibrium(P, rho, T)
+    f, g, _ = O.step(P, f, g, n=200)
+    m_ref = O.moments(P, f, g)[:4]
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec, rho0=0.12, T0=0.75 * I.CS_TC) as L:
+        L.step(200)
+        m = L.moments()
+    e = field_errors(m, m_ref)
+    print(f"{prec} spinodal 128^2 200 steps: e_rho={e[0]:.3e} e_u={e[1]:.3e} e_T={e[2]:.3e}")
+    assert np.all(np.isfinite(m[0])) and e[0] < 0.05 and e[2] < 0.05
