@@ -3,8 +3,9 @@
 
 Workload (one GPU): spinodal decomposition on a periodic 4096 x 4096 lattice,
 Carnahan-Starling EOS (a = 1, b = 4, R = 1), T = 0.75 T_c, rho = 0.12 plus
-seeded noise +-0.01 (seed 3), G = -1, tau_f = 1, tau_g = 0.8, corrected
-temperature treatment Eq. (24), FP32 populations.
+seeded noise +-0.01 (seed 3), G = -1, tau_f = 1, tau_g = 0.8, mixed
+pseudopotential force Eq. (4) with beta = 1.16, corrected temperature
+treatment Eq. (24), FP32 populations.
 
 A bench "step" is a segment of SEG fused LB time steps over the whole lattice
 (every time step is one kernel launch that reads and writes every population
@@ -42,6 +43,9 @@ NX = NY = 4096
 SEG = 100                       # LB time steps per bench step
 BYTES_PER_SITE = {"fp64": 288, "fp32": 144, "fp16": 72, "bf16": 72}
 CPU_SAMPLE = 1024               # oracle sample lattice (CPU baseline / reference arm)
+# Mixed force Eq. (4) with beta = 1.16: with Eq. (2) (beta = 1) this deep quench
+# (T = 0.75 T_c) drives the vapour density below zero within ~200 steps.
+BETA = 1.16
 
 
 def workload_params(lb, precision="fp32", thermal=None, nx=None, ny=None):
@@ -49,7 +53,7 @@ def workload_params(lb, precision="fp32", thermal=None, nx=None, ny=None):
     nx = NX if nx is None else nx
     ny = NY if ny is None else ny
     thermal = lb.LB_THERMAL_EQ24 if thermal is None else thermal
-    return lb.lb_params_default(nx=nx, ny=ny, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0,
+    return lb.lb_params_default(nx=nx, ny=ny, tau_f=1.0, tau_g=0.8, G=-1.0, beta=BETA,
                                 a=1.0, b=4.0, R=1.0, cv=1.0, thermal=thermal,
                                 precision=precision, rho0=0.12, T0=0.75 * I.CS_TC)
 
@@ -173,7 +177,7 @@ def cpu_oracle_rate(steps, threads=None):
     from paper_1405_2232_gb300 import inputs as I
     threads = threads or os.cpu_count() or 1
     rho, T = I.spinodal_fields(CPU_SAMPLE, CPU_SAMPLE)
-    P = O.params(CPU_SAMPLE, CPU_SAMPLE, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0,
+    P = O.params(CPU_SAMPLE, CPU_SAMPLE, tau_f=1.0, tau_g=0.8, G=-1.0, beta=BETA,
                  eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, thermal=O.THERMAL_EQ24)
     f, g = O.init_equilibrium(P, rho, T)
     t0 = time.perf_counter()
@@ -192,7 +196,7 @@ def run_reference(args, world, rank):
     from paper_1405_2232_gb300 import inputs as I
     threads = os.cpu_count() or 1
     rho, T = I.spinodal_fields(CPU_SAMPLE, CPU_SAMPLE)
-    P = O.params(CPU_SAMPLE, CPU_SAMPLE, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0,
+    P = O.params(CPU_SAMPLE, CPU_SAMPLE, tau_f=1.0, tau_g=0.8, G=-1.0, beta=BETA,
                  eos=O.EOS_CS, a=1.0, b=4.0, R=1.0, thermal=O.THERMAL_EQ24)
     f, g = O.init_equilibrium(P, rho, T)
     f, g, _ = O.step(P, f, g, n=args.warmup, threads=threads, check=False)
@@ -216,6 +220,12 @@ def run_reference(args, world, rank):
     return 0
 
 
+def set_size(n, seg):
+    global NX, NY, SEG
+    NX = NY = n
+    SEG = seg
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,9 +241,7 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    global NX, NY, SEG
-    NX = NY = args.nx
-    SEG = args.seg
+    set_size(args.nx, args.seg)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -365,6 +373,7 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
         "config": {"workload": f"spinodal_{NX}x{NY}_CS_T0.75Tc_rho0.12pm0.01_eq24_fp32",
                    "nx": NX, "ny": NY, "lb_steps_per_bench_step": SEG,
                    "thermal": "Eq.24", "storage": "fp32", "tau_f": 1.0, "tau_g": 0.8, "G": -1.0,
+                   "force": "Eq.4", "beta": BETA,
                    "l2": "state 2x1.21 GB > 129 MB L2, no flush needed",
                    "parallelism": f"independent lattice per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

@@ -257,12 +257,14 @@ def lb_version() -> str:
 class Lattice:
     """Convenience owner of one context (frees it on close / garbage collection)."""
 
-    def __init__(self, rho0, T0, stream=None, device_inputs=False, **params):
+    def __init__(self, rho, T, stream=None, device_inputs=False, **params):
+        """rho, T: initial density and temperature fields [ny, nx] (host float64
+        arrays, or device arrays with device_inputs=True); params: lb_params fields."""
         self.params = lb_params_default(**params)
         if device_inputs:
-            self.ctx = lb_init_device(self.params, rho0, T0, stream)
+            self.ctx = lb_init_device(self.params, rho, T, stream)
         else:
-            self.ctx = lb_init(self.params, rho0, T0, stream)
+            self.ctx = lb_init(self.params, rho, T, stream)
 
     def step(self, n=1):
         lb_step(self.ctx, n)
