@@ -64,8 +64,15 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
     if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
-    const int tx = p->tile_x ? p->tile_x : 32, ty = p->tile_y ? p->tile_y : 8;
-    if (!step_tile_supported(tx, ty)) return fail(LB_ERR_ARG, "unsupported tile %dx%d", tx, ty);
+    if (p->tile_x || p->tile_y) {
+        if (!step_tile_supported(p->tile_x, p->tile_y))
+            return fail(LB_ERR_ARG, "unsupported tile %dx%d", p->tile_x, p->tile_y);
+        if (p->tile_y == 0 && p->precision == LB_PREC_FP64 && p->tile_x != 128)
+            return fail(LB_ERR_ARG, "the FP64 strip kernel is 128 columns wide");
+        if (p->tile_y == 0 && p->nx % strip_halo(p->precision) != 0)
+            return fail(LB_ERR_ARG, "strip kernel needs nx to be a multiple of %d",
+                        strip_halo(p->precision));
+    }
     return LB_OK;
 }
 
@@ -73,7 +80,8 @@ lb_status validate(const lb_params* p) {
 
 namespace lbgb {
 bool step_tile_supported(int bx, int by) {
-    return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 4);
+    return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 4) ||
+           (by == 0 && (bx == 128 || bx == 256));
 }
 
 // Final reduction of the per-CTA partials in a fixed order (one CTA).
@@ -116,6 +124,7 @@ struct lb_ctx {
     bool have_ref = false;
     int64_t ref_time = 0;
     int64_t t = 0;
+    int nchunks = 1;            // strip kernel: row chunks per strip
 };
 
 namespace {
@@ -163,6 +172,7 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.bmode = bmode_of(c->p.beta);
     L.bx = c->p.tile_x;
     L.by = c->p.tile_y;
+    L.nchunks = c->nchunks;
     L.stream = c->stream;
     switch (c->p.precision) {
         case LB_PREC_FP64: return launch_step_fp64(L);
@@ -254,8 +264,6 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     lb_ctx* c = new (std::nothrow) lb_ctx();
     if (!c) return fail(LB_ERR_OOM, "host allocation failed");
     c->p = *p;
-    if (!c->p.tile_x) c->p.tile_x = 32;
-    if (!c->p.tile_y) c->p.tile_y = 8;
     if (stream) {
         c->stream = static_cast<cudaStream_t>(stream);
         // bind the context to the stream's device
@@ -301,6 +309,28 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         return cuda_fail(e, "allocating context buffers");
     }
     c->kp = make_kparams(c->p, pitch, plane, c->d_err);
+    // kernel choice: the strip-marching TMA kernel where its alignment rules
+    // hold, else the tile kernel
+    if (c->p.tile_x == 0 && c->p.tile_y == 0) {
+        const int bx = p->precision == LB_PREC_FP64 ? 128 : 256;
+        if (strip_eligible(p->precision, p->nx, plane, bx)) {
+            c->p.tile_x = bx;
+            c->p.tile_y = 0;
+        } else {
+            c->p.tile_x = 32;
+            c->p.tile_y = 8;
+        }
+    }
+    if (c->p.tile_y == 0) {
+        // about two resident CTAs per SM, chunks of at least 8 rows
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0)
+            sms = 152;
+        const int strips = (p->nx + c->p.tile_x - 1) / c->p.tile_x;
+        int nch = (2 * sms + strips - 1) / strips;
+        const int max_ch = p->ny / 8 > 0 ? p->ny / 8 : 1;
+        c->nchunks = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
+    }
     *out = c;
     return LB_OK;
 }

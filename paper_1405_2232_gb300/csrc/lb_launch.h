@@ -14,7 +14,8 @@ struct StepLaunch {
     KParams kp;
     int eq24;       // 0: Eq. (7), 1: Eq. (24)
     int bmode;      // BetaMode
-    int bx, by;     // CTA tile
+    int bx, by;     // CTA tile; by == 0: strip kernel of width bx
+    int nchunks;    // strip kernel: row chunks per strip
     cudaStream_t stream;
 };
 
@@ -36,7 +37,17 @@ inline int moments_grid_blocks(int nx, int ny) {
 }
 
 // Supported step tiles (bx, by); every precision instantiates all of them.
+// (bx, 0) selects the strip-marching kernel of width bx.
 bool step_tile_supported(int bx, int by);
+
+// Column halo of the strip kernel (16 bytes of elements) and its eligibility:
+// nx a multiple of the halo, and 32-bit element offsets over the 18 planes.
+inline int strip_halo(int prec) { return prec == LB_PREC_FP64 ? 2 : (prec == LB_PREC_FP32 ? 4 : 8); }
+inline bool strip_eligible(int prec, int nx, long long plane, int bx) {
+    if (prec == LB_PREC_FP64 && bx != 128) return false;
+    if (bx != 128 && bx != 256) return false;
+    return nx % strip_halo(prec) == 0 && 18LL * plane < (1LL << 32);
+}
 
 #define LBGB_DECLARE_PREC(NAME)                                                       \
     cudaError_t launch_step_##NAME(const StepLaunch& L);                               \

