@@ -95,9 +95,10 @@ cudaError_t step_strip(const StepLaunch& L) {
 cudaError_t LBGB_CAT(launch_step_, LBGB_NAME)(const StepLaunch& L) {
     if (L.by == 0) {
         if (L.bx == 128) return step_strip<128>(L);
-#if LBGB_PREC != LB_PREC_FP64
-        if (L.bx == 256) return step_strip<256>(L);
-#endif
+        // (LB_PREC_* are enum constants, invisible to the preprocessor)
+        if constexpr (LBGB_PREC != LB_PREC_FP64) {
+            if (L.bx == 256) return step_strip<256>(L);
+        }
         return cudaErrorInvalidValue;
     }
     if (L.bx == 32 && L.by == 8) return step_tile<32, 8>(L);

@@ -32,3 +32,18 @@ def test_no_symbol_shared_between_precision_objects():
                 seen.setdefault(parts[2], set()).add(o)
     shared = {s: sorted(v) for s, v in seen.items() if len(v) > 1 and s not in ALLOWED}
     assert not shared, f"symbols defined by several precision objects: {list(shared)[:5]}"
+
+
+def test_every_strip_kernel_width_is_compiled():
+    """The strip kernel exists at width 128 for every precision and at 256 for the
+    FP32 and 16-bit modes (the launcher returns cudaErrorInvalidValue otherwise)."""
+    from paper_1405_2232_gb300 import build
+    build.build()
+    want = {"fp64": ["128"], "fp32": ["128", "256"], "fp16": ["128", "256"], "bf16": ["128", "256"]}
+    prec_id = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+    for name, widths in want.items():
+        out = subprocess.run(["nm", "--defined-only", os.path.join(BUILD, f"lb_prec_{name}.o")],
+                             capture_output=True, text=True, check=True).stdout
+        for w in widths:
+            tag = f"k_step_stripILi{prec_id[name]}ELi{w}E"
+            assert tag in out, f"{name}: no strip kernel of width {w}"
