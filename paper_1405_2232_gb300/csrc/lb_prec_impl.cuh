@@ -47,7 +47,7 @@ template <int BX>
 constexpr int strip_stages() {
     constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<LBGB_PREC>::HALO) * StripCfg<LBGB_PREC>::ES;
     constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<LBGB_PREC>::real);
-    constexpr size_t budget = 110 * 1024;
+    constexpr size_t budget = 110 * 1024 - 32;
     constexpr size_t s = (budget - ring) / stage;
     return s > 12 ? 12 : (int)s;
 }
@@ -69,8 +69,8 @@ cudaError_t strip_launch(const StepLaunch& L) {
         if (dev < 64) configured |= 1ULL << dev;
     }
     const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
-    kern<<<grid, BX, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst), L.kp,
-                                       L.nchunks);
+    kern<<<grid, BX + 32, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
+                                            L.kp, L.nchunks);
     return cudaGetLastError();
 }
 

@@ -4,12 +4,12 @@
 // Each CTA owns a strip of BX columns and a chunk of rows and marches up the
 // rows.  For every pre-collision row y it needs plane i of source row
 // y - e_iy, columns [x0 - HALO, x0 + W + HALO) (HALO * sizeof(elem) = 16
-// bytes, so every copy is 16-byte aligned); one elected thread streams these
+// bytes, so every copy is 16-byte aligned); a producer warp streams these
 // 18 row segments into a STAGES-deep shared-memory ring with cp.async.bulk,
-// completion tracked by one mbarrier per stage.  The CTA then
-//   1. computes rho, T and psi of row y for columns -1..W (one site of halo on
+// completion tracked by one mbarrier per stage.  The consumer warps then
+//   1. compute rho, T and psi of row y for columns -1..W (one site of halo on
 //      each side) into a 4-row psi ring,
-//   2. collides row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
+//   2. collide row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
 //      rows are now complete, reading its populations back from the stage
 //      ring and storing the 18 post-collision values with coalesced stores.
 // psi is computed once per site (plus 2 columns per strip and 2 rows per
@@ -19,8 +19,12 @@
 // is fetched from the other end of the row with separate 16-byte copies, so
 // the kernel needs nx to be a multiple of HALO (checked on the host).
 //
+// A dedicated producer warp issues the copies; the consumer warps release a
+// stage through a second mbarrier when its last reader is done, so copy issue
+// never stalls the consumers' per-row synchronisation.
+//
 // Every mbarrier wait is bounded: on timeout the CTA records LB_ERR_TIMEOUT,
-// drains its own copies in flight (again bounded) and returns.
+// the producer waits (again bounded) for the copies it issued, and returns.
 #pragma once
 
 #include "lb_device.cuh"
@@ -122,11 +126,28 @@ template <int PREC, int BX, int STAGES>
 constexpr size_t strip_smem_bytes() {
     using C = StripCfg<PREC>;
     return (size_t)STAGES * 18 * (BX + 2 * C::HALO) * C::ES +
-           (size_t)8 * (BX + 2) * sizeof(typename C::real) + (size_t)STAGES * 8 + 16;
+           (size_t)8 * (BX + 2) * sizeof(typename C::real) + (size_t)2 * STAGES * 8 + 16;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// named barrier over the consumer warps only (the producer warp never joins)
+template <int NT>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+}
+
+// Block: BX consumer threads (BX/32 warps) plus one producer warp.
+//   producer: for every job (pre-collision row) waits until its stage is
+//     released, then lane 0 arms the stage's "full" mbarrier with the byte
+//     count and lanes 0..17 each issue the copies of one plane-row segment.
+//   consumers: wait "full", compute psi of the row into the psi ring, sync
+//     among themselves (named barrier), collide the row behind, then each
+//     warp releases the stage of the row behind on its "empty" mbarrier.
 template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
-__global__ void __launch_bounds__(BX, 2)
+__global__ void __launch_bounds__(BX + 32, 2)
     k_step_strip(const typename Store<PREC>::elem* __restrict__ src,
                  typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks) {
     using S = Store<PREC>;
@@ -137,13 +158,15 @@ __global__ void __launch_bounds__(BX, 2)
     constexpr int SEGW = BX + 2 * HALO;
     constexpr int RW = BX + 2;
     constexpr int ES = C::ES;
+    constexpr int NCW = BX / 32;  // consumer warps
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
     real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [4][RW]
     real* ring_psi2 = ring_psi + 4 * RW;                                            // [4][RW]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
+    uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
+    uint64_t* empty = full + STAGES;
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
@@ -156,47 +179,64 @@ __global__ void __launch_bounds__(BX, 2)
     const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
 
     if (t == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
         fence_mbar_init();
         s_abort = 0;
     }
     __syncthreads();
 
-    // thread 0: fill the stage of job j (pre-collision row y_start - 1 + j)
-    auto issue = [&](int j) {
-        const int s = j % STAGES;
-        int y = y_start - 1 + j;
-        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+    if (t >= BX) {
+        // ------------------------------------------------ producer warp
+        const int lane = t - BX;
         const bool left_wrap = x0 == 0;
         const bool right_wrap = x0 + W == nx;
-#pragma unroll 1
-        for (int i = 0; i < 18; ++i) {
-            const int d = i < 9 ? i : i - 9;
-            int sy = y - ey(d);
-            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-            const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
-            elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
-            if (!left_wrap && !right_wrap) {
-                bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &bars[s]);
-            } else {
-                bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &bars[s]);
-                bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &bars[s]);
-                bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &bars[s]);
+        int issued = 0;
+        for (int j = 0; j < njobs; ++j) {
+            const int s = j % STAGES;
+            if (j >= STAGES) {
+                // the stage's previous job (j - STAGES) must have been released;
+                // on timeout stop issuing (the consumers then time out on "full")
+                if (!mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                    if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
+                    break;
+                }
             }
+            int y = y_start - 1 + j;
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+            __syncwarp();
+            if (lane < 18) {
+                const int i = lane;
+                const int d = i < 9 ? i : i - 9;
+                int sy = y - ey(d);
+                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
+                elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
+                if (!left_wrap && !right_wrap) {
+                    bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &full[s]);
+                } else {
+                    bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &full[s]);
+                    bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &full[s]);
+                    bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &full[s]);
+                }
+            }
+            issued = j + 1;
         }
-    };
-
-    if (t == 0) {
-        const int pre = njobs < STAGES ? njobs : STAGES;
-        for (int j = 0; j < pre; ++j) issue(j);
+        // leave only when every copy this CTA issued has landed (bounded)
+        if (lane == 0)
+            for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
+                (void)mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+        return;
     }
 
+    // ---------------------------------------------------- consumer warps
     int flags = 0;
-    int last_issued = (njobs < STAGES ? njobs : STAGES) - 1;
     for (int j = 0; j < njobs; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait_bounded(&bars[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
         // 1. rho, T, psi of pre-collision row j for ring columns r = 0..W+1 (column r-1)
         {
             const elem* st = stage + (size_t)s * 18 * SEGW;
@@ -215,7 +255,7 @@ __global__ void __launch_bounds__(BX, 2)
                 if (BMODE != BETA_ONE) rq[r] = psi2;
             }
         }
-        __syncthreads();
+        consumer_sync<BX>();
         if (s_abort) break;
         // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
         if (j >= 2 && t < W) {
@@ -247,19 +287,14 @@ __global__ void __launch_bounds__(BX, 2)
                 S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
             }
         }
-        // 3. the stage of job j-2 is no longer read by anyone: refill it
-        if (t == 0 && j >= 2 && j - 2 + STAGES < njobs) {
-            fence_proxy_async_smem();
-            issue(j - 2 + STAGES);
-            last_issued = j - 2 + STAGES;
+        // 3. the stage of job j-1 has had its last reader (psi at j-1, collision at j)
+        if (j >= 1) {
+            __syncwarp();
+            if ((t & 31) == 0) mbar_arrive(&empty[(j - 1) % STAGES]);
         }
     }
     if (s_abort) {
-        // a copy never completed: record it, drain what this CTA issued, leave
-        if (t == 0) {
-            atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
-            for (int j = 0; j <= last_issued; ++j) (void)mbar_wait_bounded(&bars[j % STAGES], (uint32_t)((j / STAGES) & 1));
-        }
+        if (t == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
         return;
     }
     if (flags) atomicOr(kp.err, flags);

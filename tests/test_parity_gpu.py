@@ -386,7 +386,7 @@ def test_16bit_one_step_within_rounding_bound(lb, prec, u):
 
 
 @pytest.mark.parametrize("prec,drift_max,frac_tol", [("fp32", 1e-6, 0.01), ("fp16", 1e-3, 0.03),
-                                                    ("bf16", 1e-2, 0.10)])
+                                                    ("bf16", 5e-2, 0.10)])
 def test_spinodal_statistics_against_fp64(lb, prec, drift_max, frac_tol):
     """Spinodal decomposition amplifies any perturbation exponentially, so after a few
     hundred steps reduced-precision runs differ from FP64 site by site by design.  They
