@@ -259,21 +259,40 @@ __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9],
         const real uy = (my + (real)0.5 * Fy) * inv_rho;
         const real T = e / (rho * (real)kp.cv);
         const real cvT = (real)kp.cv * T;
-        const real usq15 = (real)1.5 * (ux * ux + uy * uy);
-        const real uF = ux * Fx + uy * Fy;
         const real om_f = (real)kp.omega_f, om_g = (real)kp.omega_g;
         const real guo = (real)kp.guo_pre, corr = (real)kp.corr_pre;
+        const real base = (real)1 - (real)1.5 * (ux * ux + uy * uy);
+        const real uF3 = (real)3 * (ux * Fx + uy * Fy);
+        // Opposite directions i and i' = opposite(i) share the even parts of
+        // f^eq and F_i; the odd parts change sign:
+        //   f^eq = rho w (1 - 1.5 u^2 + 4.5 (e.u)^2) +- 3 rho w (e.u)
+        //   F_i  = guo w (9 (e.u)(e.F) - 3 u.F)      +- 3 guo w (e.F)
+        //   C_i  =                                     +- 3 corr w c_v T (e.F)
+        // pairs (1,3), (2,4), (5,7), (8,6): e(i) = (dx, dy), e(i') = -(dx, dy)
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
+        for (int p = 0; p < 4; ++p) {
+            const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
+            const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
             const real w = (real)wd(i);
             const real eu = (real)ex(i) * ux + (real)ey(i) * uy;
             const real eF = (real)ex(i) * Fx + (real)ey(i) * Fy;
-            const real feq = rho * w * ((real)1 + (real)3 * eu + (real)4.5 * eu * eu - usq15);
-            const real Fi = guo * w * ((real)3 * (eF - uF) + (real)9 * eu * eF);
-            f[i] = f[i] - om_f * (f[i] - feq) + Fi;
-            real gs = g[i] - om_g * (g[i] - cvT * feq);
-            if (EQ24) gs += corr * w * cvT * (real)3 * eF;
-            g[i] = gs;
+            const real rw = rho * w;
+            const real feq_even = rw * (base + (real)4.5 * eu * eu);
+            const real feq_odd = (real)3 * rw * eu;
+            const real F_even = guo * w * ((real)9 * eu * eF - uF3);
+            const real F_odd = (real)3 * guo * w * eF;
+            const real feq_i = feq_even + feq_odd, feq_k = feq_even - feq_odd;
+            f[i] = f[i] + om_f * (feq_i - f[i]) + (F_even + F_odd);
+            f[k] = f[k] + om_f * (feq_k - f[k]) + (F_even - F_odd);
+            real gi = g[i] + om_g * (cvT * feq_i - g[i]);
+            real gk = g[k] + om_g * (cvT * feq_k - g[k]);
+            if (EQ24) {
+                const real C_odd = (real)3 * corr * w * cvT * eF;
+                gi += C_odd;
+                gk -= C_odd;
+            }
+            g[i] = gi;
+            g[k] = gk;
         }
         // The collision conserves mass and energy exactly: sum f^eq = rho,
         // sum F_i = 0, sum g^eq = rho c_v T = sum g, sum C_i = 0.  In FP32 the
