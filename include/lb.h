@@ -170,6 +170,34 @@ lb_status lb_get_params(const lb_ctx* ctx, lb_params* out);
 /* Release the context and its device memory.  NULL is accepted. */
 lb_status lb_free(lb_ctx* ctx);
 
+/* Allocation-free FP64 totals of caller-owned device fields.
+ *
+ * The paper has no counterpart: this is a service for callers that must not
+ * have device memory allocated on their behalf -- code running while a stream
+ * is captured in a mode that forbids allocation, applications that give all
+ * device memory to their own pool, or embedders that fix their memory budget
+ * before the run.  lb_totals needs a context, whose buffers lb_init allocates;
+ * this entry point allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ * library call).  Its scratch is one static device array of 4096 x 8 doubles
+ * (256 KB), held by every GPU that loads the library until the process exits.
+ *
+ * Inputs: d_rho, d_ux, d_uy, d_T -- device float64 [ny][nx] fields (as written
+ * by lb_moments_device); d_ref_rho, d_ref_T -- optional device reference fields
+ * taken K steps earlier (both NULL: residual 0).  cv: the c_v of the run.
+ * Output: d_out -- device float64[LB_TOTALS_N]: sum rho, sum rho c_v T,
+ * sum rho u_x, sum rho u_y, residual (same definitions as lb_totals), reduced
+ * in a fixed order.  Asynchronous on `stream` (NULL: the default stream).
+ *
+ * Limits and errors: nx*ny <= 16,777,216 sites (4096^2), else LB_ERR_ARG with
+ * a message.  The first call on a device looks up the scratch address (make it
+ * before any stream capture).  Every call shares the scratch; each call writes
+ * all entries it reads, so nothing needs clearing, but calls that overlap on the
+ * GPU race on it. */
+lb_status lb_field_totals_noalloc(int32_t nx, int32_t ny, double cv, const double* d_rho,
+                                  const double* d_ux, const double* d_uy, const double* d_T,
+                                  const double* d_ref_rho, const double* d_ref_T, int64_t K,
+                                  double* d_out, void* stream);
+
 /* Thread-local description of the last error ("" if none). */
 const char* lb_last_error(void);
 

@@ -79,6 +79,9 @@ lb_status validate(const lb_params* p) {
 }  // namespace
 
 namespace lbgb {
+// Lets other translation units of the library report through lb_last_error().
+lb_status record_error(lb_status st, const char* msg) { return fail(st, "%s", msg); }
+
 bool step_tile_supported(int bx, int by) {
     return (bx == 32 && by == 8) || (bx == 32 && by == 16) || (bx == 64 && by == 4) ||
            (by == 0 && (bx == 128 || bx == 256));

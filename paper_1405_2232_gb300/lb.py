@@ -61,7 +61,7 @@ EXPORTED = [
     "lb_params_default", "lb_init", "lb_init_device", "lb_step", "lb_synchronize",
     "lb_moments", "lb_moments_device", "lb_get_populations", "lb_set_populations",
     "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
-    "lb_get_params", "lb_free", "lb_last_error", "lb_version",
+    "lb_get_params", "lb_free", "lb_last_error", "lb_version", "lb_field_totals_noalloc",
 ]
 
 
@@ -102,6 +102,8 @@ def load(path: str | None = None):
         "lb_free": (st, [vp]),
         "lb_last_error": (ctypes.c_char_p, []),
         "lb_version": (ctypes.c_char_p, []),
+        "lb_field_totals_noalloc": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp,
+                                         vp, vp, vp, vp, ctypes.c_int64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -244,6 +246,15 @@ def lb_time(ctx) -> int:
 def lb_free(ctx):
     if ctx is not None:
         _check(load().lb_free(ctx))
+
+
+def lb_field_totals_noalloc(nx, ny, cv, d_rho, d_ux, d_uy, d_T, d_out, d_ref_rho=None,
+                            d_ref_T=None, K=0, stream=None):
+    """Totals of device fields without any device allocation (see include/lb.h);
+    d_out receives [mass, energy, px, py, residual] on the device."""
+    _check(load().lb_field_totals_noalloc(int(nx), int(ny), float(cv), _addr(d_rho), _addr(d_ux),
+                                          _addr(d_uy), _addr(d_T), _addr(d_ref_rho),
+                                          _addr(d_ref_T), int(K), _addr(d_out), _stream(stream)))
 
 
 def lb_last_error() -> str:
