@@ -127,8 +127,7 @@ struct lb_ctx {
     bool have_ref = false;
     int64_t ref_time = 0;
     int64_t t = 0;
-    int nchunks = 1;            // strip kernel: row chunks per full-width strip
-    int nchunks_last = 1;       // strip kernel: row chunks of a narrower last strip
+    int nchunks = 1;            // strip kernel: row chunks per strip
 };
 
 namespace {
@@ -177,7 +176,6 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.bx = c->p.tile_x;
     L.by = c->p.tile_y;
     L.nchunks = c->nchunks;
-    L.nchunks_last = c->nchunks_last;
     L.stream = c->stream;
     switch (c->p.precision) {
         case LB_PREC_FP64: return launch_step_fp64(L);
@@ -327,22 +325,16 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         }
     }
     if (c->p.tile_y == 0) {
-        // One wave of about two resident CTAs per SM.  A CTA's time per row is
-        // set by its warps' latency chain more than by the strip's width, so
-        // every strip (a narrower last one too) gets the same number of row
-        // chunks; take the most chunks that still fit the wave (chunks of at
-        // least 8 rows).
+        // one wave of two resident CTAs per SM: strips x chunks <= 2 x SMs
+        // (chunks of at least 8 rows)
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0)
             sms = 152;
-        const int slots = 2 * sms;
-        const int cols = (c->p.tile_x / 32) * 30;  // interior columns of a strip
-        const int strips = (p->nx + cols - 1) / cols;
+        const int strips = (p->nx + c->p.tile_x - 1) / c->p.tile_x;
         const int max_ch = p->ny / 8 > 0 ? p->ny / 8 : 1;
-        int nch = slots / strips;
+        int nch = (2 * sms) / strips;
         nch = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
         c->nchunks = nch;
-        c->nchunks_last = nch;
     }
     *out = c;
     return LB_OK;

@@ -15,8 +15,7 @@ struct StepLaunch {
     int eq24;       // 0: Eq. (7), 1: Eq. (24)
     int bmode;      // BetaMode
     int bx, by;     // CTA tile; by == 0: strip kernel of width bx
-    int nchunks;    // strip kernel: row chunks of each full-width strip
-    int nchunks_last;  // strip kernel: row chunks of a narrower last strip
+    int nchunks;    // strip kernel: row chunks per strip
     cudaStream_t stream;
 };
 

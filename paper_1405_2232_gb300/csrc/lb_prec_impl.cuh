@@ -41,25 +41,24 @@ cudaError_t step_tile(const StepLaunch& L) {
 // translation unit gets its own copy (shared weak symbols would let the linker
 // pick one precision's launcher for all).
 
-// Stage count per strip: the deepest ring that still lets two CTAs share an
-// SM (228 KB of shared memory).
-template <int NW>
+// Stage count per strip width: the deepest ring that still lets two CTAs
+// share an SM (228 KB of shared memory).
+template <int BX>
 constexpr int strip_stages() {
-    constexpr size_t stage =
-        (size_t)18 * (NW * WARP_COLS + 2 * StripCfg<LBGB_PREC>::HALO) * StripCfg<LBGB_PREC>::ES;
-    constexpr size_t ring = (size_t)NW * 8 * 32 * sizeof(typename StripCfg<LBGB_PREC>::real);
+    constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<LBGB_PREC>::HALO) * StripCfg<LBGB_PREC>::ES;
+    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<LBGB_PREC>::real);
     constexpr size_t budget = 110 * 1024 - 32;
     constexpr size_t s = (budget - ring) / stage;
     return s > 12 ? 12 : (int)s;
 }
 
-template <int NW, bool EQ24, int BM>
+template <int BX, bool EQ24, int BM>
 cudaError_t strip_launch(const StepLaunch& L) {
     using E = typename Store<LBGB_PREC>::elem;
-    constexpr int ST = strip_stages<NW>();
+    constexpr int ST = strip_stages<BX>();
     static_assert(ST >= 3, "strip kernel needs at least three stages");
-    constexpr size_t smem = strip_smem_bytes<LBGB_PREC, NW, ST>();
-    auto kern = k_step_strip<LBGB_PREC, NW, ST, EQ24, BM>;
+    constexpr size_t smem = strip_smem_bytes<LBGB_PREC, BX, ST>();
+    auto kern = k_step_strip<LBGB_PREC, BX, ST, EQ24, BM>;
     static unsigned long long configured = 0;  // per instantiation, one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -69,30 +68,25 @@ cudaError_t strip_launch(const StepLaunch& L) {
         if (e != cudaSuccess) return e;
         if (dev < 64) configured |= 1ULL << dev;
     }
-    constexpr int BXI = NW * WARP_COLS;
-    const int full = L.kp.nx / BXI;
-    const bool partial = L.kp.nx % BXI != 0;
-    const int grid = full * L.nchunks + (partial ? L.nchunks_last : 0);
-    kern<<<grid, NW * 32 + 32, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
-                                                 L.kp, L.nchunks, L.nchunks_last);
+    const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
+    kern<<<grid, BX + 32, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
+                                            L.kp, L.nchunks);
     return cudaGetLastError();
 }
 
-// (the strip "width" bx of the API is the consumer threads: bx/32 warps of
-// 30 interior columns each)
-template <int NW>
+template <int BX>
 cudaError_t step_strip(const StepLaunch& L) {
     if (L.eq24) {
         switch (L.bmode) {
-            case BETA_ZERO: return strip_launch<NW, true, BETA_ZERO>(L);
-            case BETA_ONE: return strip_launch<NW, true, BETA_ONE>(L);
-            default: return strip_launch<NW, true, BETA_MIXED>(L);
+            case BETA_ZERO: return strip_launch<BX, true, BETA_ZERO>(L);
+            case BETA_ONE: return strip_launch<BX, true, BETA_ONE>(L);
+            default: return strip_launch<BX, true, BETA_MIXED>(L);
         }
     }
     switch (L.bmode) {
-        case BETA_ZERO: return strip_launch<NW, false, BETA_ZERO>(L);
-        case BETA_ONE: return strip_launch<NW, false, BETA_ONE>(L);
-        default: return strip_launch<NW, false, BETA_MIXED>(L);
+        case BETA_ZERO: return strip_launch<BX, false, BETA_ZERO>(L);
+        case BETA_ONE: return strip_launch<BX, false, BETA_ONE>(L);
+        default: return strip_launch<BX, false, BETA_MIXED>(L);
     }
 }
 
@@ -100,10 +94,10 @@ cudaError_t step_strip(const StepLaunch& L) {
 
 cudaError_t LBGB_CAT(launch_step_, LBGB_NAME)(const StepLaunch& L) {
     if (L.by == 0) {
-        if (L.bx == 128) return step_strip<4>(L);
+        if (L.bx == 128) return step_strip<128>(L);
         // (LB_PREC_* are enum constants, invisible to the preprocessor)
         if constexpr (LBGB_PREC != LB_PREC_FP64) {
-            if (L.bx == 256) return step_strip<8>(L);
+            if (L.bx == 256) return step_strip<256>(L);
         }
         return cudaErrorInvalidValue;
     }

@@ -1,27 +1,27 @@
 // lb_step_strip.cuh -- the fused step as a strip-marching kernel fed by TMA
 // bulk copies (sm_90+ cp.async.bulk, mbarrier transaction counts).
 //
-// Each CTA owns a strip of columns and a chunk of rows and marches up the
+// Each CTA owns a strip of BX columns and a chunk of rows and marches up the
 // rows.  For every pre-collision row y it needs plane i of source row
 // y - e_iy, columns [x0 - HALO, x0 + W + HALO) (HALO * sizeof(elem) = 16
 // bytes, so every copy is 16-byte aligned); a producer warp streams these
 // 18 row segments into a STAGES-deep shared-memory ring with cp.async.bulk,
-// completion tracked by one mbarrier per stage.  Each consumer warp then
-//   1. computes rho, T and psi of row y for its 30 columns plus one halo
-//      column each side into its own 4-row psi ring,
-//   2. collides row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
+// completion tracked by one mbarrier per stage.  The consumer warps then
+//   1. compute rho, T and psi of row y for columns -1..W (one site of halo on
+//      each side) into a 4-row psi ring,
+//   2. collide row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
 //      rows are now complete, reading its populations back from the stage
 //      ring and storing the 18 post-collision values with coalesced stores.
-// psi is computed for 32 columns per 30 sites (plus 2 rows per chunk), and
-// every population is read from HBM once and written once.
+// psi is computed once per site (plus 2 columns per strip and 2 rows per
+// chunk), and every population is read from HBM once and written once.
 //
 // Periodic wrap: rows wrap by index; the column halo of the first/last strip
 // is fetched from the other end of the row with separate 16-byte copies, so
 // the kernel needs nx to be a multiple of HALO (checked on the host).
 //
 // A dedicated producer warp issues the copies; the consumer warps release a
-// stage through a second mbarrier when its last reader is done.  Nothing
-// synchronises the whole CTA after set-up.
+// stage through a second mbarrier when its last reader is done, so copy issue
+// never stalls the consumers' per-row synchronisation.
 //
 // Every mbarrier wait is bounded: on timeout the CTA records LB_ERR_TIMEOUT,
 // the producer waits (again bounded) for the copies it issued, and returns.
@@ -122,86 +122,75 @@ struct StripCfg {
     static constexpr int HALO = 16 / ES;  // 16-byte halo: 2 (FP64), 4 (FP32), 8 (16-bit)
 };
 
-// Columns a consumer warp owns: 30 interior sites, plus one halo column on
-// each side for its own psi, so a warp never needs another warp's psi.
-constexpr int WARP_COLS = 30;
-
-template <int PREC, int NW, int STAGES>
+template <int PREC, int BX, int STAGES>
 constexpr size_t strip_smem_bytes() {
     using C = StripCfg<PREC>;
-    return (size_t)STAGES * 18 * (NW * WARP_COLS + 2 * C::HALO) * C::ES +
-           (size_t)NW * 8 * 32 * sizeof(typename C::real) + (size_t)2 * STAGES * 8 + 16;
+    return (size_t)STAGES * 18 * (BX + 2 * C::HALO) * C::ES +
+           (size_t)8 * (BX + 2) * sizeof(typename C::real) + (size_t)2 * STAGES * 8 + 16;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Block: NW consumer warps plus one producer warp.  The strip is NW * 30
-// columns wide.
+// named barrier over the consumer warps only (the producer warp never joins)
+template <int NT>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+}
+
+// Block: BX consumer threads (BX/32 warps) plus one producer warp.
 //   producer: for every job (pre-collision row) waits until its stage is
 //     released, then lane 0 arms the stage's "full" mbarrier with the byte
 //     count and lanes 0..17 each issue the copies of one plane-row segment.
-//   consumer warp w (interior columns 30w .. 30w+29 of the strip): waits
-//     "full", lane l computes psi of column 30w + l - 1 into the warp's own
-//     4-row psi ring, __syncwarp, lanes 1..30 collide the row behind, then
-//     the warp releases that row's stage on its "empty" mbarrier.  There is
-//     no block-wide barrier: warps drift freely within the stage ring.
-template <int PREC, int NW, int STAGES, bool EQ24, int BMODE>
-__global__ void __launch_bounds__(NW * 32 + 32, 2)
+//   consumers: wait "full", compute psi of the row into the psi ring, sync
+//     among themselves (named barrier), collide the row behind, then each
+//     warp releases the stage of the row behind on its "empty" mbarrier.
+template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
+__global__ void __launch_bounds__(BX + 32, 2)
     k_step_strip(const typename Store<PREC>::elem* __restrict__ src,
-                 typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nch_full,
-                 int nch_last) {
+                 typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks) {
     using S = Store<PREC>;
     using C = StripCfg<PREC>;
     using elem = typename C::elem;
     using real = typename C::real;
     constexpr int HALO = C::HALO;
-    constexpr int BXI = NW * WARP_COLS;  // interior columns of a strip
-    constexpr int SEGW = BXI + 2 * HALO;
+    constexpr int SEGW = BX + 2 * HALO;
+    constexpr int RW = BX + 2;
     constexpr int ES = C::ES;
+    constexpr int NCW = BX / 32;  // consumer warps
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
-    real* rings = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [NW][2][4][32]
+    real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [4][RW]
+    real* ring_psi2 = ring_psi + 4 * RW;                                            // [4][RW]
     uint64_t* full = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(rings + NW * 8 * 32) + 7) & ~uintptr_t(7));
+        (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
     uint64_t* empty = full + STAGES;
+    __shared__ int s_abort;
 
     const int t = threadIdx.x;
     const int nx = kp.nx, ny = kp.ny;
-    // 1-D grid: the full-width strips get nch_full row chunks each, a narrower
-    // last strip gets nch_last, so every CTA carries about the same work
-    const int full_strips = nx / BXI;
-    int strip, chunk, nchunks;
-    if ((int)blockIdx.x < full_strips * nch_full) {
-        strip = blockIdx.x / nch_full;
-        chunk = blockIdx.x - strip * nch_full;
-        nchunks = nch_full;
-    } else {
-        strip = full_strips;
-        chunk = blockIdx.x - full_strips * nch_full;
-        nchunks = nch_last;
-    }
-    const int x0 = strip * BXI;
-    const int W = min(BXI, nx - x0);
-    const int y_start = (int)((long long)chunk * ny / nchunks);
-    const int y_end = (int)((long long)(chunk + 1) * ny / nchunks);
+    const int x0 = blockIdx.x * BX;
+    const int W = min(BX, nx - x0);
+    const int y_start = (int)((long long)blockIdx.y * ny / nchunks);
+    const int y_end = (int)((long long)(blockIdx.y + 1) * ny / nchunks);
     const int njobs = (y_end - y_start) + 2;  // pre-collision rows y_start-1 .. y_end
     const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
 
     if (t == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW);
+            mbar_init(&empty[s], NCW);
         }
         fence_mbar_init();
+        s_abort = 0;
     }
     __syncthreads();
 
-    if (t >= NW * 32) {
+    if (t >= BX) {
         // ------------------------------------------------ producer warp
-        const int lane = t - NW * 32;
+        const int lane = t - BX;
         const bool left_wrap = x0 == 0;
         const bool right_wrap = x0 + W == nx;
         int issued = 0;
@@ -244,40 +233,35 @@ __global__ void __launch_bounds__(NW * 32 + 32, 2)
     }
 
     // ---------------------------------------------------- consumer warps
-    const int warp = t >> 5, lane = t & 31;
-    const int col = warp * WARP_COLS + lane - 1;    // strip column of this lane's psi site
-    const bool has_psi = col <= W;                  // columns -1 .. W are needed
-    const bool collides = lane >= 1 && lane <= WARP_COLS && col < W;
-    real* rp = rings + (size_t)warp * 8 * 32;        // [4][32] psi
-    real* rq = rp + 4 * 32;                          // [4][32] psi^2
     int flags = 0;
-    bool abort = false;
     for (int j = 0; j < njobs; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) {
-            abort = true;
-            break;
-        }
-        // 1. rho, T, psi of pre-collision row j at this lane's column
-        if (has_psi) {
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
+        // 1. rho, T, psi of pre-collision row j for ring columns r = 0..W+1 (column r-1)
+        {
             const elem* st = stage + (size_t)s * 18 * SEGW;
-            const int c = col + HALO;  // smem column of the site
-            real f[9], g[9], rho, T, psi, psi2;
+            real* rp = ring_psi + (j & 3) * RW;
+            real* rq = ring_psi2 + (j & 3) * RW;
+            for (int r = t; r < W + 2; r += BX) {
+                const int c = r - 1 + HALO;  // smem column of the site
+                real f[9], g[9], rho, T, psi, psi2;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
-                g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                for (int i = 0; i < 9; ++i) {
+                    f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
+                    g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                }
+                site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+                if (BMODE != BETA_ZERO) rp[r] = psi;
+                if (BMODE != BETA_ONE) rq[r] = psi2;
             }
-            site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
-            if (BMODE != BETA_ZERO) rp[(j & 3) * 32 + lane] = psi;
-            if (BMODE != BETA_ONE) rq[(j & 3) * 32 + lane] = psi2;
         }
-        __syncwarp();
+        consumer_sync<BX>();
+        if (s_abort) break;
         // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
-        if (j >= 2 && collides) {
+        if (j >= 2 && t < W) {
             const int sp = (j - 1) % STAGES;
             const elem* st = stage + (size_t)sp * 18 * SEGW;
-            const int c = col + HALO;
+            const int c = t + HALO;
             real f[9], g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -287,27 +271,30 @@ __global__ void __launch_bounds__(NW * 32 + 32, 2)
             real rho = f[0];
 #pragma unroll
             for (int i = 1; i < 9; ++i) rho += f[i];
+            const int r = t + 1;
             real Fx, Fy, ux, uy, T;
             force_from_rows<real, BMODE>(
-                kp, rp + ((j - 2) & 3) * 32 + lane, rp + ((j - 1) & 3) * 32 + lane,
-                rp + (j & 3) * 32 + lane, rq + ((j - 2) & 3) * 32 + lane,
-                rq + ((j - 1) & 3) * 32 + lane, rq + (j & 3) * 32 + lane, Fx, Fy);
+                kp, ring_psi + ((j - 2) & 3) * RW + r, ring_psi + ((j - 1) & 3) * RW + r,
+                ring_psi + (j & 3) * RW + r, ring_psi2 + ((j - 2) & 3) * RW + r,
+                ring_psi2 + ((j - 1) & 3) * RW + r, ring_psi2 + (j & 3) * RW + r, Fx, Fy);
             collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
             int y = y_start + j - 2;
             y = y >= ny ? y - ny : y;
-            const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + col);
+            const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + t);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
                 S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
             }
         }
-        // 3. the stage of job j-1 has had its last reader in this warp
-        __syncwarp();
-        if (j >= 1 && lane == 0) mbar_arrive(&empty[(j - 1) % STAGES]);
+        // 3. the stage of job j-1 has had its last reader (psi at j-1, collision at j)
+        if (j >= 1) {
+            __syncwarp();
+            if ((t & 31) == 0) mbar_arrive(&empty[(j - 1) % STAGES]);
+        }
     }
-    if (abort) {
-        if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
+    if (s_abort) {
+        if (t == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
         return;
     }
     if (flags) atomicOr(kp.err, flags);

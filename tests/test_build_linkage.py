@@ -35,12 +35,11 @@ def test_no_symbol_shared_between_precision_objects():
 
 
 def test_every_strip_kernel_width_is_compiled():
-    """The strip kernel exists with 4 consumer warps (API width 128) for every
-    precision and with 8 (width 256) for the FP32 and 16-bit modes (the launcher
-    returns cudaErrorInvalidValue otherwise)."""
+    """The strip kernel exists at width 128 for every precision and at 256 for the
+    FP32 and 16-bit modes (the launcher returns cudaErrorInvalidValue otherwise)."""
     from paper_1405_2232_gb300 import build
     build.build()
-    want = {"fp64": ["4"], "fp32": ["4", "8"], "fp16": ["4", "8"], "bf16": ["4", "8"]}
+    want = {"fp64": ["128"], "fp32": ["128", "256"], "fp16": ["128", "256"], "bf16": ["128", "256"]}
     prec_id = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
     for name, widths in want.items():
         out = subprocess.run(["nm", "--defined-only", os.path.join(BUILD, f"lb_prec_{name}.o")],
