@@ -70,22 +70,28 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for fn in ("lb_device.cuh", "lb_prec_impl.cuh", "lb_prec_fp32.cu"):
+    for fn in ("lb_device.cuh", "lb_step_strip.cuh", "lb_prec_impl.cuh", "lb_prec_fp32.cu"):
         with open(os.path.join(ROOT, "paper_1405_2232_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (profiles/step_traffic.txt), or None when the kernel sources changed since
+    it was captured."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.txt")
     try:
+        kv = {}
         with open(path) as fh:
-            d = json.load(fh)
-        if d.get("kernel_hash") != kernel_source_hash():
+            for line in fh:
+                if line.startswith("#") or ":" not in line:
+                    continue
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_hash") != kernel_source_hash():
             return None
-        return float(d["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_launch"])
     except Exception:
         return None
 
