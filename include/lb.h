@@ -50,7 +50,8 @@ typedef enum lb_status {
     LB_ERR_NONFINITE = 4,   /* rho or T became NaN/Inf during a step            */
     LB_ERR_PSI_DOMAIN = 5,  /* 2 (p_EOS - rho cs^2)/G < 0 with beta != 0        */
     LB_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                    */
-    LB_ERR_UNSUPPORTED = 7  /* option not built or not available                */
+    LB_ERR_UNSUPPORTED = 7, /* option not built or not available                */
+    LB_ERR_NOT_CONVERGED = 8 /* batch domain did not reach the tolerance        */
 } lb_status;
 
 /* Equation of state p_EOS(rho, T) used by the pseudopotential (Sec. II A). */
@@ -169,6 +170,52 @@ lb_status lb_get_params(const lb_ctx* ctx, lb_params* out);
 
 /* Release the context and its device memory.  NULL is accepted. */
 lb_status lb_free(lb_ctx* ctx);
+
+/* ------------------------------------------------------------------ batch
+ * Many independent periodic domains (a parameter sweep) advanced together by
+ * one persistent fused-step kernel over a device work list of (domain, strip,
+ * row chunk) items.  All domains share the storage precision (FP32 or FP64),
+ * the temperature treatment and the force form (beta == 0, beta == 1 or
+ * mixed); size, tau_f, tau_g, G, beta, EOS and its constants and c_v are per
+ * domain.  nx must be a multiple of 4 (FP32) or 2 (FP64). */
+typedef struct lb_batch lb_batch; /* opaque; owned by the library */
+
+/* Create a batch of n domains; params[d] describes domain d, rho0[d] and T0[d]
+ * are its host float64 fields [ny][nx] (copied).  Initial state as lb_init. */
+lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const* rho0,
+                        const double* const* T0, void* stream, lb_batch** out);
+
+/* Advance every active domain n steps (asynchronous). */
+lb_status lb_batch_step(lb_batch* b, int64_t n);
+
+/* Per-domain FP64 check of the active domains (deterministic reduction):
+ * residual[d] = max over phi in {rho, T} of ||phi_t - phi_s||_2 / ((t - s) ||phi_t||_2)
+ * with s the time of the previous check (0 on the first), mass[d] = sum f,
+ * energy[d] = sum g, status[d] = the domain's sticky device error (LB_OK,
+ * LB_ERR_PSI_DOMAIN, LB_ERR_NONFINITE, ...).  Any output may be NULL; retired
+ * domains report 0.  The check becomes the new reference.  Synchronises. */
+lb_status lb_batch_check(lb_batch* b, double* residual, double* mass, double* energy,
+                         int32_t* status);
+
+/* Run to steady state: replay a CUDA graph of K fused steps (K even) plus a
+ * check until every domain has residual < tol, has failed, or max_steps have
+ * passed.  A domain that converges or fails is taken off the work list (its
+ * state is kept).  steps_out[d]: steps the domain took; residual_out[d]: its
+ * last residual; status_out[d]: LB_OK (converged), LB_ERR_PSI_DOMAIN /
+ * LB_ERR_NONFINITE (failed) or LB_ERR_NOT_CONVERGED.  Any output may be NULL.
+ * Synchronises. */
+lb_status lb_batch_run(lb_batch* b, double tol, int64_t K, int64_t max_steps, int64_t* steps_out,
+                       double* residual_out, int32_t* status_out);
+
+/* Host float64 rho and T [ny][nx] of domain d (either may be NULL).  For an
+ * active domain this runs a check (the new residual reference).  Synchronises. */
+lb_status lb_batch_fields(lb_batch* b, int32_t d, double* rho, double* T);
+
+/* Steps the batch has taken since lb_batch_init. */
+int64_t lb_batch_time(const lb_batch* b);
+
+/* Release the batch.  NULL is accepted. */
+lb_status lb_batch_free(lb_batch* b);
 
 /* Allocation-free FP64 totals of caller-owned device fields.
  *

@@ -35,7 +35,7 @@ def nvcc() -> str:
 
 # per-source extra flags: the FP64 parity mode evaluates every formula without
 # contraction so its rounding is that of the printed expressions
-EXTRA_FLAGS = {"lb_prec_fp64.cu": ["--fmad=false"]}
+EXTRA_FLAGS = {"lb_prec_fp64.cu": ["--fmad=false"], "lb_batch_fp64.cu": ["--fmad=false"]}
 
 
 def _sources():

@@ -1,0 +1,288 @@
+// lb_batch_device.cuh -- device code of the batched solver: many independent
+// periodic domains of different sizes and parameters advanced together.
+//
+// The fused step is the strip-marching kernel of lb_step_strip.cuh made
+// persistent: a fixed grid of CTAs walks a device-side list of work items
+// (domain, strip, row chunk).  The producer warp and the consumer warps keep
+// one job counter across items, so the producer streams the next item's rows
+// while the consumers still work on the current one.  The list length is read
+// from device memory at launch, so a captured CUDA graph stays valid while
+// converged domains are taken off the list.
+#pragma once
+
+#include "lb_step_strip.cuh"
+
+namespace lbgb {
+
+// One domain of a batch.
+struct BatchDomain {
+    KParams kp;          // physics, sizes, pitch/plane (elements) and error word
+    long long off;       // element offset of the domain's 18 planes in each buffer
+    long long fld_off;   // site offset of the domain in the dense field arrays
+};
+
+// One work item of the persistent step kernel.
+struct BatchItem {
+    int domain;
+    int strip;    // column strip (width BX)
+    int y0, y1;   // rows [y0, y1) collided by this item
+};
+
+// Stage count of the batched step: the deepest ring that lets two CTAs share an SM.
+template <int PREC, int BX>
+constexpr int batch_stages() {
+    constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<PREC>::HALO) * StripCfg<PREC>::ES;
+    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<PREC>::real);
+    constexpr size_t s = (110 * 1024 - 32 - ring) / stage;
+    return s > 12 ? 12 : (int)s;
+}
+
+template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
+__global__ void __launch_bounds__(BX + 32, 2)
+    k_batch_step(const typename Store<PREC>::elem* __restrict__ src_base,
+                 typename Store<PREC>::elem* __restrict__ dst_base,
+                 const BatchDomain* __restrict__ doms, const BatchItem* __restrict__ items,
+                 const int* __restrict__ n_items_ptr) {
+    using S = Store<PREC>;
+    using C = StripCfg<PREC>;
+    using elem = typename C::elem;
+    using real = typename C::real;
+    constexpr int HALO = C::HALO;
+    constexpr int SEGW = BX + 2 * HALO;
+    constexpr int RW = BX + 2;
+    constexpr int ES = C::ES;
+    constexpr int NCW = BX / 32;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
+    real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [4][RW]
+    real* ring_psi2 = ring_psi + 4 * RW;                                            // [4][RW]
+    uint64_t* full = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
+    uint64_t* empty = full + STAGES;
+    __shared__ int s_abort;
+
+    const int t = threadIdx.x;
+    const int n_items = *n_items_ptr;
+    if (t == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (t >= BX) {
+        // ------------------------------------------------ producer warp
+        const int lane = t - BX;
+        long long jg = 0;  // job counter across this CTA's items
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const BatchItem item = items[it];
+            const BatchDomain& D = doms[item.domain];
+            const int nx = D.kp.nx, ny = D.kp.ny;
+            const uint32_t plane = (uint32_t)D.kp.plane, pitch = (uint32_t)D.kp.pitch;
+            const int x0 = item.strip * BX;
+            const int W = min(BX, nx - x0);
+            const int njobs = item.y1 - item.y0 + 2;
+            const elem* src = src_base + D.off;
+            const bool left_wrap = x0 == 0, right_wrap = x0 + W == nx;
+            for (int j = 0; j < njobs; ++j, ++jg) {
+                const int s = (int)(jg % STAGES);
+                if (jg >= STAGES) {
+                    if (!mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1))) {
+                        if (lane == 0) atomicOr(D.kp.err, 1 << LB_ERR_TIMEOUT);
+                        return;  // consumers then time out on "full" and leave
+                    }
+                }
+                int y = item.y0 - 1 + j;
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+                __syncwarp();
+                if (lane < 18) {
+                    const int i = lane;
+                    const int d = i < 9 ? i : i - 9;
+                    int sy = y - ey(d);
+                    sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                    const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
+                    elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
+                    if (!left_wrap && !right_wrap) {
+                        bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &full[s]);
+                    } else {
+                        bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &full[s]);
+                        bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &full[s]);
+                        bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &full[s]);
+                    }
+                }
+            }
+        }
+        // leave only when every copy this CTA issued has landed (bounded)
+        if (lane == 0)
+            for (long long j = (jg > STAGES ? jg - STAGES : 0); j < jg; ++j)
+                (void)mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+        return;
+    }
+
+    // ---------------------------------------------------- consumer warps
+    long long jg = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const BatchDomain& D = doms[item.domain];
+        const KParams kp = D.kp;
+        const int nx = kp.nx, ny = kp.ny;
+        const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
+        const int x0 = item.strip * BX;
+        const int W = min(BX, nx - x0);
+        const int njobs = item.y1 - item.y0 + 2;
+        elem* dst = dst_base + D.off;
+        int flags = 0;
+        for (int j = 0; j < njobs; ++j, ++jg) {
+            const int s = (int)(jg % STAGES);
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort = 1;
+            {
+                const elem* st = stage + (size_t)s * 18 * SEGW;
+                real* rp = ring_psi + (int)(jg & 3) * RW;
+                real* rq = ring_psi2 + (int)(jg & 3) * RW;
+                for (int r = t; r < W + 2; r += BX) {
+                    const int c = r - 1 + HALO;
+                    real f[9], g[9], rho, T, psi, psi2;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
+                        g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                    }
+                    site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+                    if (BMODE != BETA_ZERO) rp[r] = psi;
+                    if (BMODE != BETA_ONE) rq[r] = psi2;
+                }
+            }
+            consumer_sync<BX>();
+            if (s_abort) break;
+            if (j >= 2 && t < W) {
+                const int sp = (int)((jg - 1) % STAGES);
+                const elem* st = stage + (size_t)sp * 18 * SEGW;
+                const int c = t + HALO;
+                real f[9], g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
+                    g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                }
+                real rho = f[0];
+#pragma unroll
+                for (int i = 1; i < 9; ++i) rho += f[i];
+                const int r = t + 1;
+                real Fx, Fy, ux, uy, T;
+                force_from_rows<real, BMODE>(
+                    kp, ring_psi + (int)((jg - 2) & 3) * RW + r, ring_psi + (int)((jg - 1) & 3) * RW + r,
+                    ring_psi + (int)(jg & 3) * RW + r, ring_psi2 + (int)((jg - 2) & 3) * RW + r,
+                    ring_psi2 + (int)((jg - 1) & 3) * RW + r, ring_psi2 + (int)(jg & 3) * RW + r, Fx, Fy);
+                collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+                const int y = item.y0 + j - 2;
+                const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + t);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
+                    S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
+                }
+            }
+            // the job before this one has had its last reader in this warp
+            if (j >= 1) {
+                __syncwarp();
+                if ((t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
+            }
+        }
+        if (s_abort) break;
+        // the item's last job (a halo row, never collided) is released too, so
+        // the producer may reuse its stage for the next item
+        __syncwarp();
+        if ((t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
+        if (flags) atomicOr(kp.err, flags);
+    }
+    if (s_abort && t == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);
+}
+
+// Per-domain partial sums over tiles of 256 sites: rho, rho c_v T (sum g),
+// |d rho|^2, rho^2, |dT|^2, T^2 against the reference fields, and the new
+// reference fields are written.  One CTA per (domain, tile) item.
+struct BatchTile {
+    int domain;
+    int first;   // first site (row-major) of the tile in the domain
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(256)
+    k_batch_check(const typename Store<PREC>::elem* __restrict__ src_base,
+                  const BatchDomain* __restrict__ doms, const BatchTile* __restrict__ tiles,
+                  const int* __restrict__ n_tiles_ptr, double* __restrict__ ref_rho,
+                  double* __restrict__ ref_T, int have_ref, double* __restrict__ part) {
+    using S = Store<PREC>;
+    using real = typename S::real;
+    __shared__ double s_red[8][6];
+    const int b = blockIdx.x;
+    if (b >= *n_tiles_ptr) return;  // the grid covers the longest list
+    const BatchTile tile = tiles[b];
+    const BatchDomain& D = doms[tile.domain];
+    const KParams& kp = D.kp;
+    const int n = kp.nx * kp.ny;
+    const int s = tile.first + (int)threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (s < n) {
+        const int x = s % kp.nx, y = s / kp.nx;
+        real f[9], g[9];
+        pull18<S>(src_base + D.off, kp, x, y, f, g);
+        real rho = f[0], e = g[0];
+        double m = (double)f[0], en = (double)g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            rho += f[i];
+            e += g[i];
+            m += (double)f[i];
+            en += (double)g[i];
+        }
+        const double r = (double)rho, T = (double)(e / (rho * (real)kp.cv));
+        const long long fo = D.fld_off + s;
+        v[0] = m;
+        v[1] = en;
+        if (have_ref) {
+            const double a = r - ref_rho[fo], c = T - ref_T[fo];
+            v[2] = a * a;
+            v[4] = c * c;
+        }
+        v[3] = r * r;
+        v[5] = T * T;
+        ref_rho[fo] = r;
+        ref_T[fo] = T;
+        if (!isfinite(r) || !isfinite(T)) atomicOr(kp.err, 1 << LB_ERR_NONFINITE);
+    }
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((tid & 31) == 0) s_red[tid >> 5][k] = x;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        double x = 0.0;
+        for (int w = 0; w < 8; ++w) x += s_red[w][tid];
+        part[(long long)b * 6 + tid] = x;
+    }
+}
+
+// Folds each domain's tile partials (contiguous, in order) into its totals.
+static __global__ void k_batch_fold(const double* __restrict__ part, const int* __restrict__ tile_begin,
+                             int n_domains, double* __restrict__ out6) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n_domains) return;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = tile_begin[d]; b < tile_begin[d + 1]; ++b)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += part[(long long)b * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out6[(long long)d * 6 + k] = acc[k];
+}
+
+}  // namespace lbgb

@@ -21,6 +21,7 @@ from . import build as _build
 
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM = 0, 1, 2, 3
 LB_ERR_NONFINITE, LB_ERR_PSI_DOMAIN, LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED = 4, 5, 6, 7
+LB_ERR_NOT_CONVERGED = 8
 LB_EOS_CS, LB_EOS_VDW, LB_EOS_IDEAL = 0, 1, 2
 LB_THERMAL_EQ7, LB_THERMAL_EQ24 = 0, 1
 LB_PREC_FP64, LB_PREC_FP32, LB_PREC_FP16_DEV, LB_PREC_BF16_DEV = 0, 1, 2, 3
@@ -62,6 +63,8 @@ EXPORTED = [
     "lb_moments", "lb_moments_device", "lb_get_populations", "lb_set_populations",
     "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
     "lb_get_params", "lb_free", "lb_last_error", "lb_version", "lb_field_totals_noalloc",
+    "lb_batch_init", "lb_batch_step", "lb_batch_check", "lb_batch_run", "lb_batch_fields",
+    "lb_batch_time", "lb_batch_free",
 ]
 
 
@@ -104,6 +107,15 @@ def load(path: str | None = None):
         "lb_version": (ctypes.c_char_p, []),
         "lb_field_totals_noalloc": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp,
                                          vp, vp, vp, vp, ctypes.c_int64, vp, vp]),
+        "lb_batch_init": (st, [P, ctypes.c_int32, ctypes.POINTER(dp), ctypes.POINTER(dp), vp,
+                               ctypes.POINTER(vp)]),
+        "lb_batch_step": (st, [vp, ctypes.c_int64]),
+        "lb_batch_check": (st, [vp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32)]),
+        "lb_batch_run": (st, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                              ctypes.POINTER(ctypes.c_int64), dp, ctypes.POINTER(ctypes.c_int32)]),
+        "lb_batch_fields": (st, [vp, ctypes.c_int32, dp, dp]),
+        "lb_batch_time": (ctypes.c_int64, [vp]),
+        "lb_batch_free": (st, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +275,103 @@ def lb_last_error() -> str:
 
 def lb_version() -> str:
     return load().lb_version().decode()
+
+
+def lb_batch_init(params, rhos, Ts, stream=None):
+    """params: sequence of lb_params; rhos, Ts: host float64 fields per domain."""
+    n = len(params)
+    arr = (lb_params * n)(*params)
+    rhos = [_host(r, (p.ny, p.nx)) for r, p in zip(rhos, params)]
+    Ts = [_host(t, (p.ny, p.nx)) for t, p in zip(Ts, params)]
+    rp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(r) for r in rhos])
+    tp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(t) for t in Ts])
+    b = ctypes.c_void_p()
+    _check(load().lb_batch_init(arr, n, rp, tp, _stream(stream), ctypes.byref(b)))
+    return b
+
+
+def lb_batch_step(b, n=1):
+    _check(load().lb_batch_step(b, int(n)))
+
+
+def lb_batch_check(b, n):
+    """(residual, mass, energy, status) arrays of length n."""
+    r, m, e = np.zeros(n), np.zeros(n), np.zeros(n)
+    stt = np.zeros(n, dtype=np.int32)
+    _check(load().lb_batch_check(b, _dptr(r), _dptr(m), _dptr(e),
+                                 stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return r, m, e, stt
+
+
+def lb_batch_run(b, n, tol, K=100, max_steps=10 ** 6):
+    """Run to residual < tol; returns (steps, residual, status) arrays."""
+    steps = np.zeros(n, dtype=np.int64)
+    resid = np.zeros(n)
+    stt = np.zeros(n, dtype=np.int32)
+    _check(load().lb_batch_run(b, float(tol), int(K), int(max_steps),
+                               steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(resid),
+                               stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return steps, resid, stt
+
+
+def lb_batch_fields(b, d, nx, ny):
+    rho = np.empty((ny, nx))
+    T = np.empty((ny, nx))
+    _check(load().lb_batch_fields(b, int(d), _dptr(rho), _dptr(T)))
+    return rho, T
+
+
+def lb_batch_time(b) -> int:
+    return int(load().lb_batch_time(b))
+
+
+def lb_batch_free(b):
+    if b is not None:
+        _check(load().lb_batch_free(b))
+
+
+class Batch:
+    """Owner of one batch of independent domains (see lb_batch_* in include/lb.h)."""
+
+    def __init__(self, params, rhos, Ts, stream=None):
+        self.params = list(params)
+        self.n = len(self.params)
+        self.b = lb_batch_init(self.params, rhos, Ts, stream)
+
+    def step(self, n=1):
+        lb_batch_step(self.b, n)
+        return self
+
+    def check(self):
+        return lb_batch_check(self.b, self.n)
+
+    def run(self, tol, K=100, max_steps=10 ** 6):
+        return lb_batch_run(self.b, self.n, tol, K, max_steps)
+
+    def fields(self, d):
+        p = self.params[d]
+        return lb_batch_fields(self.b, d, p.nx, p.ny)
+
+    @property
+    def time(self):
+        return lb_batch_time(self.b)
+
+    def close(self):
+        if self.b is not None:
+            lb_batch_free(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Lattice:
