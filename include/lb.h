@@ -79,6 +79,8 @@ enum {
 
 /* Numbers of lb_totals outputs. */
 enum { LB_TOTALS_N = 5 };
+enum { LB_TUNE_N = 5 };        /* step shapes lb_autotune tries        */
+enum { LB_BATCH_TUNE_N = 4 };  /* row-chunk heights lb_batch_autotune tries */
 
 typedef struct lb_params {
     int32_t nx, ny;        /* lattice size, both >= 3                                  */
@@ -171,6 +173,27 @@ lb_status lb_get_params(const lb_ctx* ctx, lb_params* out);
 /* Release the context and its device memory.  NULL is accepted. */
 lb_status lb_free(lb_ctx* ctx);
 
+/* ---------------------------------------------------------------- autotune
+ * The fused step (Eqs. 1, 2/4, 7 or 24-25) runs as one of LB_TUNE_N shapes:
+ * k = 0, 1: the strip-marching kernel, 256 or 128 columns wide (tile_y == 0;
+ * nx a multiple of 16 bytes of elements; FP64: 128 only); k = 2..4: the tile
+ * kernel with tiles 32x8, 32x16, 64x4.  Results do not depend on the shape
+ * (FP64 storage: bit for bit), only the time does.
+ *
+ * lb_tune_candidate: the (tile_x, tile_y) of shape k.  LB_ERR_ARG if k is out
+ * of range.
+ * lb_autotune: time every shape valid for *p (its lattice, precision,
+ * treatment and force form; p's own tile fields are ignored) over `steps`
+ * fused steps after 2 warm-up steps, on a uniform state (rho0, T0 of *p),
+ * with CUDA events on `stream` (NULL: a stream of its own).  *best = *p with
+ * the fastest tile_x, tile_y; ms_per_step[k] (may be NULL) = each shape's
+ * time per step in ms, NaN for shapes not valid here.  Allocates and frees
+ * one trial context at a time (two population buffers of the lattice);
+ * synchronises.  LB_ERR_ARG for NULL params/best or steps < 1. */
+lb_status lb_tune_candidate(int32_t k, int32_t* tile_x, int32_t* tile_y);
+lb_status lb_autotune(const lb_params* p, int32_t steps, void* stream, lb_params* best,
+                      double ms_per_step[LB_TUNE_N]);
+
 /* ------------------------------------------------------------------ batch
  * Many independent periodic domains (a parameter sweep) advanced together by
  * one persistent fused-step kernel over a device work list of (domain, strip,
@@ -216,6 +239,22 @@ int64_t lb_batch_time(const lb_batch* b);
 
 /* Release the batch.  NULL is accepted. */
 lb_status lb_batch_free(lb_batch* b);
+
+/* Work-list granularity: every domain strip is cut into row chunks of about
+ * `rows` rows (>= 16; default 64); smaller chunks balance uneven domains over
+ * the persistent CTAs, larger ones re-read fewer halo rows.
+ * lb_batch_set_chunk_rows rebuilds the lists (synchronises); LB_ERR_ARG for
+ * rows < 16.  lb_batch_chunk_rows returns the current height (-1 for NULL).
+ * lb_batch_autotune times `steps` batched steps (after 2 warm-up steps) for
+ * each of the LB_BATCH_TUNE_N heights 16, 32, 64, 128, keeps the fastest and
+ * writes it to *chunk_rows (may be NULL); ms_per_step[k] (may be NULL) gets
+ * each height's time per step.  The batch state, its time and its error
+ * words are restored afterwards, bit for bit (one temporary device copy of
+ * the state is allocated and freed).  Synchronises. */
+lb_status lb_batch_set_chunk_rows(lb_batch* b, int32_t rows);
+int32_t lb_batch_chunk_rows(const lb_batch* b);
+lb_status lb_batch_autotune(lb_batch* b, int32_t steps, int32_t* chunk_rows,
+                            double ms_per_step[LB_BATCH_TUNE_N]);
 
 /* Allocation-free FP64 totals of caller-owned device fields.
  *

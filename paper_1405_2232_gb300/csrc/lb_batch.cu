@@ -34,6 +34,9 @@ namespace {
 
 constexpr int BATCH_BX_FP32 = 256;
 constexpr int BATCH_BX_FP64 = 128;
+// row-chunk heights the autotuner tries; the work list is sized for the smallest
+constexpr int kChunkCand[LB_BATCH_TUNE_N] = {16, 32, 64, 128};
+constexpr int MIN_CHUNK_ROWS = 16;
 
 lb_status err(lb_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 lb_status err(lb_status st, const char* fmt, ...) {
@@ -330,7 +333,7 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         D.fld_off = fld;
         off += 18 * plane;
         fld += (long long)p.nx * p.ny;
-        max_items += ((p.nx + b->bx - 1) / b->bx) * ((p.ny + b->chunk_rows - 1) / b->chunk_rows);
+        max_items += ((p.nx + b->bx - 1) / b->bx) * ((p.ny + MIN_CHUNK_ROWS - 1) / MIN_CHUNK_ROWS);
         max_tiles += (p.nx * p.ny + 255) / 256;
     }
     b->n_sites = fld;
@@ -522,6 +525,79 @@ lb_status lb_batch_fields(lb_batch* b, int32_t d, double* rho, double* T) {
 }
 
 int64_t lb_batch_time(const lb_batch* b) { return b ? b->t : -1; }
+
+lb_status lb_batch_set_chunk_rows(lb_batch* b, int32_t rows) {
+    if (!b || rows < MIN_CHUNK_ROWS || rows > 1 << 20)
+        return err(LB_ERR_ARG, "lb_batch_set_chunk_rows: rows must be >= %d", MIN_CHUNK_ROWS);
+    BCU(cudaSetDevice(b->device), "cudaSetDevice");
+    b->chunk_rows = rows;
+    return rebuild_lists(b);
+}
+
+int32_t lb_batch_chunk_rows(const lb_batch* b) { return b ? b->chunk_rows : -1; }
+
+lb_status lb_batch_autotune(lb_batch* b, int32_t steps, int32_t* chunk_rows,
+                            double ms_per_step[LB_BATCH_TUNE_N]) {
+    if (!b || steps < 1) return err(LB_ERR_ARG, "lb_batch_autotune: NULL batch or steps < 1");
+    BCU(cudaSetDevice(b->device), "cudaSetDevice");
+    // snapshot: the current buffer (active and frozen domains) and the error words
+    void* snap = nullptr;
+    BCU(cudaMalloc(&snap, b->buf_bytes), "autotune snapshot");
+    std::vector<int> errw(b->n, 0);
+    cudaError_t e = cudaMemcpyAsync(snap, b->buf[b->cur], b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(errw.data(), b->d_err, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    const int cur0 = b->cur, rows0 = b->chunk_rows;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    lb_status st = LB_OK;
+    double best = INFINITY;
+    int best_rows = rows0;
+    for (int k = 0; k < LB_BATCH_TUNE_N && e == cudaSuccess && st == LB_OK; ++k) {
+        if (ms_per_step) ms_per_step[k] = NAN;
+        b->chunk_rows = kChunkCand[k];
+        st = rebuild_lists(b);
+        if (st != LB_OK) break;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+            e = launch_batch_step(b, b->buf[b->cur], b->buf[b->cur ^ 1]);
+            b->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], b->stream);
+        for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+            e = launch_batch_step(b, b->buf[b->cur], b->buf[b->cur ^ 1]);
+            b->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) break;
+        const double per = (double)ms / steps;
+        if (ms_per_step) ms_per_step[k] = per;
+        if (per < best) {
+            best = per;
+            best_rows = kChunkCand[k];
+        }
+    }
+    // restore the snapshot, whatever happened
+    b->cur = cur0;
+    cudaError_t e2 = cudaMemcpyAsync(b->buf[cur0], snap, b->buf_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e2 == cudaSuccess)
+        e2 = cudaMemcpyAsync(b->d_err, errw.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(b->stream);
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    cudaFree(snap);
+    if (e != cudaSuccess) return cuerr(e, "batch autotune");
+    if (e2 != cudaSuccess) return cuerr(e2, "batch autotune restore");
+    if (st != LB_OK) return st;
+    b->chunk_rows = st == LB_OK && std::isfinite(best) ? best_rows : rows0;
+    st = rebuild_lists(b);
+    if (st == LB_OK && chunk_rows) *chunk_rows = b->chunk_rows;
+    return st;
+}
 
 lb_status lb_batch_free(lb_batch* b) {
     release(b);

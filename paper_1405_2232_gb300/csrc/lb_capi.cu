@@ -72,6 +72,13 @@ lb_status validate(const lb_params* p) {
         if (p->tile_y == 0 && p->nx % strip_halo(p->precision) != 0)
             return fail(LB_ERR_ARG, "strip kernel needs nx to be a multiple of %d",
                         strip_halo(p->precision));
+        if (p->tile_y == 0) {
+            const long long es = (long long)elem_size(p->precision);
+            const long long pitch = ((long long)p->nx * es + 127) / 128 * 128 / es;
+            const long long plane = (pitch * p->ny * es + 255) / 256 * 256 / es;
+            if (!strip_eligible(p->precision, p->nx, plane, p->tile_x))
+                return fail(LB_ERR_ARG, "lattice too large for the strip kernel's 32-bit offsets");
+        }
     }
     return LB_OK;
 }

@@ -127,11 +127,13 @@ class Domain:
 
 
 def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_TC,
-                  fixed_L=None):
+                  fixed_L=None, L_multiple=4):
     """Parameter sweep of independent periodic square domains.
 
     Per domain d (stream index 16 d + k of the counter-based generator):
-    side L ~ U{L_min..L_max}, T/T_c ~ U[0.6, 0.95], G ~ U[-1.2, -0.8],
+    side L ~ U{L_min..L_max} rounded down to a multiple of L_multiple (4: a row
+    of FP32 populations is then a whole number of 16-byte units),
+    T/T_c ~ U[0.6, 0.95], G ~ U[-1.2, -0.8],
     tau_f ~ U[0.6, 1.2], tau_g fixed; droplet (radius U[L/8, L/4]) or slab
     (width U[L/4, L/2]) from a fair coin.
     """
@@ -140,6 +142,7 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
         u = uniform01(seed, np.arange(16 * d, 16 * d + 8, dtype=np.uint64))
         L = int(fixed_L) if fixed_L else int(L_min + min(int(u[0] * (L_max - L_min + 1)),
                                                          L_max - L_min))
+        L -= L % L_multiple
         T_over = 0.6 + 0.35 * u[1]
         G = -1.2 + 0.4 * u[2]
         tau_f = 0.6 + 0.6 * u[3]

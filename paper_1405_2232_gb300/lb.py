@@ -26,6 +26,8 @@ LB_EOS_CS, LB_EOS_VDW, LB_EOS_IDEAL = 0, 1, 2
 LB_THERMAL_EQ7, LB_THERMAL_EQ24 = 0, 1
 LB_PREC_FP64, LB_PREC_FP32, LB_PREC_FP16_DEV, LB_PREC_BF16_DEV = 0, 1, 2, 3
 LB_TOTALS_N = 5
+LB_TUNE_N = 5
+LB_BATCH_TUNE_N = 4
 
 PRECISIONS = {"fp64": LB_PREC_FP64, "fp32": LB_PREC_FP32, "fp16": LB_PREC_FP16_DEV,
               "bf16": LB_PREC_BF16_DEV}
@@ -64,7 +66,8 @@ EXPORTED = [
     "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
     "lb_get_params", "lb_free", "lb_last_error", "lb_version", "lb_field_totals_noalloc",
     "lb_batch_init", "lb_batch_step", "lb_batch_check", "lb_batch_run", "lb_batch_fields",
-    "lb_batch_time", "lb_batch_free",
+    "lb_batch_time", "lb_batch_free", "lb_tune_candidate", "lb_autotune",
+    "lb_batch_set_chunk_rows", "lb_batch_chunk_rows", "lb_batch_autotune",
 ]
 
 
@@ -116,6 +119,12 @@ def load(path: str | None = None):
         "lb_batch_fields": (st, [vp, ctypes.c_int32, dp, dp]),
         "lb_batch_time": (ctypes.c_int64, [vp]),
         "lb_batch_free": (st, [vp]),
+        "lb_tune_candidate": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32)]),
+        "lb_autotune": (st, [P, ctypes.c_int32, vp, P, dp]),
+        "lb_batch_set_chunk_rows": (st, [vp, ctypes.c_int32]),
+        "lb_batch_chunk_rows": (ctypes.c_int32, [vp]),
+        "lb_batch_autotune": (st, [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +334,38 @@ def lb_batch_time(b) -> int:
     return int(load().lb_batch_time(b))
 
 
+def lb_tune_candidate(k: int):
+    """(tile_x, tile_y) of step shape k (tile_y == 0: strip kernel)."""
+    tx, ty = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().lb_tune_candidate(int(k), ctypes.byref(tx), ctypes.byref(ty)))
+    return tx.value, ty.value
+
+
+def lb_autotune(p: lb_params, steps: int, stream=None):
+    """Time every valid step shape for p; returns (best params, ms per step per shape)."""
+    best = lb_params()
+    ms = np.full(LB_TUNE_N, np.nan)
+    _check(load().lb_autotune(ctypes.byref(p), int(steps), _stream(stream), ctypes.byref(best),
+                              _dptr(ms)))
+    return best, ms
+
+
+def lb_batch_set_chunk_rows(b, rows: int):
+    _check(load().lb_batch_set_chunk_rows(b, int(rows)))
+
+
+def lb_batch_chunk_rows(b) -> int:
+    return int(load().lb_batch_chunk_rows(b))
+
+
+def lb_batch_autotune(b, steps: int):
+    """Time the row-chunk heights; returns (chosen height, ms per step per height)."""
+    rows = ctypes.c_int32()
+    ms = np.full(LB_BATCH_TUNE_N, np.nan)
+    _check(load().lb_batch_autotune(b, int(steps), ctypes.byref(rows), _dptr(ms)))
+    return rows.value, ms
+
+
 def lb_batch_free(b):
     if b is not None:
         _check(load().lb_batch_free(b))
@@ -355,6 +396,17 @@ class Batch:
     @property
     def time(self):
         return lb_batch_time(self.b)
+
+    @property
+    def chunk_rows(self):
+        return lb_batch_chunk_rows(self.b)
+
+    @chunk_rows.setter
+    def chunk_rows(self, rows):
+        lb_batch_set_chunk_rows(self.b, rows)
+
+    def autotune(self, steps=20):
+        return lb_batch_autotune(self.b, steps)
 
     def close(self):
         if self.b is not None:
