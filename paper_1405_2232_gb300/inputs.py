@@ -159,3 +159,61 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
         out.append(Domain(L, float(T_over), float(G), float(tau_f), float(tau_g), kind,
                           float(size), rho, T))
     return out
+
+
+# ------------------------------------------------------- warm-start network
+#: Normalisation of the network's input planes and outputs:
+#: input (T/T_c - t_mid)/t_scale, (G - g_mid)/g_scale, 2 mask - 1;
+#: output rho = rho_mid + rho_scale y0, T/T_c = t_mid + t_scale y1.
+UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_mid=0.2, rho_scale=0.2)
+
+
+def normal01(seed: int, index: np.ndarray) -> np.ndarray:
+    """Counter-based standard normals (Box-Muller on uniform01(seed, 2i), (2i+1))."""
+    i = np.asarray(index, dtype=np.uint64)
+    u1 = uniform01(seed, np.uint64(2) * i)
+    u2 = uniform01(seed, np.uint64(2) * i + np.uint64(1))
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def unet_init_params(layers, seed=11) -> np.ndarray:
+    """He-normal initial parameters (float32 values) for a layer list of
+    (name, cin_stored, cout, ksize, cin_real): W[cout, k, k, cin_stored] with
+    std sqrt(2 / (k^2 cin_real)) for 3x3 layers and sqrt(1 / cin_real) for the
+    1x1 head, zero for input channels >= cin_real (padding); biases zero.
+    Flat order: W then b, layer by layer."""
+    out, base = [], 0
+    for _, ci, co, k, ci_real in layers:
+        n = co * k * k * ci
+        std = np.sqrt((2.0 if k == 3 else 1.0) / (k * k * ci_real))
+        W = (normal01(seed, np.arange(base, base + n, dtype=np.uint64)) * std).reshape(co, k, k, ci)
+        W[..., ci_real:] = 0.0
+        out += [W.reshape(-1), np.zeros(co)]
+        base += n
+    return np.concatenate(out).astype(np.float32)
+
+
+def unet_input_planes(T_over_Tc, G, mask) -> np.ndarray:
+    """Network input [N, H, W, 3] float32 from per-case T/T_c [N], G [N] and
+    initial liquid masks [N, H, W] (1 inside the droplet/slab)."""
+    m = np.asarray(mask, dtype=np.float64)
+    n = m.shape[0]
+    t = ((np.asarray(T_over_Tc, dtype=np.float64) - UNET_NORM["t_mid"]) / UNET_NORM["t_scale"]).reshape(n, 1, 1)
+    g = ((np.asarray(G, dtype=np.float64) - UNET_NORM["g_mid"]) / UNET_NORM["g_scale"]).reshape(n, 1, 1)
+    return np.stack([np.broadcast_to(t, m.shape), np.broadcast_to(g, m.shape), 2.0 * m - 1.0],
+                    axis=3).astype(np.float32)
+
+
+def unet_target_planes(rho, T, Tc=CS_TC) -> np.ndarray:
+    """Normalised training targets [N, H, W, 2] float32 from steady rho, T fields."""
+    r = (np.asarray(rho) - UNET_NORM["rho_mid"]) / UNET_NORM["rho_scale"]
+    t = (np.asarray(T) / Tc - UNET_NORM["t_mid"]) / UNET_NORM["t_scale"]
+    return np.stack([r, t], axis=-1).astype(np.float32)
+
+
+def warm_start_cases(n, L=256, seed=5):
+    """n sweep cases at a fixed L x L (the batched sweep's parameter
+    distributions); returns the domains and their initial liquid masks."""
+    doms = batched_sweep(n_domains=n, seed=seed, fixed_L=L)
+    masks = np.stack([(d.rho > 0.5 * (RHO_LIQUID + RHO_GAS)).astype(np.float32) for d in doms])
+    return doms, masks
