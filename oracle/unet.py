@@ -180,8 +180,9 @@ def forward(flat, x, arch, rnd=None, keep=False):
     return y
 
 
-def loss_and_grad(flat, x, target, arch, rnd=None):
-    """(mean squared error, flat gradient) at the given parameters."""
+def loss_and_grad(flat, x, target, arch, rnd=None, keep=False):
+    """(mean squared error, flat gradient) at the given parameters; with
+    keep=True also the forward cache and the activation-gradient tensors."""
     R = rnd or _id
     y, C, P, levels = forward(flat, x, arch, rnd=rnd, keep=True)
     diff = y - target
@@ -194,32 +195,41 @@ def loss_and_grad(flat, x, target, arch, rnd=None):
     G["head"] = ((gy.reshape(-1, gy.shape[3]).T @ h.reshape(-1, h.shape[3]))[:, None, None, :],
                  gy.reshape(-1, gy.shape[3]).sum(axis=0))
     g = R((gy @ Wh[:, 0, 0, :]) * (h > 0))
+    GT = {"gD0": g}
     cat_grads = {}
     # decoder, finest first
     for l in range(levels - 1):
         # g: gradient at the pre-activation of d{l}b
         G[f"d{l}b"] = conv3_wgrad(g, C[f"d{l}b"])
         g = R(conv3_dgrad(g, P[f"d{l}b"][0]) * (C[f"d{l}a:out"] > 0))
+        GT[("gC", l)] = g
         G[f"d{l}a"] = conv3_wgrad(g, C[f"d{l}a"])
         gcat = R(conv3_dgrad(g, P[f"d{l}a"][0]))
+        GT[("gCAT", l)] = gcat
         n_up = gcat.shape[3] - C[f"e{l}b:out"].shape[3]
         cat_grads[l] = gcat[..., n_up:]
         below = C[f"d{l + 1}b:out"] if l + 1 < levels - 1 else C[f"e{levels - 1}b:out"]
         g = R(up2_bwd(gcat[..., :n_up]) * (below > 0))
+        GT[("gUP", l + 1)] = g
     # bottom level: g is the gradient at the pre-activation of e{L-1}b
     for l in reversed(range(levels)):
         G[f"e{l}b"] = conv3_wgrad(g, C[f"e{l}b"])
         g = R(conv3_dgrad(g, P[f"e{l}b"][0]) * (C[f"e{l}a:out"] > 0))
+        GT[("gA", l)] = g
         G[f"e{l}a"] = conv3_wgrad(g, C[f"e{l}a"])
         if l == 0:
             break
         gp = R(conv3_dgrad(g, P[f"e{l}a"][0]))
+        GT[("gP", l - 1)] = gp
         g = R((pool2_bwd(gp) + cat_grads[l - 1]) * (C[f"e{l - 1}b:out"] > 0))
+        GT[("gS", l - 1)] = g
     out = []
     for name, ci, co, k, _ in arch:
         gW, gb = G[name]
         out.append(np.asarray(gW).reshape(-1))
         out.append(np.asarray(gb).reshape(-1))
+    if keep:
+        return loss, np.concatenate(out), C, GT
     return loss, np.concatenate(out)
 
 
@@ -233,9 +243,11 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 # --------------------------------------------------- warm-start handoff
-def denormalise(y, rho_mid, rho_scale, t_mid, t_scale, Tc):
-    """Network output -> (rho_hat, T_hat) fields."""
-    return rho_mid + rho_scale * y[..., 0], Tc * (t_mid + t_scale * y[..., 1])
+def denormalise(y, rho_mid, rho_scale, t_mid, t_scale, Tc, rho_floor=1e-4):
+    """Network output -> (rho_hat, T_hat) fields; rho_hat is kept >= rho_floor
+    (the method needs a positive density everywhere)."""
+    return (np.maximum(rho_mid + rho_scale * y[..., 0], rho_floor),
+            Tc * (t_mid + t_scale * y[..., 1]))
 
 
 def warm_project(rho_hat, T_hat, rho0, T0):

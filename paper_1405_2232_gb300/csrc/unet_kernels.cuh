@@ -1,0 +1,652 @@
+// unet_kernels.cuh -- device kernels of the warm-start network (include/unet.h).
+//
+// The 3x3 circular convolutions run as implicit GEMMs on the BF16 tensor
+// cores (mma.sync m16n8k16, FP32 accumulation) with cp.async staging:
+//   forward / input gradient: out[p][co] = sum_{tap, ci} in[shift_tap(p)][ci] W[co][tap][ci]
+//     (the input gradient uses the flipped, transposed weights
+//      Wt[ci][8 - tap][co], because shift_{8-tap} = -shift_tap);
+//   weight gradient: dW[co][tap][ci] = sum_p g[p][co] in[shift_tap(p)][ci],
+//     split over pixel ranges, partials reduced in a fixed order.
+// Everything else (pool, upsampling gradients, head, loss, Adam, handoff) is
+// element-wise or a small reduction and bound by memory traffic.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace unk {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous copy global -> shared; valid == false zero-fills
+// (no bytes are read; src must still be a mapped address)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+// D += A (16x16, row) * B (16x8, col), BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// ------------------------------------------------------------ convolution
+struct ConvArgs {
+    const bf16* x;  // input view: pixel stride xC, first channel xoff, Cin channels
+    int xC, xoff, Cin;
+    const bf16* w;  // [Cout][9][Cin]
+    const float* bias;  // [Cout] or nullptr
+    int Cout;
+    bf16* y;  // output view
+    int yC, yoff;
+    const bf16* mask;  // optional: output *= (mask > 0) (same pixel, channel co)
+    int mC, moff;
+    int N, H, W;
+    int relu;  // forward: ReLU after the bias
+    int up;    // store each output pixel to the 2x2 block of a 2H x 2W image
+};
+
+constexpr int CV_MT = 128;   // pixels per CTA
+constexpr int CV_KC = 32;    // channels per K step
+constexpr int CV_LD = 40;    // shared row stride (halves): conflict-free ldmatrix
+constexpr int CV_STAGES = 3;
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_conv3(ConvArgs a) {
+    __shared__ __align__(128) bf16 sA[CV_STAGES][CV_MT * CV_LD];
+    __shared__ __align__(128) bf16 sB[CV_STAGES][NT * CV_LD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int HW = a.H * a.W;
+    const int M = a.N * HW;
+    const int m0 = blockIdx.x * CV_MT;
+    const int co0 = blockIdx.y * NT;
+    int an[2], ay[2], ax[2];
+    bool av[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int m = m0 + (tid >> 2) + i * 64;
+        av[i] = m < M;
+        const int mm = av[i] ? m : 0;
+        an[i] = mm / HW;
+        const int r = mm - an[i] * HW;
+        ay[i] = r / a.W;
+        ax[i] = r - ay[i] * a.W;
+    }
+    const int part = tid & 3;
+    const int kchunks = a.Cin / CV_KC;
+    const int KT = 9 * kchunks;
+
+    auto load_stage = [&](int kt, int s) {
+        const int tap = kt / kchunks, c0 = (kt - tap * kchunks) * CV_KC;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int yy = wrap(ay[i] + dy, a.H), xx = wrap(ax[i] + dx, a.W);
+            const long long pix = ((long long)an[i] * a.H + yy) * a.W + xx;
+            cp_async16(&sA[s][((tid >> 2) + i * 64) * CV_LD + part * 8],
+                       a.x + pix * a.xC + a.xoff + c0 + part * 8, av[i]);
+        }
+        for (int q = tid; q < NT * 4; q += 256) {
+            const int r = q >> 2, pp = q & 3;
+            cp_async16(&sB[s][r * CV_LD + pp * 8], a.w + ((long long)(co0 + r) * 9 + tap) * a.Cin + c0 + pp * 8,
+                       true);
+        }
+    };
+
+    const int wm = warp & 3, wn = warp >> 2;
+    constexpr int WN = NT / 2;
+    constexpr int NI = WN / 8;
+    float acc[2][NI][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[mi][ni][k] = 0.0f;
+
+#pragma unroll
+    for (int s = 0; s < CV_STAGES - 1; ++s) {
+        if (s < KT) load_stage(s, s);
+        cp_async_commit();
+    }
+    const int q = lane >> 3, rr = lane & 7;
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<CV_STAGES - 2>();
+        __syncthreads();
+        {
+            const int nk = kt + CV_STAGES - 1;
+            if (nk < KT) load_stage(nk, nk % CV_STAGES);
+            cp_async_commit();
+        }
+        const bf16* A = sA[kt % CV_STAGES];
+        const bf16* B = sB[kt % CV_STAGES];
+#pragma unroll
+        for (int kk = 0; kk < CV_KC; kk += 16) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm_x4(af[mi], A + (wm * 32 + mi * 16 + rr + (q & 1) * 8) * CV_LD + kk + (q >> 1) * 8);
+#pragma unroll
+            for (int nj = 0; nj < NI; nj += 2) {
+                uint32_t bf[4];
+                ldsm_x4(bf, B + (wn * WN + nj * 8 + rr + (q >> 1) * 8) * CV_LD + kk + (q & 1) * 8);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    mma_bf16(acc[mi][nj], af[mi], bf[0], bf[1]);
+                    mma_bf16(acc[mi][nj + 1], af[mi], bf[2], bf[3]);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = m0 + wm * 32 + mi * 16 + g + h * 8;
+            if (m >= M) continue;
+            const int n = m / HW;
+            const int rem = m - n * HW;
+            const int yy = rem / a.W, xx = rem - yy * a.W;
+#pragma unroll
+            for (int ni = 0; ni < NI; ++ni) {
+                const int co = co0 + wn * WN + ni * 8 + 2 * t4;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (a.bias) {
+                    v0 += a.bias[co];
+                    v1 += a.bias[co + 1];
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                if (a.mask) {
+                    const bf16* mp = a.mask + (long long)m * a.mC + a.moff + co;
+                    v0 = __bfloat162float(mp[0]) > 0.0f ? v0 : 0.0f;
+                    v1 = __bfloat162float(mp[1]) > 0.0f ? v1 : 0.0f;
+                }
+                const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+                if (!a.up) {
+                    *reinterpret_cast<__nv_bfloat162*>(a.y + (long long)m * a.yC + a.yoff + co) = o;
+                } else {
+                    const int W2 = 2 * a.W;
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const long long pix = ((long long)n * 2 * a.H + 2 * yy + dy) * W2 + 2 * xx + dx;
+                            *reinterpret_cast<__nv_bfloat162*>(a.y + pix * a.yC + a.yoff + co) = o;
+                        }
+                }
+            }
+        }
+}
+
+// -------------------------------------------------------- weight gradient
+struct WgradArgs {
+    const bf16* g;  // gradient at the conv output: pixel stride gC, first channel goff, Cout channels
+    int gC, goff;
+    const bf16* x;  // conv input view, Cin channels
+    int xC, xoff;
+    int Cout, Cin, N, H, W;
+    int chunks_per_split;  // 32-pixel chunks per split (blockIdx.y)
+    float* part;           // [splits][Cout][9][Cin]
+};
+
+template <int MT, int NT>
+__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
+    constexpr int LG = MT + 8, LX = NT + 8;
+    __shared__ __align__(128) bf16 sG[2][32 * LG];
+    __shared__ __align__(128) bf16 sX[2][32 * LX];
+    constexpr int WM = MT / 16, WNW = 8 / WM;  // warp grid
+    constexpr int WT = NT / WNW;               // columns per warp
+    constexpr int NI = WT / 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_ci = a.Cin / NT;
+    int b = blockIdx.x;
+    const int tap = b % 9;
+    b /= 9;
+    const int cit = b % n_ci, cot = b / n_ci;
+    const int co0 = cot * MT, ci0 = cit * NT;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int HW = a.H * a.W;
+    const int M = a.N * HW;
+    const int nchunks = (M + 31) / 32;
+    const int c_begin = blockIdx.y * a.chunks_per_split;
+    const int c_end = min(c_begin + a.chunks_per_split, nchunks);
+
+    auto load = [&](int c, int s) {
+        for (int qq = tid; qq < 32 * MT / 8; qq += 256) {
+            const int px = qq / (MT / 8), pp = qq % (MT / 8);
+            const int m = c * 32 + px;
+            const bool v = m < M;
+            cp_async16(&sG[s][px * LG + pp * 8], a.g + (long long)(v ? m : 0) * a.gC + a.goff + co0 + pp * 8, v);
+        }
+        for (int qq = tid; qq < 32 * NT / 8; qq += 256) {
+            const int px = qq / (NT / 8), pp = qq % (NT / 8);
+            const int m = c * 32 + px;
+            const bool v = m < M;
+            const int mm = v ? m : 0;
+            const int n = mm / HW;
+            const int r = mm - n * HW;
+            const int yy = wrap(r / a.W + dy, a.H), xx = wrap(r % a.W + dx, a.W);
+            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
+            cp_async16(&sX[s][px * LX + pp * 8], a.x + pix * a.xC + a.xoff + ci0 + pp * 8, v);
+        }
+    };
+
+    const int wm = warp % WM, wn = warp / WM;
+    float acc[NI][4];
+#pragma unroll
+    for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[ni][k] = 0.0f;
+    const int q = lane >> 3, rr = lane & 7;
+    if (c_begin < c_end) {
+        load(c_begin, 0);
+        cp_async_commit();
+    }
+    for (int c = c_begin; c < c_end; ++c) {
+        const int s = (c - c_begin) & 1;
+        if (c + 1 < c_end) {
+            load(c + 1, s ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t af[4];
+            // A[m = co][k = px] from sG[px][co]: transposed 8x8 loads
+            ldsm_x4_t(af, &sG[s][(kk + rr + (q >> 1) * 8) * LG + wm * 16 + (q & 1) * 8]);
+#pragma unroll
+            for (int ni = 0; ni < NI; ++ni) {
+                uint32_t b0, b1;
+                ldsm_x2_t(b0, b1, &sX[s][(kk + rr + (q & 1) * 8) * LX + wn * WT + ni * 8]);
+                mma_bf16(acc[ni], af, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t4 = lane & 3;
+    float* out = a.part + (long long)blockIdx.y * a.Cout * 9 * a.Cin;
+#pragma unroll
+    for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = co0 + wm * 16 + g + h * 8;
+            const int ci = ci0 + wn * WT + ni * 8 + 2 * t4;
+            float* o = out + ((long long)co * 9 + tap) * a.Cin + ci;
+            o[0] = acc[ni][2 * h];
+            o[1] = acc[ni][2 * h + 1];
+        }
+}
+
+// out[i] = sum_s part[s * n + i], s = 0..splits-1 in order
+__global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < splits; ++k) s += part[(long long)k * n + i];
+        out[i] = s;
+    }
+}
+
+// bias gradient partials: part[block][co] = sum over the block's pixels of g[p][co]
+__global__ void __launch_bounds__(256) k_bias_partial(const bf16* __restrict__ g, int gC, int goff, int Cout,
+                                                       int M, int rows_per_block, float* __restrict__ part) {
+    __shared__ float red[256];
+    const int groups = 256 / Cout;
+    const int c = threadIdx.x % Cout, grp = threadIdx.x / Cout;
+    const int p0 = blockIdx.x * rows_per_block, p1 = min(p0 + rows_per_block, M);
+    float s = 0.0f;
+    if (grp < groups)
+        for (int p = p0 + grp; p < p1; p += groups) s += __bfloat162float(g[(long long)p * gC + goff + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < Cout) {
+        float t = 0.0f;
+        for (int k = 0; k < groups; ++k) t += red[k * Cout + threadIdx.x];
+        part[(long long)blockIdx.x * Cout + threadIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------ element-wise parts
+// network input: 3 float32 planes -> BF16 pixels of 32 channels (zero padded)
+__global__ void k_input(const float* __restrict__ in, long long P, bf16* __restrict__ x0) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        __align__(16) bf16 v[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = __float2bfloat16_rn(c < 3 ? in[p * 3 + c] : 0.0f);
+        uint4* dst = reinterpret_cast<uint4*>(x0 + p * 32);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(v)[k];
+    }
+}
+
+__device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    return u;
+}
+
+// 2x2 average pool of a view (H, W: input size) into a dense [N][H/2][W/2][C]
+__global__ void k_pool(const bf16* __restrict__ s, int sC, int soff, int C, int N, int H, int W,
+                       bf16* __restrict__ out) {
+    const int C8 = C / 8, H2 = H / 2, W2 = W / 2;
+    const long long total = (long long)N * H2 * W2 * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const long long op = i / C8;
+        const int x = (int)(op % W2);
+        const long long t = op / W2;
+        const int y = (int)(t % H2);
+        const int n = (int)(t / H2);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const long long ip = ((long long)n * H + 2 * y + dy) * W + 2 * x + dx;
+                float f[8];
+                unpack8(*reinterpret_cast<const uint4*>(s + ip * sC + soff + c8 * 8), f);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] += f[k];
+            }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] *= 0.25f;
+        *reinterpret_cast<uint4*>(out + op * C + c8 * 8) = pack8(acc);
+    }
+}
+
+// gradient through nearest upsampling: out[n][y][x][c] (coarse, dense) =
+// (sum of the 2x2 fine block of g) * (mask at fine (2y, 2x) > 0)
+__global__ void k_up_bwd(const bf16* __restrict__ g, int gC, int goff, const bf16* __restrict__ mask, int mC,
+                         int moff, int C, int N, int H, int W, bf16* __restrict__ out) {
+    const int C8 = C / 8, H2 = H / 2, W2 = W / 2;
+    const long long total = (long long)N * H2 * W2 * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const long long op = i / C8;
+        const int x = (int)(op % W2);
+        const long long t = op / W2;
+        const int y = (int)(t % H2);
+        const int n = (int)(t / H2);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const long long ip = ((long long)n * H + 2 * y + dy) * W + 2 * x + dx;
+                float f[8];
+                unpack8(*reinterpret_cast<const uint4*>(g + ip * gC + goff + c8 * 8), f);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] += f[k];
+            }
+        const long long mp = ((long long)n * H + 2 * y) * W + 2 * x;
+        float mk[8];
+        unpack8(*reinterpret_cast<const uint4*>(mask + mp * mC + moff + c8 * 8), mk);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = mk[k] > 0.0f ? acc[k] : 0.0f;
+        *reinterpret_cast<uint4*>(out + op * C + c8 * 8) = pack8(acc);
+    }
+}
+
+// skip gradient: out[p][c] (fine, dense) = (gp[parent(p)][c] / 4 + gcat[p][c]) * (s[p][c] > 0)
+__global__ void k_skip_bwd(const bf16* __restrict__ gp, const bf16* __restrict__ gcat, int gC, int goff,
+                           const bf16* __restrict__ s, int sC, int soff, int C, int N, int H, int W,
+                           bf16* __restrict__ out) {
+    const int C8 = C / 8;
+    const long long total = (long long)N * H * W * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const long long p = i / C8;
+        const int x = (int)(p % W);
+        const long long t = p / W;
+        const int y = (int)(t % H);
+        const int n = (int)(t / H);
+        const long long pp = ((long long)n * (H / 2) + y / 2) * (W / 2) + x / 2;
+        float a[8], b[8], m[8];
+        unpack8(*reinterpret_cast<const uint4*>(gp + pp * C + c8 * 8), a);
+        unpack8(*reinterpret_cast<const uint4*>(gcat + p * gC + goff + c8 * 8), b);
+        unpack8(*reinterpret_cast<const uint4*>(s + p * sC + soff + c8 * 8), m);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = m[k] > 0.0f ? 0.25f * a[k] + b[k] : 0.0f;
+        *reinterpret_cast<uint4*>(out + p * C + c8 * 8) = pack8(a);
+    }
+}
+
+// ------------------------------------------------------------------ head
+// y[p][j] = sum_c Wh[j][c] h[p][c] + bh[j], j = 0, 1 (FP32 weights)
+template <int C>
+__global__ void k_head_fwd(const bf16* __restrict__ h, const float* __restrict__ Wh, const float* __restrict__ bh,
+                           long long P, float* __restrict__ y) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float y0 = bh[0], y1 = bh[1];
+#pragma unroll
+        for (int c8 = 0; c8 < C / 8; ++c8) {
+            float f[8];
+            unpack8(*reinterpret_cast<const uint4*>(h + p * C + c8 * 8), f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                y0 += Wh[c8 * 8 + k] * f[k];
+                y1 += Wh[C + c8 * 8 + k] * f[k];
+            }
+        }
+        y[p * 2] = y0;
+        y[p * 2 + 1] = y1;
+    }
+}
+
+// Head forward + squared error + backward over a contiguous pixel range per
+// block.  gh[p][c] = (sum_j gy_j Wh[j][c]) * (h > 0), gy = 2 (y - t) / count.
+// Per-block partials: pw[block][2C + 2] (dWh then dbh), pl[block] (sum of squares).
+template <int C>
+__global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ h, const float* __restrict__ Wh,
+                                                   const float* __restrict__ bh, const float* __restrict__ tgt,
+                                                   long long P, int rows_per_block, float inv_count2,
+                                                   bf16* __restrict__ gh, float* __restrict__ pw,
+                                                   double* __restrict__ pl) {
+    constexpr int NV = 2 * C + 2;
+    __shared__ float sw[8][NV];
+    __shared__ double sl[8];
+    float acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0f;
+    double loss = 0.0;
+    const long long p0 = (long long)blockIdx.x * rows_per_block;
+    const long long p1 = min(p0 + rows_per_block, P);
+    for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        float hv[C];
+#pragma unroll
+        for (int c8 = 0; c8 < C / 8; ++c8) {
+            float f[8];
+            unpack8(*reinterpret_cast<const uint4*>(h + p * C + c8 * 8), f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) hv[c8 * 8 + k] = f[k];
+        }
+        float y0 = bh[0], y1 = bh[1];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            y0 += Wh[c] * hv[c];
+            y1 += Wh[C + c] * hv[c];
+        }
+        const float d0 = y0 - tgt[p * 2], d1 = y1 - tgt[p * 2 + 1];
+        loss += (double)d0 * d0 + (double)d1 * d1;
+        const float g0 = d0 * inv_count2, g1 = d1 * inv_count2;
+        float gv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            gv[c] = hv[c] > 0.0f ? g0 * Wh[c] + g1 * Wh[C + c] : 0.0f;
+            acc[c] += g0 * hv[c];
+            acc[C + c] += g1 * hv[c];
+        }
+        acc[2 * C] += g0;
+        acc[2 * C + 1] += g1;
+#pragma unroll
+        for (int c8 = 0; c8 < C / 8; ++c8) {
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = gv[c8 * 8 + k];
+            *reinterpret_cast<uint4*>(gh + p * C + c8 * 8) = pack8(f);
+        }
+    }
+    // warp then block reduction in a fixed order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sw[warp][k] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane == 0) sl[warp] = loss;
+    __syncthreads();
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+        float v = 0.0f;
+        for (int w = 0; w < 8; ++w) v += sw[w][k];
+        pw[(long long)blockIdx.x * NV + k] = v;
+    }
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sl[w];
+        pl[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_sum_doubles(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += part[k];
+        *out = s;
+    }
+}
+
+// ------------------------------------------------------------------ Adam
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// BF16 copies of a 3x3 layer: Wb[co][tap][ci] and the input-gradient form
+// Wt[ci][8 - tap][co]
+__global__ void k_refresh_w(const float* __restrict__ Wm, int Cout, int Cin, bf16* __restrict__ Wb,
+                            bf16* __restrict__ Wt) {
+    const long long n = (long long)Cout * 9 * Cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % Cin);
+        const long long r = i / Cin;
+        const int tap = (int)(r % 9);
+        const int co = (int)(r / 9);
+        const bf16 b = __float2bfloat16_rn(Wm[i]);
+        Wb[i] = b;
+        Wt[((long long)ci * 9 + (8 - tap)) * Cout + co] = b;
+    }
+}
+
+// ------------------------------------------------------ warm-start handoff
+struct WarmArgs {
+    const float* pred;
+    double rho_mid, rho_scale, rho_floor, t_mid, t_scale, Tc;
+    const double* rho0;
+    const double* T0;
+    double* rho;
+    double* T;
+    long long P;  // sites per case
+};
+
+__device__ __forceinline__ void warm_hat(const WarmArgs& a, long long i, double& r, double& t) {
+    r = fmax(a.rho_mid + a.rho_scale * (double)a.pred[2 * i], a.rho_floor);
+    t = a.Tc * (a.t_mid + a.t_scale * (double)a.pred[2 * i + 1]);
+}
+
+// one block per case: S0 = sum rho0, S1 = sum rho_hat, E0 = sum rho0 T0,
+// Q = sum rho_hat T_hat (fixed-order block reduction), then the outputs
+__global__ void __launch_bounds__(256) k_warm(WarmArgs a) {
+    __shared__ double red[4][256];
+    const long long base = (long long)blockIdx.x * a.P;
+    double s[4] = {0, 0, 0, 0};
+    for (long long i = threadIdx.x; i < a.P; i += 256) {
+        double r, t;
+        warm_hat(a, base + i, r, t);
+        s[0] += a.rho0[base + i];
+        s[1] += r;
+        s[2] += a.rho0[base + i] * a.T0[base + i];
+        s[3] += r * t;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    const double fr = red[0][0] / red[1][0];
+    const double ft = red[2][0] / (fr * red[3][0]);
+    for (long long i = threadIdx.x; i < a.P; i += 256) {
+        double r, t;
+        warm_hat(a, base + i, r, t);
+        a.rho[base + i] = r * fr;
+        a.T[base + i] = t * ft;
+    }
+}
+
+}  // namespace unk
