@@ -243,19 +243,35 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 # --------------------------------------------------- warm-start handoff
-def denormalise(y, rho_mid, rho_scale, t_mid, t_scale, Tc, rho_floor=1e-4):
-    """Network output -> (rho_hat, T_hat) fields; rho_hat is kept >= rho_floor
-    (the method needs a positive density everywhere)."""
+def denormalise(y, rho_mid, rho_scale, t_dev_scale, T0, rho_floor=1e-4):
+    """Network output -> (rho_hat, T_hat): rho_hat = max(rho_mid + rho_scale y0,
+    rho_floor) (the method needs a positive density), T_hat = T0 (1 + t_dev_scale y1)
+    (the temperature output is the relative deviation from the initial T0)."""
     return (np.maximum(rho_mid + rho_scale * y[..., 0], rho_floor),
-            Tc * (t_mid + t_scale * y[..., 1]))
+            T0 * (1.0 + t_dev_scale * y[..., 1]))
 
 
 def warm_project(rho_hat, T_hat, rho0, T0):
-    """Per sample: scale rho_hat so that sum rho_hat = sum rho0 (mass, Eq. 13
-    conserved by the method), then scale T_hat so that
-    sum rho_hat T_hat = sum rho0 T0 (energy; sum C_i = 0 keeps it under Eq. 24)."""
+    """Per case, match the mass (Eq. 13) and energy (sum C_i = 0 under Eq. 24)
+    of the initial state:
+    1. move mass inside the interfaces: rho1 = rho_hat + lam w with the
+       interface weight w = (rho_hat - lo)(hi - rho_hat), lo/hi the case's
+       extreme predicted densities (w = 0 in both bulk phases), and
+       lam = (sum rho0 - sum rho_hat) / sum w, limited to |lam| (hi - lo) <= 1
+       so that rho1 stays within [lo, hi] (lam = 0 if sum w = 0);
+    2. rho = rho1 sum(rho0) / sum(rho1) (exact mass whatever step 1 left);
+    3. T = T_hat sum(rho0 T0) / sum(rho T_hat)."""
     ax = tuple(range(1, rho_hat.ndim))
-    r = rho_hat * (rho0.sum(axis=ax, keepdims=True) / rho_hat.sum(axis=ax, keepdims=True))
+    lo = rho_hat.min(axis=ax, keepdims=True)
+    hi = rho_hat.max(axis=ax, keepdims=True)
+    w = (rho_hat - lo) * (hi - rho_hat)
+    S0 = rho0.sum(axis=ax, keepdims=True)
+    SW = w.sum(axis=ax, keepdims=True)
+    lam = np.where(SW > 0, (S0 - rho_hat.sum(axis=ax, keepdims=True)) / np.where(SW > 0, SW, 1.0), 0.0)
+    cap = 1.0 / np.where(hi > lo, hi - lo, 1.0)
+    lam = np.clip(lam, -cap, cap)
+    r1 = rho_hat + lam * w
+    r = r1 * (S0 / r1.sum(axis=ax, keepdims=True))
     e0 = (rho0 * T0).sum(axis=ax, keepdims=True)
     T = T_hat * (e0 / (r * T_hat).sum(axis=ax, keepdims=True))
     return r, T

@@ -35,6 +35,59 @@ CS_RHOC = 0.130443
 RHO_LIQUID = 0.35
 RHO_GAS = 0.03
 
+#: Liquid-vapour coexistence of the Carnahan-Starling EOS (a = 1, b = 4,
+#: R = 1) by Maxwell's equal-area construction: (T/T_c, rho_g, rho_l).
+#: Written by ``python -m oracle.coexistence``; the seeded sweep starts each
+#: droplet or slab at these densities.
+COEXISTENCE_CS = (
+    (0.60, 0.003081458539929346, 0.40620413975436337),
+    (0.61, 0.0034997542027268625, 0.4014427889164023),
+    (0.62, 0.003957347577293854, 0.39667751203982027),
+    (0.63, 0.004456311234053168, 0.3919060639255548),
+    (0.64, 0.004998765384390647, 0.38712614902380965),
+    (0.65, 0.005586886973241947, 0.3823354103809645),
+    (0.66, 0.0062229202616471595, 0.3775314175849033),
+    (0.67, 0.006909189021726869, 0.3727116535129428),
+    (0.68, 0.007648110510058689, 0.36787349965044014),
+    (0.69, 0.008442211437681275, 0.36301421970323666),
+    (0.70, 0.009294146218119775, 0.35813094117095823),
+    (0.71, 0.010206717851948169, 0.3532206344776867),
+    (0.72, 0.011182901901625615, 0.34828008916736725),
+    (0.73, 0.012225874129302991, 0.34330588655791816),
+    (0.74, 0.013339042520686866, 0.3382943681025933),
+    (0.75, 0.014526084610435294, 0.3332415985191704),
+    (0.76, 0.015790991273582196, 0.328143322502446),
+    (0.77, 0.01713811847365384, 0.3229949135127225),
+    (0.78, 0.018572248890532, 0.3177913127035731),
+    (0.79, 0.020098665931519172, 0.3125269554742717),
+    (0.80, 0.021723243418436067, 0.3071956823451157),
+    (0.81, 0.023452555332236853, 0.30179062976703364),
+    (0.82, 0.025294011520760037, 0.2963040949543186),
+    (0.83, 0.02725602744411192, 0.2907273666617526),
+    (0.84, 0.029348239174172765, 0.28505051068649256),
+    (0.85, 0.031581779506976666, 0.27926209423373366),
+    (0.86, 0.03396963805744112, 0.2733488262751818),
+    (0.87, 0.03652713905616116, 0.2672950801797546),
+    (0.88, 0.03927258783124093, 0.26108224763314025),
+    (0.89, 0.042228165302860006, 0.254687844518532),
+    (0.90, 0.04542119807150263, 0.2480842411779343),
+    (0.91, 0.04888601735264928, 0.24123680380179505),
+    (0.92, 0.05266677984293328, 0.23410107386271845),
+    (0.93, 0.05682194002225034, 0.22661829608964376),
+    (0.94, 0.06143173695676035, 0.2187079319185452),
+    (0.95, 0.06661162923820178, 0.21025422478526803),
+)
+
+
+def coexistence_densities(T_over_Tc):
+    """(rho_g, rho_l) at T/T_c, linearly interpolated in COEXISTENCE_CS (0.60..0.95)."""
+    t = np.array([r[0] for r in COEXISTENCE_CS])
+    if not (t[0] - 1e-12 <= T_over_Tc <= t[-1] + 1e-12):
+        raise ValueError(f"T/T_c = {T_over_Tc} outside the table")
+    g = float(np.interp(T_over_Tc, t, [r[1] for r in COEXISTENCE_CS]))
+    l = float(np.interp(T_over_Tc, t, [r[2] for r in COEXISTENCE_CS]))
+    return g, l
+
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -127,7 +180,7 @@ class Domain:
 
 
 def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_TC,
-                  fixed_L=None, L_multiple=4):
+                  fixed_L=None, L_multiple=4, densities="coexistence"):
     """Parameter sweep of independent periodic square domains.
 
     Per domain d (stream index 16 d + k of the counter-based generator):
@@ -135,7 +188,9 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
     of FP32 populations is then a whole number of 16-byte units),
     T/T_c ~ U[0.6, 0.95], G ~ U[-1.2, -0.8],
     tau_f ~ U[0.6, 1.2], tau_g fixed; droplet (radius U[L/8, L/4]) or slab
-    (width U[L/4, L/2]) from a fair coin.
+    (width U[L/4, L/2]) from a fair coin.  densities="coexistence" starts the
+    liquid and the vapour at the EOS coexistence densities of the domain's
+    T/T_c (COEXISTENCE_CS); "fixed" at RHO_LIQUID / RHO_GAS.
     """
     out = []
     for d in range(n_domains):
@@ -146,15 +201,16 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
         T_over = 0.6 + 0.35 * u[1]
         G = -1.2 + 0.4 * u[2]
         tau_f = 0.6 + 0.6 * u[3]
+        rg, rl = coexistence_densities(T_over) if densities == "coexistence" else (RHO_GAS, RHO_LIQUID)
         if u[4] < 0.5:
             kind = "droplet"
             size = L / 8 + (L / 4 - L / 8) * u[5]
-            rho, _ = droplet_fields(L, L, size)
+            rho, _ = droplet_fields(L, L, size, rho_l=rl, rho_g=rg)
         else:
             kind = "slab"
             size = L / 4 + (L / 2 - L / 4) * u[5]
             w = max(2, 2 * int(size / 2))
-            rho, _ = slab_fields(L, L, width=w, noise=0.0)
+            rho, _ = slab_fields(L, L, width=w, rho_l=rl, rho_g=rg, noise=0.0)
         T = np.full((L, L), T_over * Tc)
         out.append(Domain(L, float(T_over), float(G), float(tau_f), float(tau_g), kind,
                           float(size), rho, T))
@@ -164,8 +220,9 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
 # ------------------------------------------------------- warm-start network
 #: Normalisation of the network's input planes and outputs:
 #: input (T/T_c - t_mid)/t_scale, (G - g_mid)/g_scale, 2 mask - 1;
-#: output rho = rho_mid + rho_scale y0, T/T_c = t_mid + t_scale y1.
-UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_mid=0.2, rho_scale=0.2)
+#: output rho = rho_mid + rho_scale y0, T = T0 (1 + t_dev_scale y1).
+UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_mid=0.2, rho_scale=0.2,
+                 t_dev_scale=0.01)
 
 
 def normal01(seed: int, index: np.ndarray) -> np.ndarray:
@@ -204,10 +261,15 @@ def unet_input_planes(T_over_Tc, G, mask) -> np.ndarray:
                     axis=3).astype(np.float32)
 
 
-def unet_target_planes(rho, T, Tc=CS_TC) -> np.ndarray:
-    """Normalised training targets [N, H, W, 2] float32 from steady rho, T fields."""
-    r = (np.asarray(rho) - UNET_NORM["rho_mid"]) / UNET_NORM["rho_scale"]
-    t = (np.asarray(T) / Tc - UNET_NORM["t_mid"]) / UNET_NORM["t_scale"]
+def unet_target_planes(rho, T, T0) -> np.ndarray:
+    """Normalised training targets [N, H, W, 2] float32 from steady rho, T fields
+    and the cases' initial temperatures T0 (scalars [N] or fields)."""
+    r = (np.asarray(rho, dtype=np.float64) - UNET_NORM["rho_mid"]) / UNET_NORM["rho_scale"]
+    T = np.asarray(T, dtype=np.float64)
+    T0 = np.asarray(T0, dtype=np.float64)
+    if T0.ndim == 1:
+        T0 = T0.reshape(-1, 1, 1)
+    t = (T / T0 - 1.0) / UNET_NORM["t_dev_scale"]
     return np.stack([r, t], axis=-1).astype(np.float32)
 
 
@@ -215,5 +277,5 @@ def warm_start_cases(n, L=256, seed=5):
     """n sweep cases at a fixed L x L (the batched sweep's parameter
     distributions); returns the domains and their initial liquid masks."""
     doms = batched_sweep(n_domains=n, seed=seed, fixed_L=L)
-    masks = np.stack([(d.rho > 0.5 * (RHO_LIQUID + RHO_GAS)).astype(np.float32) for d in doms])
+    masks = np.stack([(d.rho > 0.5 * (d.rho.max() + d.rho.min())).astype(np.float32) for d in doms])
     return doms, masks

@@ -187,7 +187,31 @@ def test_warm_project_conserves_mass_and_energy():
     assert np.allclose(rho.sum(axis=(1, 2)), rho0.sum(axis=(1, 2)), rtol=1e-14)
     assert np.allclose((rho * T).sum(axis=(1, 2)), (rho0 * T0).sum(axis=(1, 2)), rtol=1e-14)
     same = U.warm_project(rho0, T0, rho0, T0)
-    assert np.allclose(same[0], rho0, rtol=1e-15) and np.allclose(same[1], T0, rtol=1e-15)
+    assert np.allclose(same[0], rho0, rtol=1e-14) and np.allclose(same[1], T0, rtol=1e-14)
+
+
+def test_warm_project_moves_interfaces_not_bulk():
+    """A smooth slab predicted about one site too wide: the correction lands in
+    the two interfaces and leaves both bulk densities untouched."""
+    L = 64
+    x = np.arange(L) + 0.5
+    def slab(half):
+        return (0.165 + 0.135 * np.tanh((half - np.abs(x - 32)) / 2.0))[None, None, :].repeat(L, axis=1)
+    rho0, pred = slab(12.0), slab(12.5)
+    T0 = np.full_like(rho0, 0.08)
+    rho, _ = U.warm_project(pred, T0, rho0, T0)
+    assert np.isclose(rho.sum(), rho0.sum(), rtol=1e-14)
+    bulk = (np.abs(x - 32) < 2) | (np.abs(x - 32) > 26)
+    assert np.abs(rho[0][:, bulk] - pred[0][:, bulk]).max() < 1e-4
+    assert np.abs(rho - rho0).max() < 0.2 * np.abs(pred - rho0).max()
+    assert rho.min() >= pred.min() - 1e-15 and rho.max() <= pred.max() + 1e-15
+
+
+def test_denormalise():
+    y = np.array([[[[0.5, 2.0], [-3.0, 0.0]]]])
+    T0 = np.full((1, 1, 2), 0.08)
+    r, T = U.denormalise(y, 0.2, 0.2, 0.01, T0, rho_floor=1e-4)
+    assert np.allclose(r, [[[0.3, 1e-4]]]) and np.allclose(T, [[[0.08 * 1.02, 0.08]]])
 
 
 def test_initial_parameters_recipe():
