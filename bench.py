@@ -18,6 +18,13 @@ ranks.  ``e2e`` repeats the job through the public C ABI from pinned host
 buffers: lb_init (upload of rho0, T0 and the equilibrium start) + SEG*K steps
 + lb_moments (download of rho, u, T), wall-clocked.
 
+``sweep`` (after the timed region, not part of ``value``): the batched
+solver on 256 seeded domains of the sweep recipe (L ~ U{64..512}, T/T_c,
+G, tau_f drawn per domain), one persistent kernel per step with autotuned
+work-list granularity, run to residual < 1e-8 with a step cap: batched MLUPS
+and the wall-clock time to steady state, with converged / failed / capped
+counts.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs its own lattice: weak scaling, no
 data-path collective (independent problems).
@@ -244,6 +251,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nx", type=int, default=NX, help="lattice side (profiling: small case)")
     ap.add_argument("--seg", type=int, default=SEG, help="LB time steps per bench step")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep run to steady state")
+    ap.add_argument("--sweep-cap", type=int, default=60000, help="step cap of the batched sweep")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -304,11 +313,61 @@ def main():
     if not args.no_variants:
         variants = run_variants(lb, torch, rho, T, stream, sites)
 
+    # ---- the batched sweep (256 domains) run to steady state
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(lb, torch, dist, world, rank, args)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    return report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites)
+    return report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep)
+
+
+def run_sweep(lb, torch, dist, world, rank, args):
+    """256 seeded domains (L ~ U{64..512}), FP32, Eq. (24), beta 1.3, psi from T0;
+    domains are dealt round-robin to the ranks (no exchange).  Times one batched
+    step (autotuned row chunks) and the run to residual < 1e-8 (K = 100)."""
+    from paper_1405_2232_gb300 import inputs as I
+    doms = I.batched_sweep()[rank::world]
+    params = [lb.lb_params_default(nx=d.L, ny=d.L, tau_f=d.tau_f, tau_g=d.tau_g, G=d.G, beta=BETA,
+                                   precision="fp32", psi_uses_local_T=0, T_psi=d.T_over_Tc * I.CS_TC)
+              for d in doms]
+    sites = sum(q.nx * q.ny for q in params)
+    with lb.Batch(params, [d.rho for d in doms], [d.T for d in doms]) as B:
+        rows, _ = B.autotune(20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.step(200)
+        B.check()  # synchronises
+        t_step = (time.perf_counter() - t0) / 200
+    with lb.Batch(params, [d.rho for d in doms], [d.T for d in doms]) as B:
+        B.chunk_rows = rows
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        steps, resid, st = B.run(1e-8, K=100, max_steps=args.sweep_cap)
+        wall = time.perf_counter() - t0
+    res = torch.tensor([wall, float(np.sum(st == 0)), float(np.sum((st != 0) & (st != 8))),
+                        float(np.sum(st == 8)), float(sites)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = res.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(res, op=dist.ReduceOp.SUM)
+        res[0] = mx[0]
+    wall, conv, fail, capped, tot_sites = res.tolist()
+    ok = st == 0
+    return {"workload": "256 periodic domains, L~U{64..512} (multiple of 4), T/Tc~U[0.6,0.95], "
+                        "G~U[-1.2,-0.8], tau_f~U[0.6,1.2], droplet/slab, seed 4; FP32, Eq.24, beta 1.3, "
+                        "psi(rho, T0)",
+            "sites": int(tot_sites), "chunk_rows": rows,
+            "batched_step_ms": round(t_step * 1e3, 3),
+            "batched_MLUPS": round(world * sites / t_step / 1e6, 1),
+            "tol": 1e-8, "K": 100, "max_steps": args.sweep_cap,
+            "time_to_steady_s": round(wall, 2),
+            "converged": int(conv), "failed": int(fail), "capped": int(capped),
+            "median_steps_converged_rank0": float(np.median(steps[ok])) if ok.any() else None}
 
 
 def run_e2e(lb, torch, dist, p, rho, T, stream, args):
@@ -357,7 +416,7 @@ def run_variants(lb, torch, rho, T, stream, sites):
     return variants
 
 
-def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites):
+def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep=None):
     peak, peak_kind = peaks()
     achieved = alg_bytes / launch_s / 1e9
     cpu = None
@@ -397,6 +456,7 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
         "clocks": clocks,
         "totals_after": {"mass": tot[0], "energy": tot[1]},
         "variants": variants,
+        "sweep": sweep,
     }
     print(json.dumps(out))
     if args.dist:

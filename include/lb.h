@@ -204,7 +204,8 @@ lb_status lb_autotune(const lb_params* p, int32_t steps, void* stream, lb_params
 typedef struct lb_batch lb_batch; /* opaque; owned by the library */
 
 /* Create a batch of n domains; params[d] describes domain d, rho0[d] and T0[d]
- * are its host float64 fields [ny][nx] (copied).  Initial state as lb_init. */
+ * are its float64 fields [ny][nx], in host or device memory (copied; the
+ * copy direction follows from unified addressing).  Initial state as lb_init. */
 lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const* rho0,
                         const double* const* T0, void* stream, lb_batch** out);
 

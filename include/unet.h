@@ -124,19 +124,27 @@ lb_status un_synchronize(un_net* net);
 /* Release the net.  NULL is accepted. */
 lb_status un_free(un_net* net);
 
-/* Warm-start handoff for N cases of H x W sites (all pointers device):
- * rho_hat = max(rho_mid + rho_scale y0, rho_floor),
- * T_hat = Tc (t_mid + t_scale y1) from the prediction d_pred [N][H][W][2];
- * then per case rho = rho_hat * sum(rho0) / sum(rho_hat) (mass of the
- * initial state, Eq. 13) and T = T_hat * sum(rho0 T0) / sum(rho T_hat)
- * (its energy).  d_rho0, d_T0: the case's initial fields (float64
- * [N][H][W]); d_rho, d_T: float64 outputs of the same shape, ready for
- * lb_init_device / lb_batch_init.  Sums in FP64, fixed order.
- * Asynchronous on `stream`. */
+/* Warm-start handoff for N cases of H x W sites (all pointers device).
+ * From the prediction d_pred [N][H][W][2]:
+ *   rho_hat = max(rho_mid + rho_scale y0, rho_floor),
+ *   T_hat = T0 (1 + t_dev_scale y1)  (the T output is the relative deviation
+ *   from the case's initial temperature).
+ * Per case, with lo/hi the extreme values of rho_hat:
+ *   1. rho1 = rho_hat + lam (rho_hat - lo)(hi - rho_hat): mass moved inside
+ *      the interfaces only (the weight vanishes in both bulk phases), with
+ *      lam = (sum rho0 - sum rho_hat) / sum of the weight, limited to
+ *      |lam| (hi - lo) <= 1 so that rho1 stays within [lo, hi];
+ *   2. rho = rho1 sum(rho0) / sum(rho1): exactly the initial mass (Eq. 13);
+ *   3. T = T_hat sum(rho0 T0) / sum(rho T_hat): the initial energy (conserved
+ *      under Eq. 24, sum_i C_i = 0).
+ * d_rho0, d_T0: the case's initial fields (float64 [N][H][W]); d_rho, d_T:
+ * float64 outputs of the same shape, ready for lb_init_device / lb_batch_init.
+ * One block per case, sums in FP64 in a fixed order.  Asynchronous on
+ * `stream`.  LB_ERR_ARG for NULL pointers or empty sizes. */
 lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_mid,
-                         double rho_scale, double rho_floor, double t_mid, double t_scale,
-                         double Tc, const double* d_rho0, const double* d_T0, double* d_rho,
-                         double* d_T, void* stream);
+                         double rho_scale, double rho_floor, double t_dev_scale,
+                         const double* d_rho0, const double* d_T0, double* d_rho, double* d_T,
+                         void* stream);
 
 #ifdef __cplusplus
 }

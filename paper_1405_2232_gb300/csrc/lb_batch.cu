@@ -369,8 +369,9 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         const size_t nb = sizeof(double) * (size_t)params[d].nx * params[d].ny;
         double* r = b->d_ref_rho + b->doms[d].fld_off;
         double* tt = b->d_ref_T + b->doms[d].fld_off;
-        e = cudaMemcpyAsync(r, rho0[d], nb, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(tt, T0[d], nb, cudaMemcpyHostToDevice, b->stream);
+        // host or device sources (unified addressing decides the direction)
+        e = cudaMemcpyAsync(r, rho0[d], nb, cudaMemcpyDefault, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tt, T0[d], nb, cudaMemcpyDefault, b->stream);
         if (e == cudaSuccess) {
             const KParams& k = b->doms[d].kp;
             if (prec == LB_PREC_FP32)

@@ -233,6 +233,7 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
     a.W = Wl(n, l);
     a.chunks_per_split = cps;
     a.part = n->wpart;
+    a.bpart = n->bpart;
     const dim3 grid(tiles, splits);
     if (MT == 32 && NT == 32) unk::k_wgrad<32, 32><<<grid, 256, 0, n->stream>>>(a);
     else if (MT == 32) unk::k_wgrad<32, 64><<<grid, 256, 0, n->stream>>>(a);
@@ -240,13 +241,8 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
     else unk::k_wgrad<64, 64><<<grid, 256, 0, n->stream>>>(a);
     const long long nw = (long long)L.cout * 9 * L.cin;
     unk::k_sum_splits<<<grid_for(nw), 256, 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
-    // bias: per-block partials over pixel ranges, then a fixed-order sum
-    int nb = (int)((M + 255) / 256);
-    if (nb > 1024) nb = 1024;
-    const int rows = (int)((M + nb - 1) / nb);
-    nb = (int)((M + rows - 1) / rows);
-    unk::k_bias_partial<<<nb, 256, 0, n->stream>>>(g, gC, goff, L.cout, (int)M, rows, n->bpart);
-    unk::k_sum_splits<<<1, 256, 0, n->stream>>>(n->bpart, nb, L.cout, n->grad + L.boff);
+    // bias: partials of the centre-tap CTAs, summed over the splits in order
+    unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
     return cudaGetLastError();
 }
 
@@ -331,8 +327,8 @@ cudaError_t backward(un_net* n, int N, const float* d_target) {
             break;
         default: return cudaErrorInvalidValue;
     }
-    unk::k_sum_splits<<<1, 256, 0, n->stream>>>(n->hpart, hb, 2LL * C + 2, n->grad + H.woff);
-    unk::k_sum_doubles<<<1, 32, 0, n->stream>>>(n->lpart, hb, n->d_loss);
+    unk::k_sum_splits_wide<<<2 * C + 2, 256, 0, n->stream>>>(n->hpart, hb, 2LL * C + 2, n->grad + H.woff);
+    unk::k_sum_doubles<<<1, 256, 0, n->stream>>>(n->lpart, hb, n->d_loss);
     // decoder, finest level first
     for (int l = 0; l < LV - 1; ++l) {
         const bf16* gin = l == 0 ? n->gd0 : n->gup[l];
@@ -631,8 +627,8 @@ lb_status un_free(un_net* n) {
 }
 
 lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_mid, double rho_scale,
-                         double rho_floor, double t_mid, double t_scale, double Tc, const double* d_rho0,
-                         const double* d_T0, double* d_rho, double* d_T, void* stream) {
+                         double rho_floor, double t_dev_scale, const double* d_rho0, const double* d_T0,
+                         double* d_rho, double* d_T, void* stream) {
     if (N < 1 || H < 1 || W < 1 || !d_pred || !d_rho0 || !d_T0 || !d_rho || !d_T)
         return uerr(LB_ERR_ARG, "un_warm_fields: invalid argument");
     unk::WarmArgs a;
@@ -640,9 +636,7 @@ lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, d
     a.rho_mid = rho_mid;
     a.rho_scale = rho_scale;
     a.rho_floor = rho_floor;
-    a.t_mid = t_mid;
-    a.t_scale = t_scale;
-    a.Tc = Tc;
+    a.t_dev_scale = t_dev_scale;
     a.rho0 = d_rho0;
     a.T0 = d_T0;
     a.rho = d_rho;

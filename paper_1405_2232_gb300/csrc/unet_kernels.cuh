@@ -226,6 +226,7 @@ struct WgradArgs {
     int Cout, Cin, N, H, W;
     int chunks_per_split;  // 32-pixel chunks per split (blockIdx.y)
     float* part;           // [splits][Cout][9][Cin]
+    float* bpart;          // [splits][Cout]: bias gradient partials (centre-tap CTAs of ci tile 0)
 };
 
 template <int MT, int NT>
@@ -277,6 +278,8 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[ni][k] = 0.0f;
     const int q = lane >> 3, rr = lane & 7;
+    const bool do_bias = tap == 4 && cit == 0;
+    float bsum = 0.0f;
     if (c_begin < c_end) {
         load(c_begin, 0);
         cp_async_commit();
@@ -291,6 +294,9 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
             cp_async_wait<0>();
         }
         __syncthreads();
+        if (do_bias && tid < MT)
+#pragma unroll 8
+            for (int px = 0; px < 32; ++px) bsum += __bfloat162float(sG[s][px * LG + tid]);
 #pragma unroll
         for (int kk = 0; kk < 32; kk += 16) {
             uint32_t af[4];
@@ -305,6 +311,7 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
         }
         __syncthreads();
     }
+    if (do_bias && tid < MT) a.bpart[(long long)blockIdx.y * a.Cout + co0 + tid] = bsum;
     const int g = lane >> 2, t4 = lane & 3;
     float* out = a.part + (long long)blockIdx.y * a.Cout * 9 * a.Cin;
 #pragma unroll
@@ -326,6 +333,23 @@ __global__ void k_sum_splits(const float* __restrict__ part, int splits, long lo
         for (int k = 0; k < splits; ++k) s += part[(long long)k * n + i];
         out[i] = s;
     }
+}
+
+// out[i] = sum_s part[s * n + i] for few outputs and many partials: one block
+// per output, a strided per-thread sum and a fixed-order tree (deterministic)
+__global__ void __launch_bounds__(256) k_sum_splits_wide(const float* __restrict__ part, int splits, long long n,
+                                                          float* __restrict__ out) {
+    __shared__ float red[256];
+    const long long i = blockIdx.x;
+    float s = 0.0f;
+    for (int k = threadIdx.x; k < splits; k += 256) s += part[(long long)k * n + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = red[0];
 }
 
 // bias gradient partials: part[block][co] = sum over the block's pixels of g[p][co]
@@ -562,12 +586,18 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ h, co
     }
 }
 
-__global__ void k_sum_doubles(const double* __restrict__ part, int n, double* __restrict__ out) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += part[k];
-        *out = s;
+// *out = sum of n doubles: strided per-thread sums, fixed-order tree (one block of 256)
+__global__ void __launch_bounds__(256) k_sum_doubles(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += part[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // ------------------------------------------------------------------ Adam
@@ -603,7 +633,7 @@ __global__ void k_refresh_w(const float* __restrict__ Wm, int Cout, int Cin, bf1
 // ------------------------------------------------------ warm-start handoff
 struct WarmArgs {
     const float* pred;
-    double rho_mid, rho_scale, rho_floor, t_mid, t_scale, Tc;
+    double rho_mid, rho_scale, rho_floor, t_dev_scale;
     const double* rho0;
     const double* T0;
     double* rho;
@@ -611,41 +641,79 @@ struct WarmArgs {
     long long P;  // sites per case
 };
 
-__device__ __forceinline__ void warm_hat(const WarmArgs& a, long long i, double& r, double& t) {
-    r = fmax(a.rho_mid + a.rho_scale * (double)a.pred[2 * i], a.rho_floor);
-    t = a.Tc * (a.t_mid + a.t_scale * (double)a.pred[2 * i + 1]);
+__device__ __forceinline__ double warm_rho_hat(const WarmArgs& a, long long i) {
+    return fmax(a.rho_mid + a.rho_scale * (double)a.pred[2 * i], a.rho_floor);
+}
+__device__ __forceinline__ double warm_T_hat(const WarmArgs& a, long long i) {
+    return a.T0[i] * (1.0 + a.t_dev_scale * (double)a.pred[2 * i + 1]);
 }
 
-// one block per case: S0 = sum rho0, S1 = sum rho_hat, E0 = sum rho0 T0,
-// Q = sum rho_hat T_hat (fixed-order block reduction), then the outputs
-__global__ void __launch_bounds__(256) k_warm(WarmArgs a) {
-    __shared__ double red[4][256];
-    const long long base = (long long)blockIdx.x * a.P;
-    double s[4] = {0, 0, 0, 0};
-    for (long long i = threadIdx.x; i < a.P; i += 256) {
-        double r, t;
-        warm_hat(a, base + i, r, t);
-        s[0] += a.rho0[base + i];
-        s[1] += r;
-        s[2] += a.rho0[base + i] * a.T0[base + i];
-        s[3] += r * t;
-    }
+// fixed-order block reduction of NV values (sum, or min/max where asked)
+template <int NV>
+__device__ void block_reduce(double (&v)[NV], double (*red)[256], const int (&op)[NV]) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = v[k];
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+            for (int k = 0; k < NV; ++k) {
+                const double a = red[k][threadIdx.x], b = red[k][threadIdx.x + w];
+                red[k][threadIdx.x] = op[k] == 0 ? a + b : (op[k] < 0 ? fmin(a, b) : fmax(a, b));
+            }
         __syncthreads();
     }
-    const double fr = red[0][0] / red[1][0];
-    const double ft = red[2][0] / (fr * red[3][0]);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = red[k][0];
+    __syncthreads();
+}
+
+// One block per case.  Mass is moved inside the interfaces with the weight
+// w = (rho_hat - lo)(hi - rho_hat) (zero in both bulk phases), then a final
+// scaling makes it exact; T is scaled to the initial energy.
+__global__ void __launch_bounds__(256) k_warm(WarmArgs a) {
+    __shared__ double red[5][256];
+    const long long base = (long long)blockIdx.x * a.P;
+    // pass 1: S0 = sum rho0, S1 = sum rho_hat, E0 = sum rho0 T0, lo, hi
+    double v1[5] = {0.0, 0.0, 0.0, INFINITY, -INFINITY};
     for (long long i = threadIdx.x; i < a.P; i += 256) {
-        double r, t;
-        warm_hat(a, base + i, r, t);
-        a.rho[base + i] = r * fr;
-        a.T[base + i] = t * ft;
+        const double r = warm_rho_hat(a, base + i);
+        v1[0] += a.rho0[base + i];
+        v1[1] += r;
+        v1[2] += a.rho0[base + i] * a.T0[base + i];
+        v1[3] = fmin(v1[3], r);
+        v1[4] = fmax(v1[4], r);
+    }
+    const int op1[5] = {0, 0, 0, -1, 1};
+    block_reduce<5>(v1, red, op1);
+    const double S0 = v1[0], S1 = v1[1], E0 = v1[2], lo = v1[3], hi = v1[4];
+    // pass 2: SW = sum w
+    double v2[1] = {0.0};
+    for (long long i = threadIdx.x; i < a.P; i += 256) {
+        const double r = warm_rho_hat(a, base + i);
+        v2[0] += (r - lo) * (hi - r);
+    }
+    const int op2[1] = {0};
+    block_reduce<1>(v2, red, op2);
+    double lam = v2[0] > 0.0 ? (S0 - S1) / v2[0] : 0.0;
+    const double cap = hi > lo ? 1.0 / (hi - lo) : 1.0;
+    lam = fmin(fmax(lam, -cap), cap);
+    // pass 3: S2 = sum rho1, Q = sum rho1 T_hat
+    double v3[2] = {0.0, 0.0};
+    for (long long i = threadIdx.x; i < a.P; i += 256) {
+        const double r = warm_rho_hat(a, base + i);
+        const double r1 = r + lam * (r - lo) * (hi - r);
+        v3[0] += r1;
+        v3[1] += r1 * warm_T_hat(a, base + i);
+    }
+    const int op3[2] = {0, 0};
+    block_reduce<2>(v3, red, op3);
+    const double fr = S0 / v3[0];
+    const double ft = E0 / (fr * v3[1]);
+    for (long long i = threadIdx.x; i < a.P; i += 256) {
+        const double r = warm_rho_hat(a, base + i);
+        a.rho[base + i] = (r + lam * (r - lo) * (hi - r)) * fr;
+        a.T[base + i] = warm_T_hat(a, base + i) * ft;
     }
 }
 

@@ -286,14 +286,20 @@ def lb_version() -> str:
     return load().lb_version().decode()
 
 
-def lb_batch_init(params, rhos, Ts, stream=None):
-    """params: sequence of lb_params; rhos, Ts: host float64 fields per domain."""
+def lb_batch_init(params, rhos, Ts, stream=None, device_inputs=False):
+    """params: sequence of lb_params; rhos, Ts: float64 fields per domain (host
+    arrays, or device addresses / tensors with device_inputs=True)."""
     n = len(params)
     arr = (lb_params * n)(*params)
-    rhos = [_host(r, (p.ny, p.nx)) for r, p in zip(rhos, params)]
-    Ts = [_host(t, (p.ny, p.nx)) for t, p in zip(Ts, params)]
-    rp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(r) for r in rhos])
-    tp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(t) for t in Ts])
+    if device_inputs:
+        addr = lambda a: ctypes.cast(_addr(a), ctypes.POINTER(ctypes.c_double))
+        rp = (ctypes.POINTER(ctypes.c_double) * n)(*[addr(r) for r in rhos])
+        tp = (ctypes.POINTER(ctypes.c_double) * n)(*[addr(t) for t in Ts])
+    else:
+        rhos = [_host(r, (p.ny, p.nx)) for r, p in zip(rhos, params)]
+        Ts = [_host(t, (p.ny, p.nx)) for t, p in zip(Ts, params)]
+        rp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(r) for r in rhos])
+        tp = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(t) for t in Ts])
     b = ctypes.c_void_p()
     _check(load().lb_batch_init(arr, n, rp, tp, _stream(stream), ctypes.byref(b)))
     return b
@@ -374,10 +380,10 @@ def lb_batch_free(b):
 class Batch:
     """Owner of one batch of independent domains (see lb_batch_* in include/lb.h)."""
 
-    def __init__(self, params, rhos, Ts, stream=None):
+    def __init__(self, params, rhos, Ts, stream=None, device_inputs=False):
         self.params = list(params)
         self.n = len(self.params)
-        self.b = lb_batch_init(self.params, rhos, Ts, stream)
+        self.b = lb_batch_init(self.params, rhos, Ts, stream, device_inputs)
 
     def step(self, n=1):
         lb_batch_step(self.b, n)

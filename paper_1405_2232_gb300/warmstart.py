@@ -1,0 +1,242 @@
+"""Learned warm start of the batched steady-state solve.
+
+Pipeline (every numerical step runs in the CUDA library):
+
+1. ``generate``: run sweep cases (``inputs.warm_start_cases``: T/T_c, G,
+   tau_f from the batched sweep's distributions, droplet or slab, fixed L x L)
+   to steady state with the batched solver; the converged states are the
+   training targets.
+2. ``train``: fit the U-Net (include/unet.h) to map (T/T_c, G, initial liquid
+   mask) to the steady (rho, T), with Adam on shuffled mini-batches.
+3. ``evaluate``: on unseen cases, solve once from the plain initial state and
+   once from the network's prediction (handoff ``un_warm_fields``: density and
+   temperature rescaled to the initial mass and energy), both with the same
+   batched solver and residual test; report wall-clock seconds and steps.
+
+Run as ``python -m paper_1405_2232_gb300.warmstart [--train N] [--test N]``;
+it prints one JSON object.  The sweep recipe: psi from the domain's T0
+(passive temperature), the mixed force of Eq. (4) with beta = 1.3, Eq. (24)
+for g, FP32 storage, tau_g = 0.8.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import lb
+from . import unet as UN
+
+BETA = 1.3
+TOL = 1e-8
+K = 100
+
+
+def sweep_params(doms, thermal=lb.LB_THERMAL_EQ24, precision="fp32"):
+    return [lb.lb_params_default(nx=d.L, ny=d.L, tau_f=d.tau_f, tau_g=d.tau_g, G=d.G, beta=BETA,
+                                 thermal=thermal, precision=precision, psi_uses_local_T=0,
+                                 T_psi=d.T_over_Tc * I.CS_TC) for d in doms]
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def solve(params, rhos, Ts, cap, device_inputs=False, chunk_rows=None):
+    """Batched run to r < TOL; returns steps, residual, status, wall seconds, batch."""
+    B = lb.Batch(params, rhos, Ts, device_inputs=device_inputs)
+    if chunk_rows:
+        B.chunk_rows = chunk_rows
+    t0 = time.perf_counter()
+    steps, resid, st = B.run(TOL, K=K, max_steps=cap)
+    return steps, resid, st, time.perf_counter() - t0, B
+
+
+def generate(n, L=256, seed=5, cap=40000, chunk_rows=None, near_tol=1e-6):
+    """Steady states of n sweep cases: (domains, masks, index, rho, T, info).
+
+    The targets are the converged cases plus those stopped by the step cap
+    with a residual below near_tol (their geometry has settled; what is left
+    is the slow decay of sound waves in the periodic box)."""
+    doms, masks = I.warm_start_cases(n, L=L, seed=seed)
+    params = sweep_params(doms)
+    steps, resid, st, wall, B = solve(params, [d.rho for d in doms], [d.T for d in doms], cap,
+                                      chunk_rows=chunk_rows)
+    ok = np.flatnonzero((st == lb.LB_OK) | ((st == lb.LB_ERR_NOT_CONVERGED) & (resid < near_tol)))
+    rho = np.empty((ok.size, L, L), dtype=np.float32)
+    T = np.empty((ok.size, L, L), dtype=np.float32)
+    for j, d in enumerate(ok):
+        r, t = B.fields(int(d))
+        rho[j], T[j] = r, t
+    B.close()
+    info = dict(cases=n, converged=int(np.sum(st == lb.LB_OK)), targets=int(ok.size), failed=int(np.sum((st != lb.LB_OK) & (st != lb.LB_ERR_NOT_CONVERGED))),
+                capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)), wall_s=wall,
+                median_steps=float(np.median(steps[st == lb.LB_OK])) if np.any(st == lb.LB_OK) else None)
+    return doms, masks, ok, rho, T, info
+
+
+def case_inputs(doms, masks):
+    return I.unet_input_planes([d.T_over_Tc for d in doms], [d.G for d in doms], masks)
+
+
+def train(X, Y, L, epochs=30, batch=16, lr=1e-3, seed=7, log=None, augment=True):
+    """Train a fresh network on device tensors X [n, L, L, 3], Y [n, L, L, 2]."""
+    import torch
+    net = UN.UNet(L, L, batch)
+    arch = [("", ci, co, k, (3 if i == 0 else ci)) for i, (ci, co, k, _) in enumerate(UN.layer_table(net.cfg))]
+    net.set_params(I.unet_init_params(arch, seed=11))
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    losses = []
+    per_epoch = max(1, n // batch)
+    total = epochs * per_epoch
+    step = 0
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        for s in range(0, n - batch + 1, batch):
+            idx = torch.from_numpy(order[s:s + batch]).to(X.device)
+            xb = X.index_select(0, idx)
+            yb = Y.index_select(0, idx)
+            if augment:
+                # the periodic box is invariant under shifts, reflections and
+                # the transposition of x and y: one random symmetry per batch
+                sh = (int(rng.integers(L)), int(rng.integers(L)))
+                xb, yb = torch.roll(xb, sh, dims=(1, 2)), torch.roll(yb, sh, dims=(1, 2))
+                for ax in (1, 2):
+                    if rng.random() < 0.5:
+                        xb, yb = torch.flip(xb, (ax,)), torch.flip(yb, (ax,))
+                if rng.random() < 0.5:
+                    xb, yb = xb.transpose(1, 2), yb.transpose(1, 2)
+            xb, yb = xb.contiguous(), yb.contiguous()
+            last = s + 2 * batch > n
+            # cosine decay from lr to lr / 20
+            lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * step / total)))
+            loss = net.train_step(xb, yb, batch, lr_t, want_loss=last)
+            step += 1
+        losses.append(loss)
+        if log:
+            log(f"epoch {ep}: loss {loss:.5f}")
+    net.synchronize()
+    return net, losses, time.perf_counter() - t0
+
+
+def predict(net, X, batch):
+    import torch
+    n, L = X.shape[0], X.shape[1]
+    out = torch.empty((n, L, L, 2), dtype=torch.float32, device=X.device)
+    for s in range(0, n, batch):
+        m = min(batch, n - s)
+        net.forward(X[s:s + m], out[s:s + m], m)
+    net.synchronize()
+    return out
+
+
+def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
+    import torch
+    dev = torch.device("cuda")
+    L = doms[0].L
+    params = sweep_params(doms)
+    rho0 = np.stack([d.rho for d in doms])
+    T0 = np.stack([d.T for d in doms])
+    # plain
+    steps_p, _, st_p, wall_p, Bp = solve(params, list(rho0), list(T0), cap, chunk_rows=chunk_rows)
+    ok_p = np.flatnonzero(st_p == lb.LB_OK)
+    ref = {int(d): Bp.fields(int(d)) for d in ok_p}
+    Bp.close()
+    # warm: inference + handoff + solve, all timed
+    X = torch.from_numpy(case_inputs(doms, masks)).to(dev)
+    d_rho0 = torch.from_numpy(rho0).to(dev)
+    d_T0 = torch.from_numpy(T0).to(dev)
+    _sync()
+    t0 = time.perf_counter()
+    pred = predict(net, X, batch)
+    d_rho = torch.empty_like(d_rho0)
+    d_T = torch.empty_like(d_T0)
+    UN.warm_fields(len(doms), L, L, pred, I.UNET_NORM, d_rho0, d_T0, d_rho, d_T)
+    _sync()
+    t_inf = time.perf_counter() - t0
+    stride = L * L * 8
+    rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
+    tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
+    steps_w, _, st_w, wall_w, Bw = solve(params, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
+    Bw.close()
+    # prediction error against the plain steady state
+    h_rho, h_T = d_rho.cpu().numpy(), d_T.cpu().numpy()
+    e_rho = [np.abs(h_rho[d] - ref[d][0]).max() / np.abs(ref[d][0]).max() for d in ref]
+    e_T = [np.abs(h_T[d] - ref[d][1]).max() / np.abs(ref[d][1]).max() for d in ref]
+    rms_rho = [float(np.sqrt(np.mean((h_rho[d] - ref[d][0]) ** 2))) for d in ref]
+    med_rho = [float(np.median(np.abs(h_rho[d] - ref[d][0]))) for d in ref]
+    rms_rho0 = [float(np.sqrt(np.mean((rho0[d] - ref[d][0]) ** 2))) for d in ref]
+    both = np.flatnonzero((st_p == lb.LB_OK) & (st_w == lb.LB_OK))
+    return dict(
+        cases=len(doms), L=L, cap=cap,
+        plain=dict(wall_s=wall_p, converged=int(ok_p.size), failed=int(np.sum((st_p != 0) & (st_p != 8))),
+                   capped=int(np.sum(st_p == 8))),
+        warm=dict(wall_s=wall_w + t_inf, solve_s=wall_w, inference_s=t_inf,
+                  converged=int(np.sum(st_w == 0)), failed=int(np.sum((st_w != 0) & (st_w != 8))),
+                  capped=int(np.sum(st_w == 8))),
+        both_converged=int(both.size),
+        median_steps_plain=float(np.median(steps_p[both])) if both.size else None,
+        median_steps_warm=float(np.median(steps_w[both])) if both.size else None,
+        steps_ratio=float(np.sum(steps_w[both]) / np.sum(steps_p[both])) if both.size else None,
+        prediction_error=dict(e_rho_median=float(np.median(e_rho)) if e_rho else None,
+                              e_T_median=float(np.median(e_T)) if e_T else None,
+                              e_rho_max=float(np.max(e_rho)) if e_rho else None,
+                              rms_rho_median=float(np.median(rms_rho)) if rms_rho else None,
+                              abs_rho_median_of_medians=float(np.median(med_rho)) if med_rho else None,
+                              rms_rho_initial_state_median=float(np.median(rms_rho0)) if rms_rho0 else None),
+        per_case=dict(T_over_Tc=[d.T_over_Tc for d in doms], tau_f=[d.tau_f for d in doms],
+                      kind=[d.kind for d in doms], steps_plain=steps_p.tolist(), status_plain=st_p.tolist(),
+                      steps_warm=steps_w.tolist(), status_warm=st_w.tolist(),
+                      e_rho={int(d): float(e) for d, e in zip(ref, e_rho)}),
+    )
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=256)
+    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--cap", type=int, default=40000)
+    ap.add_argument("--test-cap", type=int, default=80000)
+    ap.add_argument("--epochs", type=int, default=120)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--dump", default=None, help="write per-case results (JSON) to this path")
+    a = ap.parse_args(argv)
+    import torch
+    dev = torch.device("cuda")
+    log = (lambda s: print(s, flush=True)) if a.verbose else None
+    doms, masks, ok, rho, T, gen = generate(a.train, L=a.L, seed=5, cap=a.cap)
+    if log:
+        log(f"generated: {gen}")
+    X = torch.from_numpy(case_inputs([doms[i] for i in ok], masks[ok])).to(dev)
+    Y = torch.from_numpy(I.unet_target_planes(rho, T, [doms[i].T_over_Tc * I.CS_TC for i in ok])).to(dev)
+    net, losses, t_train = train(X, Y, a.L, epochs=a.epochs, batch=a.batch, lr=a.lr, log=log)
+    # fit on (up to) 64 training cases, in the units of the targets
+    m = min(64, X.shape[0])
+    P = predict(net, X[:m], a.batch)
+    fit = ((P - Y[:m]) ** 2).mean(dim=(0, 1, 2)).sqrt().cpu().numpy()
+    if log:
+        log(f"train fit rms (rho, T channels, normalised): {fit}")
+    tdoms, tmasks = I.warm_start_cases(a.test, L=a.L, seed=6)
+    ev = evaluate(net, tdoms, tmasks, a.test_cap, batch=a.batch)
+    net.close()
+    per_case = ev.pop("per_case")
+    if a.dump:
+        with open(a.dump, "w") as fh:
+            json.dump(per_case, fh)
+    print(json.dumps(dict(generate=gen, train=dict(samples=int(ok.size), epochs=a.epochs, batch=a.batch,
+                                                   lr=a.lr, seconds=t_train, loss_first=losses[0],
+                                                   loss_last=losses[-1], fit_rms_normalised=fit.tolist()),
+                          test=ev)))
+
+
+if __name__ == "__main__":
+    main()
