@@ -22,6 +22,11 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                                         Chapman-Enskog drift rate (Eq. 23)
                                         and steady states (Eq. 23 / A11),
                                         brute-force per-site recomputation
+  fd_rhs, fd_rk2, step_fd (Eqs. 26-27) -- closed-form eigenvalues of the
+                                        isotropic gradient and Laplacian on
+                                        Fourier modes, RK2 amplification
+                                        factors, uniform-state invariance
+  unet (warm-start network)          -- see oracle/unet.py
 """
 from __future__ import annotations
 
@@ -152,6 +157,12 @@ def _bind(lib):
     lib.or_critical_point.argtypes = [P, dp, dp]
     lib.or_critical_point.restype = ctypes.c_int
     lib.or_num_threads_available.restype = ctypes.c_int
+    lib.or_fd_rhs.argtypes = [P, dp, dp, dp, dp, dp]
+    lib.or_fd_rhs.restype = None
+    lib.or_fd_rk2.argtypes = [P, dp, dp, dp, dp, ctypes.c_int, dp]
+    lib.or_fd_rk2.restype = ctypes.c_int
+    lib.or_step_fd.argtypes = [P, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    lib.or_step_fd.restype = ctypes.c_int
     return lib
 
 
@@ -253,6 +264,51 @@ def step_sites(P, f, g, sites):
     if rc == ERR_ARG:
         raise ValueError("or_step_sites: invalid arguments")
     return of, og
+
+
+def _field(a, P):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == (P.ny, P.nx)
+    return a
+
+
+def fd_rhs(P, T, rho, ux, uy):
+    """K(T) of Eq. (26) at every site ([ny, nx])."""
+    T, rho, ux, uy = (_field(a, P) for a in (T, rho, ux, uy))
+    K = np.zeros((P.ny, P.nx))
+    _load().or_fd_rhs(ctypes.byref(P), _ptr(T), _ptr(rho), _ptr(ux), _ptr(uy), _ptr(K))
+    return K
+
+
+def fd_rk2(P, T, rho, ux, uy, printed=False):
+    """One Eq. (27) update of T with rho, u fixed (printed: a = 1/2, else Heun)."""
+    T, rho, ux, uy = (_field(a, P) for a in (T, rho, ux, uy))
+    Tn = np.zeros((P.ny, P.nx))
+    rc = _load().or_fd_rk2(ctypes.byref(P), _ptr(T), _ptr(rho), _ptr(ux), _ptr(uy), int(bool(printed)), _ptr(Tn))
+    if rc == ERR_ARG:
+        raise ValueError("or_fd_rk2 failed")
+    return Tn
+
+
+def step_fd(P, f, T, n=1, printed=False, threads=1, check=True):
+    """n steps of the hybrid scheme (f by Eq. (1), T by Eqs. (26)-(27)).
+    Returns (f, T, status, (rho, ux, uy) of the last step's time level)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    T = _field(T, P).copy()
+    fn, Tn = np.empty_like(f), np.empty_like(T)
+    rho, ux, uy = (np.zeros((P.ny, P.nx)) for _ in range(3))
+    worst = OK
+    for _ in range(int(n)):
+        rc = _load().or_step_fd(ctypes.byref(P), _ptr(f), _ptr(T), _ptr(fn), _ptr(Tn), int(bool(printed)),
+                                _ptr(rho), _ptr(ux), _ptr(uy), int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step_fd: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        T, Tn = Tn, T
+    if check and worst:
+        raise FloatingPointError(f"oracle FD step reported status {worst}")
+    return f, T, worst, (rho, ux, uy)
 
 
 def totals(P, f, g):

@@ -531,3 +531,137 @@ int or_num_threads_available(void)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------- */
+/* Finite-difference temperature treatment, Eqs. (26)-(27).
+ *
+ * Eq. (26): dT/dt = -u . grad T + (1 / (rho c_v)) div(lambda grad T) = K(T).
+ * Readings (the paper gives no more than this):
+ *   - lambda = rho c_v chi with chi = (tau_g - 1/2) c_s^2, the diffusivity of
+ *     the thermal LB equation, so that the three treatments solve the same
+ *     Eq. (6); then K = -u . grad T + chi (lap T + grad rho . grad T / rho).
+ *   - u is the velocity of the density LBE, (sum_i e_i f_i + F/2) / rho, and
+ *     rho, u are taken at time n for both stages of the update.
+ *   - "isotropic central schemes": on the D2Q9 stencil,
+ *       grad phi (x) = (1/cs^2) sum_i omega_i e_i phi(x + e_i),
+ *       lap  phi (x) = (2/cs^2) sum_i omega_i (phi(x + e_i) - phi(x)).
+ * Eq. (27): T^{n+1} = T^n + (dt/2)(h1 + h2), h1 = K(T^n), h2 = K(T^n + a dt h1)
+ * with a = 1/2 as printed, or a = 1 (Heun's second-order method, which the
+ * printed form is not); dt = 1.                                            */
+void or_fd_rhs(const or_params* P, const double* T, const double* rho, const double* ux,
+               const double* uy, double* K)
+{
+    const int nx = P->nx, ny = P->ny;
+    const double chi = (P->tau_g - 0.5) * CS2;
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t c = (int64_t)y * nx + x;
+            double gTx = 0.0, gTy = 0.0, grx = 0.0, gry = 0.0, lap = 0.0;
+            for (int i = 1; i < 9; ++i) {
+                const int64_t n = (int64_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+                gTx += OMEGA[i] * EX[i] * T[n];
+                gTy += OMEGA[i] * EY[i] * T[n];
+                grx += OMEGA[i] * EX[i] * rho[n];
+                gry += OMEGA[i] * EY[i] * rho[n];
+                lap += OMEGA[i] * (T[n] - T[c]);
+            }
+            gTx /= CS2;
+            gTy /= CS2;
+            grx /= CS2;
+            gry /= CS2;
+            lap *= 2.0 / CS2;
+            K[c] = -(ux[c] * gTx + uy[c] * gTy) + chi * (lap + (grx * gTx + gry * gTy) / rho[c]);
+        }
+    }
+}
+
+/* One Eq. (27) update of T with rho, u fixed; printed != 0 takes a = 1/2. */
+int or_fd_rk2(const or_params* P, const double* T, const double* rho, const double* ux,
+              const double* uy, int printed, double* Tn)
+{
+    const int64_t N = (int64_t)P->nx * P->ny;
+    double* h1 = (double*)malloc(sizeof(double) * N);
+    double* h2 = (double*)malloc(sizeof(double) * N);
+    double* Ts = (double*)malloc(sizeof(double) * N);
+    if (!h1 || !h2 || !Ts) {
+        free(h1); free(h2); free(Ts);
+        return OR_ERR_ARG;
+    }
+    const double a = printed ? 0.5 : 1.0;
+    or_fd_rhs(P, T, rho, ux, uy, h1);
+    for (int64_t s = 0; s < N; ++s) Ts[s] = T[s] + a * h1[s];
+    or_fd_rhs(P, Ts, rho, ux, uy, h2);
+    int err = OR_OK;
+    for (int64_t s = 0; s < N; ++s) {
+        Tn[s] = T[s] + 0.5 * (h1[s] + h2[s]);
+        if (!isfinite(Tn[s])) err = OR_ERR_NONFINITE;
+    }
+    free(h1); free(h2); free(Ts);
+    return err;
+}
+
+/* One step of the hybrid scheme: f by Eq. (1) with psi(rho, T^n) (or T_psi),
+ * then T by Eq. (27).  f: pre-collision populations at n (9 planes), T: T^n;
+ * fn, Tn: the state at n + 1.  rho_out, ux_out, uy_out (may be NULL) receive
+ * rho^n and u^n. */
+int or_step_fd(const or_params* P, const double* f, const double* T, double* fn, double* Tn,
+               int printed, double* rho_out, double* ux_out, double* uy_out, int nthreads)
+{
+    if (!P || P->nx < 3 || P->ny < 3 || !(P->tau_f > 0.5) || !(P->tau_g > 0.5) || P->G == 0.0 ||
+        !(P->cv > 0.0) || P->eos < 0 || P->eos > 2)
+        return OR_ERR_ARG;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    if (!rho || !psi || !psi2 || !ux || !uy) {
+        free(rho); free(psi); free(psi2); free(ux); free(uy);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    int err = OR_OK;
+    for (int64_t s = 0; s < N; ++s) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[i * N + s];
+        rho[s] = r;
+        const double Te = P->psi_uses_local_T ? T[s] : P->T_psi;
+        psi2[s] = or_psi_sq(P, r, Te);
+        psi[s] = 0.0;
+        if (!isfinite(r) || !isfinite(T[s])) err = err < OR_ERR_NONFINITE ? OR_ERR_NONFINITE : err;
+        if (P->beta != 0.0) {
+            if (psi2[s] < 0.0) {
+                err = OR_ERR_PSI_DOMAIN;
+                psi[s] = NAN;
+            } else {
+                psi[s] = sqrt(psi2[s]);
+            }
+        }
+    }
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = 0.0;
+            }
+            force_at(P, psi, psi2, x, y, &Fx, &Fy);
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, &ux[s], &uy[s]);
+            for (int i = 0; i < 9; ++i) {
+                const int64_t d = (int64_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+                fn[i * N + d] = fs[i];
+            }
+        }
+    }
+    const int e2 = or_fd_rk2(P, T, rho, ux, uy, printed, Tn);
+    if (e2 > err) err = e2;
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * N);
+    if (ux_out) memcpy(ux_out, ux, sizeof(double) * N);
+    if (uy_out) memcpy(uy_out, uy, sizeof(double) * N);
+    free(rho); free(psi); free(psi2); free(ux); free(uy);
+    return err;
+}
