@@ -64,7 +64,19 @@ enum {
 /* Temperature treatment (Sec. II B). */
 enum {
     LB_THERMAL_EQ7 = 0,  /* Eq. (7): g relaxes to c_v T f^eq; recovers Eq. (23)       */
-    LB_THERMAL_EQ24 = 1  /* Eq. (24): Eq. (7) + C_i of Eq. (25); recovers Eq. (6)/(A11) */
+    LB_THERMAL_EQ24 = 1, /* Eq. (24): Eq. (7) + C_i of Eq. (25); recovers Eq. (6)/(A11) */
+    /* Eqs. (26)-(27): no g populations; T is a field advanced by a second-order
+     * Runge-Kutta step of dT/dt = -u.grad T + (1/(rho c_v)) div(lambda grad T)
+     * with lambda = rho c_v (tau_g - 1/2) c_s^2 (the diffusivity of the thermal
+     * LBE), the isotropic central D2Q9 stencils for grad and the Laplacian,
+     * and rho, u (with F/2) of the density LBE at time n in both stages.
+     * FD26: Heun, h2 = K(T^n + dt h1); FD26_PRINTED: h2 = K(T^n + dt/2 h1) as
+     * printed with Eq. (27).  Storage FP64 or FP32 only (else
+     * LB_ERR_UNSUPPORTED); tile kernel only (tile_y == 0 is LB_ERR_ARG);
+     * not available in the batched solver; lb_get/set_populations and the
+     * state calls return LB_ERR_UNSUPPORTED (there is no g). */
+    LB_THERMAL_FD26 = 2,
+    LB_THERMAL_FD26_PRINTED = 3
 };
 
 /* Storage of the populations in device memory; collision arithmetic is FP64

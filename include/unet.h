@@ -125,10 +125,11 @@ lb_status un_synchronize(un_net* net);
 lb_status un_free(un_net* net);
 
 /* Warm-start handoff for N cases of H x W sites (all pointers device).
- * From the prediction d_pred [N][H][W][2]:
- *   rho_hat = max(rho_mid + rho_scale y0, rho_floor),
- *   T_hat = T0 (1 + t_dev_scale y1)  (the T output is the relative deviation
- *   from the case's initial temperature).
+ * The network outputs deviations from the case's initial fields; from the
+ * prediction d_pred [N][H][W][2]:
+ *   rho_hat = max(rho0 + rho_dev_scale y0, rho_floor),
+ *   T_hat = T0 (1 + t_dev_scale y1)
+ * (a zero prediction gives back the initial state).
  * Per case, with lo/hi the extreme values of rho_hat:
  *   1. rho1 = rho_hat + lam (rho_hat - lo)(hi - rho_hat): mass moved inside
  *      the interfaces only (the weight vanishes in both bulk phases), with
@@ -141,10 +142,9 @@ lb_status un_free(un_net* net);
  * float64 outputs of the same shape, ready for lb_init_device / lb_batch_init.
  * One block per case, sums in FP64 in a fixed order.  Asynchronous on
  * `stream`.  LB_ERR_ARG for NULL pointers or empty sizes. */
-lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_mid,
-                         double rho_scale, double rho_floor, double t_dev_scale,
-                         const double* d_rho0, const double* d_T0, double* d_rho, double* d_T,
-                         void* stream);
+lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_dev_scale,
+                         double rho_floor, double t_dev_scale, const double* d_rho0,
+                         const double* d_T0, double* d_rho, double* d_T, void* stream);
 
 #ifdef __cplusplus
 }

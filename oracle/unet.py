@@ -243,11 +243,11 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 # --------------------------------------------------- warm-start handoff
-def denormalise(y, rho_mid, rho_scale, t_dev_scale, T0, rho_floor=1e-4):
-    """Network output -> (rho_hat, T_hat): rho_hat = max(rho_mid + rho_scale y0,
-    rho_floor) (the method needs a positive density), T_hat = T0 (1 + t_dev_scale y1)
-    (the temperature output is the relative deviation from the initial T0)."""
-    return (np.maximum(rho_mid + rho_scale * y[..., 0], rho_floor),
+def denormalise(y, rho_dev_scale, t_dev_scale, rho0, T0, rho_floor=1e-4):
+    """Network output -> (rho_hat, T_hat).  Both outputs are deviations from the
+    case's initial fields: rho_hat = max(rho0 + rho_dev_scale y0, rho_floor)
+    (the method needs a positive density), T_hat = T0 (1 + t_dev_scale y1)."""
+    return (np.maximum(rho0 + rho_dev_scale * y[..., 0], rho_floor),
             T0 * (1.0 + t_dev_scale * y[..., 1]))
 
 

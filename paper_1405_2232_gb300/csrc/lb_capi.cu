@@ -60,10 +60,16 @@ lb_status validate(const lb_params* p) {
     if (!std::isfinite(p->beta)) return fail(LB_ERR_ARG, "beta must be finite");
     if (!(p->cv > 0.0)) return fail(LB_ERR_ARG, "c_v must be > 0");
     if (p->eos < LB_EOS_CS || p->eos > LB_EOS_IDEAL) return fail(LB_ERR_ARG, "unknown eos %d", p->eos);
-    if (p->thermal < LB_THERMAL_EQ7 || p->thermal > LB_THERMAL_EQ24)
+    if (p->thermal < LB_THERMAL_EQ7 || p->thermal > LB_THERMAL_FD26_PRINTED)
         return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
     if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
+    if (p->thermal >= LB_THERMAL_FD26) {
+        if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
+            return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment stores FP64 or FP32 only");
+        if ((p->tile_x || p->tile_y) && p->tile_y == 0)
+            return fail(LB_ERR_ARG, "the finite-difference treatment runs the tile kernel (tile_y != 0)");
+    }
     if (p->tile_x || p->tile_y) {
         if (!step_tile_supported(p->tile_x, p->tile_y))
             return fail(LB_ERR_ARG, "unsupported tile %dx%d", p->tile_x, p->tile_y);
@@ -135,6 +141,12 @@ struct lb_ctx {
     int64_t ref_time = 0;
     int64_t t = 0;
     int nchunks = 1;            // strip kernel: row chunks per strip
+    // finite-difference temperature treatment (Eqs. 26-27)
+    bool fd = false;
+    void* Tf[2] = {nullptr, nullptr};  // T^n, T^{n+1} (storage real)
+    int tcur = 0;
+    void *fd_h1 = nullptr, *fd_Ts = nullptr, *fd_rho = nullptr, *fd_ux = nullptr, *fd_uy = nullptr;
+    double* fd_u2 = nullptr;           // [2][n] velocity scratch of lb_totals
 };
 
 namespace {
@@ -235,6 +247,46 @@ cudaError_t dispatch_scatter(const lb_ctx* c, const double* in) {
     }
 }
 
+FdLaunch fd_launch(const lb_ctx* c) {
+    FdLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.kp = c->kp;
+    L.bmode = bmode_of(c->p.beta);
+    L.chi = (c->p.tau_g - 0.5) * (1.0 / 3.0);
+    L.a = c->p.thermal == LB_THERMAL_FD26_PRINTED ? 0.5 : 1.0;
+    L.stream = c->stream;
+    L.src = c->buf[c->cur];
+    L.T = c->Tf[c->tcur];
+    return L;
+}
+
+cudaError_t dispatch_fd_step(lb_ctx* c) {
+    FdLaunch L = fd_launch(c);
+    L.dst = c->buf[c->cur ^ 1];
+    L.T_next = c->Tf[c->tcur ^ 1];
+    L.h1 = c->fd_h1;
+    L.Ts = c->fd_Ts;
+    L.rho = c->fd_rho;
+    L.ux = c->fd_ux;
+    L.uy = c->fd_uy;
+    return c->p.precision == LB_PREC_FP64 ? launch_fd_step_fp64(L) : launch_fd_step_fp32(L);
+}
+
+cudaError_t dispatch_fd_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    FdLaunch L = fd_launch(c);
+    L.m_rho = rho;
+    L.m_ux = ux;
+    L.m_uy = uy;
+    L.m_T = T;
+    return c->p.precision == LB_PREC_FP64 ? launch_fd_moments_fp64(L) : launch_fd_moments_fp32(L);
+}
+
+cudaError_t dispatch_fd_set_T(lb_ctx* c, const double* d_T0) {
+    const long long n = (long long)c->p.nx * c->p.ny;
+    return c->p.precision == LB_PREC_FP64 ? launch_fd_set_T_fp64(c->Tf[c->tcur], d_T0, n, c->stream)
+                                          : launch_fd_set_T_fp32(c->Tf[c->tcur], d_T0, n, c->stream);
+}
+
 void release(lb_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -246,6 +298,14 @@ void release(lb_ctx* c) {
     cudaFree(c->d_snap);
     cudaFree(c->d_part);
     cudaFree(c->d_out8);
+    cudaFree(c->Tf[0]);
+    cudaFree(c->Tf[1]);
+    cudaFree(c->fd_h1);
+    cudaFree(c->fd_Ts);
+    cudaFree(c->fd_rho);
+    cudaFree(c->fd_ux);
+    cudaFree(c->fd_uy);
+    cudaFree(c->fd_u2);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -318,6 +378,24 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         release(c);
         return cuda_fail(e, "allocating context buffers");
     }
+    c->fd = p->thermal >= LB_THERMAL_FD26;
+    if (c->fd) {
+        const size_t fb = es * (size_t)n;
+        cudaError_t e2 = cudaMalloc(&c->Tf[0], fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->Tf[1], fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_h1, fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_Ts, fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_rho, fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_ux, fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_uy, fb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_u2, sizeof(double) * 2 * n);
+        if (e2 != cudaSuccess) {
+            release(c);
+            return cuda_fail(e2, "allocating the finite-difference fields");
+        }
+        c->p.tile_x = FD_BX;  // the FD front end has one tile shape
+        c->p.tile_y = FD_BY;
+    }
     c->kp = make_kparams(c->p, pitch, plane, c->d_err);
     // kernel choice: the strip-marching TMA kernel where its alignment rules
     // hold, else the tile kernel
@@ -382,6 +460,7 @@ lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double*
     lb_status st = create(p, stream, &c);
     if (st) return st;
     cudaError_t e = dispatch_init(c, d_rho0, d_T0);
+    if (e == cudaSuccess && c->fd) e = dispatch_fd_set_T(c, d_T0);
     if (e != cudaSuccess) {
         release(c);
         return cuda_fail(e, "init kernel");
@@ -402,6 +481,7 @@ lb_status lb_init(const lb_params* p, const double* rho0, const double* T0, void
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_ref + (size_t)p->nx * p->ny, T0, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = dispatch_init(c, c->d_ref, c->d_ref + (size_t)p->nx * p->ny);
+    if (e == cudaSuccess && c->fd) e = dispatch_fd_set_T(c, c->d_ref + (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         release(c);
@@ -416,9 +496,10 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     for (int64_t k = 0; k < n; ++k) {
-        cudaError_t e = dispatch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+        cudaError_t e = c->fd ? dispatch_fd_step(c) : dispatch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         c->cur ^= 1;
+        if (c->fd) c->tcur ^= 1;
         c->t += 1;
     }
     return LB_OK;
@@ -426,8 +507,8 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
 
 lb_status lb_synchronize(lb_ctx* c) {
     if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
-    return check_device_error(c);
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    return check_device_error(c);
 }
 
 lb_status lb_moments_device(lb_ctx* c, double* d_rho, double* d_ux, double* d_uy, double* d_T) {
@@ -439,7 +520,7 @@ lb_status lb_moments_device(lb_ctx* c, double* d_rho, double* d_ux, double* d_uy
     L.ux = d_ux;
     L.uy = d_uy;
     L.T = d_T;
-    cudaError_t e = dispatch_moments(c, L);
+    cudaError_t e = c->fd ? dispatch_fd_moments(c, d_rho, d_ux, d_uy, d_T) : dispatch_moments(c, L);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
     return LB_OK;
 }
@@ -464,6 +545,7 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) 
 
 lb_status lb_get_populations(lb_ctx* c, double* f, double* g) {
     if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
     const size_t n = (size_t)c->p.nx * c->p.ny;
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     double* d = nullptr;
@@ -480,6 +562,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f, double* g) {
 
 lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
     if (!c || !f || !g) return fail(LB_ERR_ARG, "NULL argument");
+    if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
     const size_t n = (size_t)c->p.nx * c->p.ny;
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     double* d = nullptr;
@@ -506,7 +589,15 @@ lb_status lb_totals(lb_ctx* c, double out[LB_TOTALS_N]) {
     L.ref_rho = use_ref ? c->d_ref : nullptr;
     L.ref_T = use_ref ? c->d_ref + n : nullptr;
     L.part = c->d_part;
-    cudaError_t e = dispatch_moments(c, L);
+    cudaError_t e = cudaSuccess;
+    if (c->fd) {
+        e = dispatch_fd_moments(c, L.rho, c->fd_u2, c->fd_u2 + n, L.T);
+        if (e == cudaSuccess)
+            e = launch_fd_partials(L.rho, c->fd_u2, c->fd_u2 + n, L.T, L.ref_rho, L.ref_T, (long long)n, c->p.cv,
+                                   c->d_part, moments_grid_blocks(c->p.nx, c->p.ny), c->stream);
+    } else {
+        e = dispatch_moments(c, L);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "totals kernel");
     k_reduce_partials<<<1, 256, 0, c->stream>>>(c->d_part, moments_grid_blocks(c->p.nx, c->p.ny), c->d_out8);
     CU(cudaGetLastError(), "reduce kernel");
@@ -536,12 +627,14 @@ lb_status lb_totals(lb_ctx* c, double out[LB_TOTALS_N]) {
 
 lb_status lb_state_size(const lb_ctx* c, size_t* bytes) {
     if (!c || !bytes) return fail(LB_ERR_ARG, "NULL argument");
+    if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
     *bytes = c->buf_bytes + sizeof(int64_t);
     return LB_OK;
 }
 
 lb_status lb_save_state(lb_ctx* c, void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
+    if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
     CU(cudaMemcpyAsync(host_blob, c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     CU(cudaStreamSynchronize(c->stream), "synchronize");
@@ -551,6 +644,7 @@ lb_status lb_save_state(lb_ctx* c, void* host_blob) {
 
 lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
+    if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
     CU(cudaMemcpyAsync(c->buf[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     CU(cudaStreamSynchronize(c->stream), "synchronize");

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lb_device.cuh"
+#include "lb_fd.cuh"
 
 namespace lbgb {
 
@@ -28,6 +29,28 @@ struct MomentsLaunch {
     double* part;                       // may be null; [grid][8]
     cudaStream_t stream;
 };
+
+// One time step (or a moments evaluation) of the finite-difference
+// temperature treatment, Eqs. (26)-(27).  Fields are dense [ny][nx] of the
+// storage precision's arithmetic type (FP64 or FP32).
+struct FdLaunch {
+    const void* src;      // f, pre-collision at n
+    void* dst;            // f, post-collision (step)
+    const void* T;        // T^n
+    void* T_next;         // T^{n+1} (step)
+    void *h1, *Ts;        // RK2 scratch
+    void *rho, *ux, *uy;  // rho^n, u^n (step)
+    double *m_rho, *m_ux, *m_uy, *m_T;  // moments outputs (any may be null)
+    KParams kp;
+    int bmode;
+    double chi;           // (tau_g - 1/2) c_s^2
+    double a;             // RK2 stage factor: 1 (Heun) or 1/2 (printed form)
+    cudaStream_t stream;
+};
+
+cudaError_t launch_fd_partials(const double* rho, const double* ux, const double* uy, const double* T,
+                               const double* ref_rho, const double* ref_T, long long n, double cv,
+                               double* part, int blocks, cudaStream_t st);
 
 // Tile used by the moments/totals kernel (one fixed shape: deterministic grid).
 constexpr int MOM_BX = 32, MOM_BY = 8;
@@ -57,7 +80,10 @@ inline bool strip_eligible(int prec, int nx, long long plane, int bx) {
     cudaError_t launch_gather_##NAME(const void* src, const KParams& kp, double* out,  \
                                      cudaStream_t st);                                 \
     cudaError_t launch_scatter_##NAME(void* dst, const KParams& kp, const double* in,  \
-                                      cudaStream_t st);
+                                      cudaStream_t st);                                \
+    cudaError_t launch_fd_step_##NAME(const FdLaunch& L);                              \
+    cudaError_t launch_fd_moments_##NAME(const FdLaunch& L);                           \
+    cudaError_t launch_fd_set_T_##NAME(void* T, const double* T0, long long n, cudaStream_t st);
 
 LBGB_DECLARE_PREC(fp64)
 LBGB_DECLARE_PREC(fp32)

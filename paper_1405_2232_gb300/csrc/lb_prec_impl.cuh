@@ -3,6 +3,7 @@
 // value) and LBGB_NAME (the suffix of the launch functions).
 #pragma once
 
+#include "lb_fd.cuh"
 #include "lb_launch.h"
 #include "lb_step_strip.cuh"
 
@@ -156,6 +157,76 @@ cudaError_t LBGB_CAT(launch_scatter_, LBGB_NAME)(void* dst, const KParams& kp, c
     using E = typename Store<LBGB_PREC>::elem;
     k_scatter<LBGB_PREC><<<elementwise_blocks(kp), 256, 0, st>>>(static_cast<E*>(dst), kp, in);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ finite-difference T (Eqs. 26-27)
+namespace {
+constexpr bool kFdSupported = LBGB_PREC == LB_PREC_FP64 || LBGB_PREC == LB_PREC_FP32;
+
+template <bool STEP>
+cudaError_t fd_front(const FdLaunch& L) {
+    if constexpr (!kFdSupported) {
+        return cudaErrorNotSupported;
+    } else {
+        using S = Store<LBGB_PREC>;
+        using E = typename S::elem;
+        using R = typename S::real;
+        const dim3 block(FD_BX, FD_BY);
+        const dim3 grid((L.kp.nx + FD_BX - 1) / FD_BX, (L.kp.ny + FD_BY - 1) / FD_BY);
+        const E* src = static_cast<const E*>(L.src);
+        E* dst = static_cast<E*>(L.dst);
+        const R* T = static_cast<const R*>(L.T);
+        R *rho = static_cast<R*>(L.rho), *ux = static_cast<R*>(L.ux), *uy = static_cast<R*>(L.uy);
+        switch (L.bmode) {
+            case BETA_ZERO:
+                k_fd_front<LBGB_PREC, BETA_ZERO, STEP><<<grid, block, 0, L.stream>>>(src, dst, T, rho, ux, uy, L.m_rho,
+                                                                                   L.m_ux, L.m_uy, L.m_T, L.kp);
+                break;
+            case BETA_ONE:
+                k_fd_front<LBGB_PREC, BETA_ONE, STEP><<<grid, block, 0, L.stream>>>(src, dst, T, rho, ux, uy, L.m_rho,
+                                                                                  L.m_ux, L.m_uy, L.m_T, L.kp);
+                break;
+            default:
+                k_fd_front<LBGB_PREC, BETA_MIXED, STEP><<<grid, block, 0, L.stream>>>(src, dst, T, rho, ux, uy,
+                                                                                    L.m_rho, L.m_ux, L.m_uy, L.m_T, L.kp);
+                break;
+        }
+        return cudaGetLastError();
+    }
+}
+}  // namespace
+
+cudaError_t LBGB_CAT(launch_fd_step_, LBGB_NAME)(const FdLaunch& L) {
+    if constexpr (!kFdSupported) {
+        return cudaErrorNotSupported;
+    } else {
+        using R = typename Store<LBGB_PREC>::real;
+        cudaError_t e = fd_front<true>(L);
+        if (e != cudaSuccess) return e;
+        const dim3 block(32, 8);
+        const dim3 grid((L.kp.nx + 31) / 32, (L.kp.ny + 7) / 8);
+        const R *T = static_cast<const R*>(L.T), *rho = static_cast<const R*>(L.rho);
+        const R *ux = static_cast<const R*>(L.ux), *uy = static_cast<const R*>(L.uy);
+        R *h1 = static_cast<R*>(L.h1), *Ts = static_cast<R*>(L.Ts), *Tn = static_cast<R*>(L.T_next);
+        k_fd_stage<R, 1><<<grid, block, 0, L.stream>>>(T, nullptr, rho, ux, uy, h1, Ts, L.kp.nx, L.kp.ny, (R)L.chi,
+                                                      (R)L.a, L.kp.err);
+        k_fd_stage<R, 2><<<grid, block, 0, L.stream>>>(T, Ts, rho, ux, uy, h1, Tn, L.kp.nx, L.kp.ny, (R)L.chi,
+                                                      (R)L.a, L.kp.err);
+        return cudaGetLastError();
+    }
+}
+
+cudaError_t LBGB_CAT(launch_fd_moments_, LBGB_NAME)(const FdLaunch& L) { return fd_front<false>(L); }
+
+cudaError_t LBGB_CAT(launch_fd_set_T_, LBGB_NAME)(void* T, const double* T0, long long n, cudaStream_t st) {
+    if constexpr (!kFdSupported) {
+        return cudaErrorNotSupported;
+    } else {
+        using R = typename Store<LBGB_PREC>::real;
+        long long b = (n + 255) / 256;
+        k_fd_set_T<R><<<(int)(b < 2432 ? (b < 1 ? 1 : b) : 2432), 256, 0, st>>>(static_cast<R*>(T), T0, n);
+        return cudaGetLastError();
+    }
 }
 
 }  // namespace lbgb

@@ -626,15 +626,14 @@ lb_status un_free(un_net* n) {
     return LB_OK;
 }
 
-lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_mid, double rho_scale,
+lb_status un_warm_fields(int32_t N, int32_t H, int32_t W, const float* d_pred, double rho_dev_scale,
                          double rho_floor, double t_dev_scale, const double* d_rho0, const double* d_T0,
                          double* d_rho, double* d_T, void* stream) {
     if (N < 1 || H < 1 || W < 1 || !d_pred || !d_rho0 || !d_T0 || !d_rho || !d_T)
         return uerr(LB_ERR_ARG, "un_warm_fields: invalid argument");
     unk::WarmArgs a;
     a.pred = d_pred;
-    a.rho_mid = rho_mid;
-    a.rho_scale = rho_scale;
+    a.rho_dev_scale = rho_dev_scale;
     a.rho_floor = rho_floor;
     a.t_dev_scale = t_dev_scale;
     a.rho0 = d_rho0;

@@ -633,7 +633,7 @@ __global__ void k_refresh_w(const float* __restrict__ Wm, int Cout, int Cin, bf1
 // ------------------------------------------------------ warm-start handoff
 struct WarmArgs {
     const float* pred;
-    double rho_mid, rho_scale, rho_floor, t_dev_scale;
+    double rho_dev_scale, rho_floor, t_dev_scale;
     const double* rho0;
     const double* T0;
     double* rho;
@@ -642,7 +642,7 @@ struct WarmArgs {
 };
 
 __device__ __forceinline__ double warm_rho_hat(const WarmArgs& a, long long i) {
-    return fmax(a.rho_mid + a.rho_scale * (double)a.pred[2 * i], a.rho_floor);
+    return fmax(a.rho0[i] + a.rho_dev_scale * (double)a.pred[2 * i], a.rho_floor);
 }
 __device__ __forceinline__ double warm_T_hat(const WarmArgs& a, long long i) {
     return a.T0[i] * (1.0 + a.t_dev_scale * (double)a.pred[2 * i + 1]);

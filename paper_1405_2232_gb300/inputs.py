@@ -220,8 +220,9 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
 # ------------------------------------------------------- warm-start network
 #: Normalisation of the network's input planes and outputs:
 #: input (T/T_c - t_mid)/t_scale, (G - g_mid)/g_scale, 2 mask - 1;
-#: output rho = rho_mid + rho_scale y0, T = T0 (1 + t_dev_scale y1).
-UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_mid=0.2, rho_scale=0.2,
+#: output (deviations from the case's initial fields rho0, T0):
+#: rho = rho0 + rho_dev_scale y0, T = T0 (1 + t_dev_scale y1).
+UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_dev_scale=0.1,
                  t_dev_scale=0.01)
 
 
@@ -261,10 +262,11 @@ def unet_input_planes(T_over_Tc, G, mask) -> np.ndarray:
                     axis=3).astype(np.float32)
 
 
-def unet_target_planes(rho, T, T0) -> np.ndarray:
+def unet_target_planes(rho, T, rho0, T0) -> np.ndarray:
     """Normalised training targets [N, H, W, 2] float32 from steady rho, T fields
-    and the cases' initial temperatures T0 (scalars [N] or fields)."""
-    r = (np.asarray(rho, dtype=np.float64) - UNET_NORM["rho_mid"]) / UNET_NORM["rho_scale"]
+    and the cases' initial fields rho0 [N, H, W] and temperatures T0 (scalars
+    [N] or fields)."""
+    r = (np.asarray(rho, dtype=np.float64) - np.asarray(rho0, dtype=np.float64)) / UNET_NORM["rho_dev_scale"]
     T = np.asarray(T, dtype=np.float64)
     T0 = np.asarray(T0, dtype=np.float64)
     if T0.ndim == 1:

@@ -23,7 +23,7 @@ LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM = 0, 1, 2, 3
 LB_ERR_NONFINITE, LB_ERR_PSI_DOMAIN, LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED = 4, 5, 6, 7
 LB_ERR_NOT_CONVERGED = 8
 LB_EOS_CS, LB_EOS_VDW, LB_EOS_IDEAL = 0, 1, 2
-LB_THERMAL_EQ7, LB_THERMAL_EQ24 = 0, 1
+LB_THERMAL_EQ7, LB_THERMAL_EQ24, LB_THERMAL_FD26, LB_THERMAL_FD26_PRINTED = 0, 1, 2, 3
 LB_PREC_FP64, LB_PREC_FP32, LB_PREC_FP16_DEV, LB_PREC_BF16_DEV = 0, 1, 2, 3
 LB_TOTALS_N = 5
 LB_TUNE_N = 5

@@ -56,7 +56,7 @@ def load():
         "un_get_tensor": (st, [vp, i32, fp, i64]),
         "un_synchronize": (st, [vp]),
         "un_free": (st, [vp]),
-        "un_warm_fields": (st, [i32, i32, i32, vp, dbl, dbl, dbl, dbl, vp, vp, vp, vp, vp]),
+        "un_warm_fields": (st, [i32, i32, i32, vp, dbl, dbl, dbl, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -166,7 +166,7 @@ class UNet:
 
 def warm_fields(N, H, W, d_pred, norm, d_rho0, d_T0, d_rho, d_T, rho_floor=1e-4, stream=None):
     """Handoff: network prediction -> mass- and energy-matched FP64 rho, T (device)."""
-    lb._check(load().un_warm_fields(int(N), int(H), int(W), lb._addr(d_pred), norm["rho_mid"],
-                                    norm["rho_scale"], float(rho_floor), norm["t_dev_scale"],
+    lb._check(load().un_warm_fields(int(N), int(H), int(W), lb._addr(d_pred), norm["rho_dev_scale"],
+                                    float(rho_floor), norm["t_dev_scale"],
                                     lb._addr(d_rho0), lb._addr(d_T0), lb._addr(d_rho), lb._addr(d_T),
                                     lb._stream(stream)))

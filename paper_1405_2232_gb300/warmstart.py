@@ -217,7 +217,8 @@ def main(argv=None):
     if log:
         log(f"generated: {gen}")
     X = torch.from_numpy(case_inputs([doms[i] for i in ok], masks[ok])).to(dev)
-    Y = torch.from_numpy(I.unet_target_planes(rho, T, [doms[i].T_over_Tc * I.CS_TC for i in ok])).to(dev)
+    Y = torch.from_numpy(I.unet_target_planes(rho, T, np.stack([doms[i].rho for i in ok]),
+                                              [doms[i].T_over_Tc * I.CS_TC for i in ok])).to(dev)
     net, losses, t_train = train(X, Y, a.L, epochs=a.epochs, batch=a.batch, lr=a.lr, log=log)
     # fit on (up to) 64 training cases, in the units of the targets
     m = min(64, X.shape[0])

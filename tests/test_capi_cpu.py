@@ -60,7 +60,7 @@ def test_params_default_layout(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 2), ("ny", 0), ("tau_f", 0.5), ("tau_g", 0.3), ("G", 0.0), ("cv", 0.0),
-    ("eos", 7), ("thermal", 3), ("precision", 9), ("tile_x", 17),
+    ("eos", 7), ("thermal", 4), ("precision", 9), ("tile_x", 17),
 ])
 def test_invalid_params_rejected_on_host(lib, field, value):
     import numpy as np

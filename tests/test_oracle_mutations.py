@@ -18,8 +18,11 @@ MUTATIONS = [
      "double pre = 1.0 - 1.0 / tau_g;"),
     ("diagonal_weight", "w2 = 1.0 / 12.0;", "w2 = 1.0 / 6.0;"),
     ("stencil_pair_swapped", "(psi[SE] - psi[NW])", "(psi[NW] - psi[SE])"),
-    ("streaming_direction", "wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx)",
-     "wrap(y - EY[i], ny) * nx + wrap(x - EX[i], nx)"),
+    ("streaming_direction",
+     "d = (int64_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);\n                fn[i * N + d] = fs[i];\n"
+     "                gn[i * N + d] = gs[i];",
+     "d = (int64_t)wrap(y - EY[i], ny) * nx + wrap(x - EX[i], nx);\n                fn[i * N + d] = fs[i];\n"
+     "                gn[i * N + d] = gs[i];"),
     ("tau_in_place_of_inverse", "(1.0 / P->tau_f) * (fl[i] - feq[i])",
      "(P->tau_f) * (fl[i] - feq[i])"),
     ("g_relaxes_with_tau_f", "(1.0 / P->tau_g) * (gl[i] - geq)",

@@ -51,5 +51,5 @@ def test_unsupported_width_and_null_arguments():
     assert lib.un_create(ctypes.byref(cfg), None, ctypes.byref(net)) == lb.LB_ERR_UNSUPPORTED
     assert lib.un_forward(None, 1, None, None) == lb.LB_ERR_ARG
     assert lib.un_adam_step(None, 1e-3, 0.9, 0.999, 1e-8) == lb.LB_ERR_ARG
-    assert lib.un_warm_fields(0, 8, 8, None, 0, 0, 0, 0, None, None, None, None, None) == lb.LB_ERR_ARG
+    assert lib.un_warm_fields(0, 8, 8, None, 0, 0, 0, None, None, None, None, None) == lb.LB_ERR_ARG
     assert lib.un_free(None) == lb.LB_OK

@@ -239,7 +239,7 @@ def test_warm_handoff(torch, N):
     N.warm_fields(n, h, w, d(pred), I.UNET_NORM, d(rho0), d(T0), d_rho, d_T)
     torch.cuda.synchronize()
     nm = I.UNET_NORM
-    rh, th = U.denormalise(pred.astype(np.float64), nm["rho_mid"], nm["rho_scale"], nm["t_dev_scale"], T0)
+    rh, th = U.denormalise(pred.astype(np.float64), nm["rho_dev_scale"], nm["t_dev_scale"], rho0, T0)
     rr, tr = U.warm_project(rh, th, rho0, T0)
     assert np.allclose(d_rho.cpu().numpy(), rr, rtol=1e-13, atol=0)
     assert np.allclose(d_T.cpu().numpy(), tr, rtol=1e-13, atol=0)

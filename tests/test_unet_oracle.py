@@ -209,9 +209,13 @@ def test_warm_project_moves_interfaces_not_bulk():
 
 def test_denormalise():
     y = np.array([[[[0.5, 2.0], [-3.0, 0.0]]]])
+    rho0 = np.array([[[0.1, 0.2]]])
     T0 = np.full((1, 1, 2), 0.08)
-    r, T = U.denormalise(y, 0.2, 0.2, 0.01, T0, rho_floor=1e-4)
-    assert np.allclose(r, [[[0.3, 1e-4]]]) and np.allclose(T, [[[0.08 * 1.02, 0.08]]])
+    r, T = U.denormalise(y, 0.1, 0.01, rho0, T0, rho_floor=1e-4)
+    assert np.allclose(r, [[[0.15, 1e-4]]]) and np.allclose(T, [[[0.08 * 1.02, 0.08]]])
+    # a zero output gives back the initial state
+    r, T = U.denormalise(np.zeros((1, 1, 2, 2)), 0.1, 0.01, rho0, T0)
+    assert np.array_equal(r, rho0) and np.array_equal(T, T0)
 
 
 def test_initial_parameters_recipe():
