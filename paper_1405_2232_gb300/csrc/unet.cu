@@ -133,7 +133,6 @@ struct un_net {
     float* hpart = nullptr;   // [hblocks][2C + 2]
     double* lpart = nullptr;  // [hblocks]
     double* d_loss = nullptr;
-    int* d_err = nullptr;     // sticky error word of the kernels (bit per lb_status)
     int hblocks = 0;
     std::vector<void*> allocs;
 };
@@ -205,20 +204,12 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
     a.W = Wl(n, l);
     a.relu = relu;
     a.up = up;
-    a.err = n->d_err;
     const long long M = (long long)N * a.H * a.W;
-    const unsigned gx = (unsigned)((M + unk::TC_M - 1) / unk::TC_M);
-    const bool k64 = Cin % 64 == 0;
-#define UN_TC_LAUNCH(NT_, KC_) \
-    unk::k_conv3_tc<NT_, KC_><<<dim3(gx, Cout / NT_), 128, unk::tc_smem_bytes<NT_, KC_>(), n->stream>>>(a)
-    if (Cout % 128 == 0) {
-        if (k64) UN_TC_LAUNCH(128, 64); else UN_TC_LAUNCH(128, 32);
-    } else if (Cout % 64 == 0) {
-        if (k64) UN_TC_LAUNCH(64, 64); else UN_TC_LAUNCH(64, 32);
-    } else {
-        if (k64) UN_TC_LAUNCH(32, 64); else UN_TC_LAUNCH(32, 32);
-    }
-#undef UN_TC_LAUNCH
+    const unsigned gx = (unsigned)((M + unk::CV_MT - 1) / unk::CV_MT);
+    if (Cout % 64 == 0)
+        unk::k_conv3<64><<<dim3(gx, Cout / 64), 256, 0, n->stream>>>(a);
+    else
+        unk::k_conv3<32><<<dim3(gx, Cout / 32), 256, 0, n->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -428,22 +419,6 @@ bool tensor_of(const un_net* n, int id, int N, const bf16** ptr, long long* coun
 
 }  // namespace
 
-namespace {
-// read (and clear) the kernels' error word; synchronises
-lb_status check_err(un_net* n) {
-    int h = 0;
-    UCU(cudaMemcpyAsync(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream), "error word");
-    UCU(cudaStreamSynchronize(n->stream), "synchronize");
-    if (h) {
-        UCU(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream), "clear error word");
-        UCU(cudaStreamSynchronize(n->stream), "synchronize");
-        return uerr(LB_ERR_TIMEOUT, "a tensor-core wait gave up (error word 0x%x)", h);
-    }
-    return LB_OK;
-}
-
-}  // namespace
-
 extern "C" {
 
 int64_t un_param_count(const un_config* cfg) {
@@ -534,15 +509,7 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess) e = alloc(n, &n->hpart, (long long)n->hblocks * (2 * cfg->base + 2));
     if (e == cudaSuccess) e = alloc(n, &n->lpart, n->hblocks);
     if (e == cudaSuccess) e = alloc(n, &n->d_loss, 1);
-    if (e == cudaSuccess) e = alloc(n, &n->d_err, 1);
-    if (e == cudaSuccess) e = cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream);
-#define UN_TC_ATTR(NT_, KC_)                                                                             \
-    if (e == cudaSuccess)                                                                                \
-        e = cudaFuncSetAttribute(unk::k_conv3_tc<NT_, KC_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)unk::tc_smem_bytes<NT_, KC_>());
-    UN_TC_ATTR(128, 64) UN_TC_ATTR(128, 32) UN_TC_ATTR(64, 64) UN_TC_ATTR(64, 32) UN_TC_ATTR(32, 64)
-    UN_TC_ATTR(32, 32)
-#undef UN_TC_ATTR
+
     if (e == cudaSuccess) e = cudaMemsetAsync(n->p, 0, sizeof(float) * n->nparam, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, sizeof(float) * n->nparam, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, sizeof(float) * n->nparam, n->stream);
@@ -605,8 +572,7 @@ lb_status un_loss_grad(un_net* n, int32_t N, const float* d_in, const float* d_t
     if (loss) {
         double s = 0.0;
         UCU(cudaMemcpyAsync(&s, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream), "loss download");
-        lb_status st = check_err(n);
-        if (st) return st;
+        UCU(cudaStreamSynchronize(n->stream), "synchronize");
         *loss = s / ((double)Pl(n, 0, N) * UN_OUT);
     }
     return LB_OK;
@@ -652,7 +618,8 @@ lb_status un_get_tensor(un_net* n, int32_t id, float* host, int64_t count) {
 lb_status un_synchronize(un_net* n) {
     if (!n) return uerr(LB_ERR_ARG, "un_synchronize: NULL net");
     UCU(cudaSetDevice(n->device), "cudaSetDevice");
-    return check_err(n);
+    UCU(cudaStreamSynchronize(n->stream), "synchronize");
+    return LB_OK;
 }
 
 lb_status un_free(un_net* n) {

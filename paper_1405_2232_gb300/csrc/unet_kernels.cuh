@@ -95,7 +95,6 @@ struct ConvArgs {
     int N, H, W;
     int relu;  // forward: ReLU after the bias
     int up;    // store each output pixel to the 2x2 block of a 2H x 2W image
-    int* err;  // sticky error word (bit LB_ERR_TIMEOUT = 6 on a wait that gave up)
 };
 
 constexpr int CV_MT = 128;   // pixels per CTA
@@ -234,241 +233,6 @@ __global__ void __launch_bounds__(256) k_conv3(ConvArgs a) {
                 }
             }
         }
-}
-
-// ------------------------------------------- convolution on tcgen05 / TMEM
-// The same implicit GEMM as k_conv3 on the 5th-generation tensor cores:
-// one thread issues tcgen05.mma (M = 128 pixels, N = NT output channels,
-// K = 16 per instruction, BF16 x BF16 -> FP32) reading A (pixels x channels)
-// and B (output channels x channels) from shared memory through matrix
-// descriptors; the accumulator lives in tensor memory (NT columns of the 128
-// lanes) and is read back with tcgen05.ld by the four warps, one lane per
-// pixel.  Operands are staged with cp.async in a STAGES-deep ring in the
-// no-swizzle K-major core-matrix layout: 8 rows x 16 bytes per 128-byte core
-// matrix, core matrices adjacent in K 128 bytes apart (leading byte offset),
-// 8-row groups 512 bytes apart (stride byte offset: 4 core matrices of K).
-// Each stage is released by a tcgen05.commit on its mbarrier.  Every wait is
-// bounded; a timeout sets the error word and the CTA stops issuing work.
-constexpr int TC_STAGES = 4;
-constexpr int TC_M = 128;
-constexpr uint32_t TC_TIMEOUT_CLK = 2000000000u;
-
-__device__ __forceinline__ void tc_mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool tc_mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (tc_mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!tc_mbar_try(bar, parity))
-        if (clock64() - t0 > (long long)TC_TIMEOUT_CLK) return false;
-    return true;
-}
-// shared-memory matrix descriptor: start address, leading / stride byte
-// offsets (>> 4), descriptor version 1 (bits 46-47), no swizzle (bits 61-63 = 0)
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24
-template <int N>
-__host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-}
-
-template <int NT, int KC>
-__host__ __device__ constexpr int tc_stages() {
-    return (TC_M + NT) * KC * 2 > 24 * 1024 ? 3 : TC_STAGES;
-}
-template <int NT, int KC>
-__host__ __device__ constexpr size_t tc_smem_bytes() {
-    return (size_t)tc_stages<NT, KC>() * (TC_M + NT) * KC * 2 + 8 * TC_STAGES + 16 + 128;
-}
-
-// NT output channels (32..128) per CTA, KC input channels (32 or 64) per stage
-template <int NT, int KC>
-__global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a) {
-    static_assert(NT == 32 || NT == 64 || NT == 128, "N tile");
-    static_assert(KC == 32 || KC == 64, "K chunk");
-    constexpr int STAGES = tc_stages<NT, KC>();
-    constexpr int K8 = KC / 8;           // 16-byte chunks of a row per stage
-    constexpr int SBO = K8 * 128;         // 8-row group stride of the core-matrix layout
-    extern __shared__ __align__(128) uint8_t tc_smem_raw[];
-    // 128-byte aligned carve-up: A stages, B stages, mbarriers, TMEM address
-    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~uintptr_t(127));
-    constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = NT * KC * 2;
-    uint8_t* sA = base;
-    uint8_t* sB = base + STAGES * A_BYTES;
-    uint64_t* done = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + TC_STAGES);
-    __shared__ int s_abort;
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int HW = a.H * a.W;
-    const int M = a.N * HW;
-    const int m0 = blockIdx.x * TC_M;
-    const int co0 = blockIdx.y * NT;
-    // this thread's pixel row of the A tile
-    const int m = m0 + tid;
-    const bool mv = m < M;
-    const int mm = mv ? m : 0;
-    const int pn = mm / HW, pr = mm - (mm / HW) * HW;
-    const int py = pr / a.W, px = pr - (pr / a.W) * a.W;
-    const int kchunks = a.Cin / KC;
-    const int KT = 9 * kchunks;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
-                     "r"((uint32_t)NT)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) tc_mbar_init(&done[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *s_tmem;
-
-    // core-matrix layout: row r, 8-channel chunk k8 -> (r / 8) * SBO + k8 * 128 + (r % 8) * 16
-    auto load_stage = [&](int kt, int s) {
-        const int tap = kt / kchunks, c0 = (kt - tap * kchunks) * KC;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const int yy = wrap(py + dy, a.H), xx = wrap(px + dx, a.W);
-        const bf16* src = a.x + (((long long)pn * a.H + yy) * a.W + xx) * a.xC + a.xoff + c0;
-        uint8_t* dA = sA + s * A_BYTES + (tid >> 3) * SBO + (tid & 7) * 16;
-#pragma unroll
-        for (int k8 = 0; k8 < K8; ++k8) cp_async16(dA + k8 * 128, src + k8 * 8, mv);
-        for (int q = tid; q < NT * K8; q += 128) {
-            const int r = q / K8, k8 = q - (q / K8) * K8;
-            cp_async16(sB + s * B_BYTES + (r >> 3) * SBO + k8 * 128 + (r & 7) * 16,
-                       a.w + ((long long)(co0 + r) * 9 + tap) * a.Cin + c0 + k8 * 8, true);
-        }
-    };
-
-    constexpr uint32_t IDESC = tc_idesc<NT>();
-    // loads run DIST stages ahead; the stage refilled at iteration kt was read
-    // by the MMAs of kt + DIST - STAGES, so up to STAGES - DIST MMA groups stay
-    // queued on the tensor core while the loads are in flight
-    constexpr int DIST = STAGES >= 4 ? STAGES - 2 : STAGES - 1;
-#pragma unroll
-    for (int p = 0; p < DIST; ++p) {
-        if (p < KT) load_stage(p, p);
-        cp_async_commit();
-    }
-    for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % STAGES;
-        cp_async_wait<DIST - 1>();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && !s_abort) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aA = smem_addr(sA + s * A_BYTES), aB = smem_addr(sB + s * B_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < KC / 16; ++kk) {
-                const uint64_t da = tc_desc(aA + kk * 256, 128, SBO);
-                const uint64_t db = tc_desc(aB + kk * 256, 128, SBO);
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(IDESC), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&done[s]))
-                         : "memory");
-        }
-        // refill the stage last read by the MMAs of iteration nk - STAGES
-        const int nk = kt + DIST;
-        if (nk < KT) {
-            const int pk = nk - STAGES;
-            if (pk >= 0) {
-                if (!tc_mbar_wait(&done[pk % STAGES], (uint32_t)((pk / STAGES) & 1))) {
-                    s_abort = 1;
-                    if (a.err) atomicOr(a.err, 1 << 6);
-                }
-            }
-            if (!s_abort) load_stage(nk, nk % STAGES);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    // all MMAs done: the last commit tracks every earlier tcgen05.mma of the issuing thread
-    if (KT > 0 && !tc_mbar_wait(&done[(KT - 1) % STAGES], (uint32_t)(((KT - 1) / STAGES) & 1))) {
-        if (a.err) atomicOr(a.err, 1 << 6);
-        s_abort = 1;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // s_abort is final and the same for every thread from here
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool aborted = s_abort != 0;
-
-    // epilogue: lane tid of TMEM = pixel row tid; NT columns in chunks of 32
-    if (!aborted) {
-        const int n = pn, yy = py, xx = px;
-#pragma unroll
-        for (int cc = 0; cc < NT; cc += 32) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (mv) {
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int co = co0 + cc + j;
-                    float t = __uint_as_float(r[j]);
-                    if (a.bias) t += a.bias[co];
-                    if (a.relu) t = fmaxf(t, 0.0f);
-                    if (a.mask) t = __bfloat162float(a.mask[(long long)m * a.mC + a.moff + co]) > 0.0f ? t : 0.0f;
-                    v[j] = t;
-                }
-#pragma unroll
-                for (int j8 = 0; j8 < 4; ++j8) {
-                    float f8[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) f8[k] = v[j8 * 8 + k];
-                    const uint4 u = pack8(f8);
-                    const int co = co0 + cc + j8 * 8;
-                    if (!a.up) {
-                        *reinterpret_cast<uint4*>(a.y + (long long)m * a.yC + a.yoff + co) = u;
-                    } else {
-#pragma unroll
-                        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                            for (int dx = 0; dx < 2; ++dx) {
-                                const long long pix = ((long long)n * 2 * a.H + 2 * yy + dy) * (2 * a.W) + 2 * xx + dx;
-                                *reinterpret_cast<uint4*>(a.y + pix * a.yC + a.yoff + co) = u;
-                            }
-                    }
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT) : "memory");
 }
 
 // -------------------------------------------------------- weight gradient
