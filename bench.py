@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--seg", type=int, default=SEG, help="LB time steps per bench step")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep run to steady state")
     ap.add_argument("--sweep-cap", type=int, default=60000, help="step cap of the batched sweep")
+    ap.add_argument("--sweep-domains", type=int, default=256,
+                    help="domains of the batched sweep (profiling: a smaller case)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -330,7 +332,7 @@ def run_sweep(lb, torch, dist, world, rank, args):
     domains are dealt round-robin to the ranks (no exchange).  Times one batched
     step (autotuned row chunks) and the run to residual < 1e-8 (K = 100)."""
     from paper_1405_2232_gb300 import inputs as I
-    doms = I.batched_sweep()[rank::world]
+    doms = I.batched_sweep(n_domains=args.sweep_domains)[rank::world]
     params = [lb.lb_params_default(nx=d.L, ny=d.L, tau_f=d.tau_f, tau_g=d.tau_g, G=d.G, beta=BETA,
                                    precision="fp32", psi_uses_local_T=0, T_psi=d.T_over_Tc * I.CS_TC)
               for d in doms]
@@ -358,7 +360,7 @@ def run_sweep(lb, torch, dist, world, rank, args):
         res[0] = mx[0]
     wall, conv, fail, capped, tot_sites = res.tolist()
     ok = st == 0
-    return {"workload": "256 periodic domains, L~U{64..512} (multiple of 4), T/Tc~U[0.6,0.95], "
+    return {"workload": f"{args.sweep_domains} periodic domains, L~U{{64..512}} (multiple of 4), T/Tc~U[0.6,0.95], "
                         "G~U[-1.2,-0.8], tau_f~U[0.6,1.2], droplet/slab, seed 4; FP32, Eq.24, beta 1.3, "
                         "psi(rho, T0)",
             "sites": int(tot_sites), "chunk_rows": rows,

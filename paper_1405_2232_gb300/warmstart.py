@@ -197,6 +197,39 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     )
 
 
+def train_step_bench(L=256, batch=16, steps=10, warmup=3):
+    """Time the network's training step (forward, backward, Adam) on random
+    inputs with CUDA events on the net's stream; returns (ms per step, GFLOP)."""
+    import torch
+    dev = torch.device("cuda")
+    s = torch.cuda.Stream()
+    net = UN.UNet(L, L, batch, stream=s)
+    table = UN.layer_table(net.cfg)
+    arch = [("", ci, co, k, (3 if i == 0 else ci)) for i, (ci, co, k, _) in enumerate(table)]
+    net.set_params(I.unet_init_params(arch))
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn((batch, L, L, 3), device=dev, generator=g)
+    t = torch.tanh(x[..., :2]).contiguous()
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        net.train_step(x, t, batch, 1e-3, want_loss=False)
+    net.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        net.train_step(x, t, batch, 1e-3, want_loss=False)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / max(steps, 1)
+    levels = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
+    gflop = 0.0
+    for (ci, co, k, _), lev in zip(table, levels):
+        px = batch * (L >> lev) ** 2
+        gflop += 2.0 * px * co * ci * k * k * (3 if k == 3 else 2) / 1e9  # forward, input and weight gradients
+    net.close()
+    return ms, gflop
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--train", type=int, default=2000)
@@ -209,7 +242,15 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--dump", default=None, help="write per-case results (JSON) to this path")
+    ap.add_argument("--train-step-bench", action="store_true",
+                    help="only time the training step on random data (--L, --batch) and exit")
+    ap.add_argument("--steps", type=int, default=10, help="timed steps of --train-step-bench")
     a = ap.parse_args(argv)
+    if a.train_step_bench:
+        ms, gflop = train_step_bench(a.L, a.batch, a.steps, warmup=min(3, a.steps))
+        print(json.dumps(dict(L=a.L, batch=a.batch, ms_per_step=ms, gflop_per_step=gflop,
+                              tflops=gflop / ms)))
+        return
     import torch
     dev = torch.device("cuda")
     log = (lambda s: print(s, flush=True)) if a.verbose else None
