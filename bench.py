@@ -49,6 +49,9 @@ sys.path.insert(0, ROOT)
 NX = NY = 4096
 SEG = 100                       # LB time steps per bench step
 BYTES_PER_SITE = {"fp64": 288, "fp32": 144, "fp16": 72, "bf16": 72}
+# finite-difference temperature treatment (Eqs. 26-27): f read + write and the
+# T field read + write per site (rho^n, u^n and the RK2 stage fields are overhead)
+BYTES_PER_SITE_FD = {"fp64": 160, "fp32": 80}
 CPU_SAMPLE = 1024               # oracle sample lattice (CPU baseline / reference arm)
 # Mixed force Eq. (4) with beta = 1.3: with Eq. (2) (beta = 1) this deep quench
 # (T = 0.75 T_c) drives the vapour density below zero within ~200 steps, and
@@ -159,6 +162,33 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(dist, value, device):
+    """The largest value over all ranks (the job takes as long as its slowest rank)."""
+    if not dist:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def combine_sweep(dist, wall, converged, failed, capped, sites, device):
+    """Whole-job sweep result: the slowest rank's wall time, summed counts and sites."""
+    if not dist:
+        return float(wall), int(converged), int(failed), int(capped), int(sites)
+    import torch
+    res = torch.tensor([wall, converged, failed, capped, sites], dtype=torch.float64, device=device)
+    mx = res.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(res, op=dist.ReduceOp.SUM)
+    return float(mx[0]), int(res[1]), int(res[2]), int(res[3]), int(res[4])
+
+
+def shard(items, rank, world):
+    """Round-robin share of independent work items of one rank (no exchange)."""
+    return items[rank::world]
 
 
 def dist_setup():
@@ -291,10 +321,7 @@ def main():
     with ClockSampler(gpu_id) as clk:
         t = time_device(lb, ctx, stream, args.steps, args.warmup, torch)
     lb.lb_synchronize(ctx)  # raises if the run left the EOS domain or went non-finite
-    if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(dist, t, "cuda")
     sites = NX * NY
     updates = sites * SEG * args.steps
     value = world * updates / t / 1e6
@@ -332,7 +359,7 @@ def run_sweep(lb, torch, dist, world, rank, args):
     domains are dealt round-robin to the ranks (no exchange).  Times one batched
     step (autotuned row chunks) and the run to residual < 1e-8 (K = 100)."""
     from paper_1405_2232_gb300 import inputs as I
-    doms = I.batched_sweep(n_domains=args.sweep_domains)[rank::world]
+    doms = shard(I.batched_sweep(n_domains=args.sweep_domains), rank, world)
     params = [lb.lb_params_default(nx=d.L, ny=d.L, tau_f=d.tau_f, tau_g=d.tau_g, G=d.G, beta=BETA,
                                    precision="fp32", psi_uses_local_T=0, T_psi=d.T_over_Tc * I.CS_TC)
               for d in doms]
@@ -351,14 +378,9 @@ def run_sweep(lb, torch, dist, world, rank, args):
         t0 = time.perf_counter()
         steps, resid, st = B.run(1e-8, K=100, max_steps=args.sweep_cap)
         wall = time.perf_counter() - t0
-    res = torch.tensor([wall, float(np.sum(st == 0)), float(np.sum((st != 0) & (st != 8))),
-                        float(np.sum(st == 8)), float(sites)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = res.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(res, op=dist.ReduceOp.SUM)
-        res[0] = mx[0]
-    wall, conv, fail, capped, tot_sites = res.tolist()
+    wall, conv, fail, capped, tot_sites = combine_sweep(
+        dist, wall, int(np.sum(st == 0)), int(np.sum((st != 0) & (st != 8))), int(np.sum(st == 8)), sites,
+        "cuda")
     ok = st == 0
     return {"workload": f"{args.sweep_domains} periodic domains, L~U{{64..512}} (multiple of 4), T/Tc~U[0.6,0.95], "
                         "G~U[-1.2,-0.8], tau_f~U[0.6,1.2], droplet/slab, seed 4; FP32, Eq.24, beta 1.3, "
@@ -385,10 +407,7 @@ def run_e2e(lb, torch, dist, p, rho, T, stream, args):
     lb.load().lb_moments(ctx, *[lb._dptr(o.numpy()) for o in outs])
     t_e2e = time.perf_counter() - t0
     lb.lb_free(ctx)
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(dist, t_e2e, "cuda")
     return t_e2e
 
 
@@ -397,7 +416,9 @@ def run_variants(lb, torch, rho, T, stream, sites):
     if True:
         for name, prec, thermal in (("fp32_eq7", "fp32", lb.LB_THERMAL_EQ7),
                                     ("fp16dev_eq24", "fp16", None), ("bf16dev_eq24", "bf16", None),
-                                    ("fp64_eq24", "fp64", None)):
+                                    ("fp64_eq24", "fp64", None),
+                                    ("fp32_fd26", "fp32", lb.LB_THERMAL_FD26),
+                                    ("fp64_fd26", "fp64", lb.LB_THERMAL_FD26)):
             pv = workload_params(lb, prec, thermal)
             d_rho = torch.from_numpy(rho).cuda()
             d_T = torch.from_numpy(T).cuda()
@@ -411,8 +432,9 @@ def run_variants(lb, torch, rho, T, stream, sites):
                 ok = False
             lb.lb_free(c)
             mlups = sites * SEG * nseg / tv / 1e6
+            bps = BYTES_PER_SITE_FD[prec] if thermal is not None and thermal >= lb.LB_THERMAL_FD26 else BYTES_PER_SITE[prec]
             variants[name] = {"MLUPS": round(mlups, 1),
-                              "GBps_algorithmic": round(BYTES_PER_SITE[prec] * mlups / 1e3, 1),
+                              "GBps_algorithmic": round(bps * mlups / 1e3, 1),
                               "state_ok": ok}
             del d_rho, d_T
     return variants
