@@ -205,6 +205,12 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
     a.relu = relu;
     a.up = up;
     const long long M = (long long)N * a.H * a.W;
+    if (a.W % unk::HT_W == 0 && a.H % unk::HT_H == 0 && Cout % unk::HT_NT == 0) {
+        // halo-tile form: one staged input halo serves all nine taps
+        const unsigned tiles = (unsigned)((long long)N * (a.H / unk::HT_H) * (a.W / unk::HT_W));
+        unk::k_conv3_halo<<<dim3(tiles, Cout / unk::HT_NT), 256, unk::halo_smem_bytes(), n->stream>>>(a);
+        return cudaGetLastError();
+    }
     const unsigned gx = (unsigned)((M + unk::CV_MT - 1) / unk::CV_MT);
     if (Cout % 64 == 0)
         unk::k_conv3<64><<<dim3(gx, Cout / 64), 256, 0, n->stream>>>(a);
@@ -509,6 +515,9 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess) e = alloc(n, &n->hpart, (long long)n->hblocks * (2 * cfg->base + 2));
     if (e == cudaSuccess) e = alloc(n, &n->lpart, n->hblocks);
     if (e == cudaSuccess) e = alloc(n, &n->d_loss, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unk::halo_smem_bytes());
 
     if (e == cudaSuccess) e = cudaMemsetAsync(n->p, 0, sizeof(float) * n->nparam, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, sizeof(float) * n->nparam, n->stream);

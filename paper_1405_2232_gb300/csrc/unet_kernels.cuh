@@ -235,6 +235,147 @@ __global__ void __launch_bounds__(256) k_conv3(ConvArgs a) {
         }
 }
 
+// ------------------------------------------- convolution, halo-tile form
+// For images at least 16 wide: a CTA computes an 8 x 16 pixel tile of one
+// image for NT = 32 output channels.  Per 32-channel chunk it stages the
+// 10 x 18 input halo once and the weights of all nine taps, then runs the
+// nine taps from shared memory (ldmatrix row addresses point at the shifted
+// halo pixel), so each input pixel is fetched once per chunk instead of once
+// per tap.  Chunks are double buffered.  Same epilogue as k_conv3.
+constexpr int HT_H = 8, HT_W = 16, HT_HH = HT_H + 2, HT_HW = HT_W + 2;
+constexpr int HT_NT = 32;
+constexpr int HT_A = HT_HH * HT_HW * CV_LD;   // halves per halo stage
+constexpr int HT_B = 9 * HT_NT * CV_LD;       // halves per weight stage
+
+__host__ __device__ constexpr size_t halo_smem_bytes() { return (size_t)2 * (HT_A + HT_B) * 2; }
+
+__global__ void __launch_bounds__(256) k_conv3_halo(ConvArgs a) {
+    extern __shared__ __align__(128) bf16 ht_smem[];
+    bf16* sA = ht_smem;                 // [2][HT_A]
+    bf16* sB = ht_smem + 2 * HT_A;      // [2][HT_B]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = a.W / HT_W, tiles_y = a.H / HT_H;
+    int b = blockIdx.x;
+    const int tx0 = (b % tiles_x) * HT_W;
+    b /= tiles_x;
+    const int ty0 = (b % tiles_y) * HT_H;
+    const int n = b / tiles_y;
+    const int co0 = blockIdx.y * HT_NT;
+    const int kchunks = a.Cin / CV_KC;
+
+    auto load_chunk = [&](int c, int s) {
+        const int c0 = c * CV_KC;
+        bf16* A = sA + s * HT_A;
+        for (int q = tid; q < HT_HH * HT_HW * 4; q += 256) {
+            const int hp = q >> 2, part = q & 3;
+            const int hy = hp / HT_HW, hx = hp - (hp / HT_HW) * HT_HW;
+            const int yy = wrap(ty0 + hy - 1, a.H), xx = wrap(tx0 + hx - 1, a.W);
+            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
+            cp_async16(A + hp * CV_LD + part * 8, a.x + pix * a.xC + a.xoff + c0 + part * 8, true);
+        }
+        bf16* B = sB + s * HT_B;
+        for (int q = tid; q < 9 * HT_NT * 4; q += 256) {
+            const int row = q >> 2, part = q & 3;  // row = tap * NT + co
+            const int tap = row / HT_NT, co = row - (row / HT_NT) * HT_NT;
+            cp_async16(B + row * CV_LD + part * 8, a.w + ((long long)(co0 + co) * 9 + tap) * a.Cin + c0 + part * 8,
+                       true);
+        }
+    };
+
+    const int wm = warp & 3, wn = warp >> 2;
+    constexpr int WN = HT_NT / 2;   // 16 columns per warp
+    constexpr int NI = WN / 8;      // 2
+    float acc[2][NI][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[mi][ni][k] = 0.0f;
+    const int q = lane >> 3, rr = lane & 7;
+    // halo index of this lane's A row (tap centre) for the two m16 tiles
+    int hbase[2];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+        const int r = wm * 32 + mi * 16 + rr + (q & 1) * 8;  // pixel row of the tile
+        hbase[mi] = (r / HT_W + 1) * HT_HW + (r % HT_W) + 1;
+    }
+
+    load_chunk(0, 0);
+    cp_async_commit();
+    for (int c = 0; c < kchunks; ++c) {
+        const int s = c & 1;
+        if (c + 1 < kchunks) {
+            load_chunk(c + 1, s ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const bf16* A = sA + s * HT_A;
+        const bf16* B = sB + s * HT_B;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int off = (tap / 3 - 1) * HT_HW + (tap % 3 - 1);
+#pragma unroll
+            for (int kk = 0; kk < CV_KC; kk += 16) {
+                uint32_t af[2][4];
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], A + (hbase[mi] + off) * CV_LD + kk + (q >> 1) * 8);
+                uint32_t bf[4];
+                ldsm_x4(bf, B + (tap * HT_NT + wn * WN + rr + (q >> 1) * 8) * CV_LD + kk + (q & 1) * 8);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    mma_bf16(acc[mi][0], af[mi], bf[0], bf[1]);
+                    mma_bf16(acc[mi][1], af[mi], bf[2], bf[3]);
+                }
+            }
+        }
+        __syncthreads();  // the stage is refilled two chunks later
+    }
+
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = wm * 32 + mi * 16 + g + h * 8;
+            const int yy = ty0 + r / HT_W, xx = tx0 + r % HT_W;
+            const long long m = ((long long)n * a.H + yy) * a.W + xx;
+#pragma unroll
+            for (int ni = 0; ni < NI; ++ni) {
+                const int co = co0 + wn * WN + ni * 8 + 2 * t4;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (a.bias) {
+                    v0 += a.bias[co];
+                    v1 += a.bias[co + 1];
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                if (a.mask) {
+                    const bf16* mp = a.mask + m * a.mC + a.moff + co;
+                    v0 = __bfloat162float(mp[0]) > 0.0f ? v0 : 0.0f;
+                    v1 = __bfloat162float(mp[1]) > 0.0f ? v1 : 0.0f;
+                }
+                const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+                if (!a.up) {
+                    *reinterpret_cast<__nv_bfloat162*>(a.y + m * a.yC + a.yoff + co) = o;
+                } else {
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const long long pix = ((long long)n * 2 * a.H + 2 * yy + dy) * (2 * a.W) + 2 * xx + dx;
+                            *reinterpret_cast<__nv_bfloat162*>(a.y + pix * a.yC + a.yoff + co) = o;
+                        }
+                }
+            }
+        }
+}
+
 // -------------------------------------------------------- weight gradient
 struct WgradArgs {
     const bf16* g;  // gradient at the conv output: pixel stride gC, first channel goff, Cout channels
