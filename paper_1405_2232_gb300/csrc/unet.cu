@@ -223,6 +223,36 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
 cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16* x, int xC, int xoff, int N, int l) {
     const Layer& L = n->L[k];
     const long long M = Pl(n, l, N);
+    if (Wl(n, l) % unk::HT_W == 0 && Hl(n, l) % unk::HT_H == 0) {
+        // halo-tile form: one staged gradient tile and input halo per 128 pixels, all taps
+        unk::WgradHaloArgs a;
+        a.g = g;
+        a.gC = gC;
+        a.goff = goff;
+        a.x = x;
+        a.xC = xC;
+        a.xoff = xoff;
+        a.Cout = L.cout;
+        a.Cin = L.cin;
+        a.N = N;
+        a.H = Hl(n, l);
+        a.W = Wl(n, l);
+        const int blocks = (L.cout / 32) * (L.cin / 32);
+        const long long n_tiles = M / (unk::HT_H * unk::HT_W);
+        long long sp = (4LL * n->sms + blocks - 1) / blocks;
+        if (sp > n_tiles) sp = n_tiles;
+        if (sp < 1) sp = 1;
+        const long long tps = (n_tiles + sp - 1) / sp;
+        const int splits = (int)((n_tiles + tps - 1) / tps);
+        a.tiles_per_split = (int)tps;
+        a.part = n->wpart;
+        a.bpart = n->bpart;
+        unk::k_wgrad_halo<<<dim3(blocks, splits), 256, unk::wgrad_halo_smem_bytes(), n->stream>>>(a);
+        const long long nw = (long long)L.cout * 9 * L.cin;
+        unk::k_sum_splits<<<grid_for(nw), 256, 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
+        unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
+        return cudaGetLastError();
+    }
     int MT, NT, tiles, splits, cps;
     wgrad_shape(n, L, M, &MT, &NT, &tiles, &splits, &cps);
     unk::WgradArgs a;
@@ -504,7 +534,11 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
         const int lev = k < 2 * LV ? k / 2 : (UN_LEVELS - 2) - (k - 2 * LV) / 2;
         wgrad_shape(n, n->L[k], Pl(n, lev, N), &MT, &NT, &tiles, &splits, &cps);
         // the split count never exceeds ceil(4 SMs / tiles) at any N
-        const long long smax = (4LL * n->sms + tiles - 1) / tiles;
+        // (the halo-tile form splits (cout/32)(cin/32) blocks the same way)
+        const long long hblocks = (long long)(n->L[k].cout / 32) * (n->L[k].cin / 32);
+        long long smax = (4LL * n->sms + tiles - 1) / tiles;
+        const long long smax_h = (4LL * n->sms + hblocks - 1) / hblocks;
+        if (smax_h > smax) smax = smax_h;
         const long long need = smax * n->L[k].cout * 9 * n->L[k].cin;
         if (need > cap) cap = need;
     }
@@ -518,6 +552,9 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::halo_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_wgrad_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unk::wgrad_halo_smem_bytes());
 
     if (e == cudaSuccess) e = cudaMemsetAsync(n->p, 0, sizeof(float) * n->nparam, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, sizeof(float) * n->nparam, n->stream);

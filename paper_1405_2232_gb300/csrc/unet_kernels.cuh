@@ -485,6 +485,125 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
         }
 }
 
+// Weight gradient, halo-tile form (images at least 16 wide): a CTA owns a
+// 32 (co) x 32 (ci) block for all nine taps and walks a range of 8 x 16
+// pixel tiles; per tile it stages the output gradient (128 pixels x 32 co)
+// and the 10 x 18 input halo (32 ci) once; the A fragment (gradient,
+// transposed) of a 16-pixel K step is loaded once and used for all nine taps,
+// whose B fragments come from the halo at the shifted pixel rows.  Warp w owns
+// co rows 16 (w & 1) .. +15 and ci columns 8 (w >> 1) .. +7 of every tap.
+struct WgradHaloArgs {
+    const bf16* g;  // gradient at the conv output (pixel stride gC, first channel goff)
+    int gC, goff;
+    const bf16* x;  // conv input view
+    int xC, xoff;
+    int Cout, Cin, N, H, W;
+    int tiles_per_split;  // pixel tiles per split (blockIdx.y)
+    float* part;          // [splits][Cout][9][Cin]
+    float* bpart;         // [splits][Cout] (ci tile 0 CTAs)
+};
+
+constexpr int WH_G = HT_H * HT_W * CV_LD;       // halves per gradient stage
+constexpr int WH_X = HT_HH * HT_HW * CV_LD;     // halves per halo stage
+__host__ __device__ constexpr size_t wgrad_halo_smem_bytes() { return (size_t)2 * (WH_G + WH_X) * 2; }
+
+__global__ void __launch_bounds__(256) k_wgrad_halo(WgradHaloArgs a) {
+    extern __shared__ __align__(128) bf16 wh_smem[];
+    bf16* sG = wh_smem;              // [2][WH_G]: [pixel][co]
+    bf16* sX = wh_smem + 2 * WH_G;   // [2][WH_X]: [halo pixel][ci]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_ci = a.Cin / 32;
+    const int cit = blockIdx.x % n_ci, cot = blockIdx.x / n_ci;
+    const int co0 = cot * 32, ci0 = cit * 32;
+    const int tiles_x = a.W / HT_W, tiles_y = a.H / HT_H;
+    const int n_tiles = a.N * tiles_x * tiles_y;
+    const int t_begin = blockIdx.y * a.tiles_per_split;
+    const int t_end = min(t_begin + a.tiles_per_split, n_tiles);
+
+    auto load_tile = [&](int tile, int s) {
+        int b = tile;
+        const int tx0 = (b % tiles_x) * HT_W;
+        b /= tiles_x;
+        const int ty0 = (b % tiles_y) * HT_H;
+        const int n = b / tiles_y;
+        bf16* G = sG + s * WH_G;
+        for (int q = tid; q < HT_H * HT_W * 4; q += 256) {
+            const int r = q >> 2, part = q & 3;
+            const long long pix = ((long long)n * a.H + ty0 + r / HT_W) * a.W + tx0 + (r % HT_W);
+            cp_async16(G + r * CV_LD + part * 8, a.g + pix * a.gC + a.goff + co0 + part * 8, true);
+        }
+        bf16* X = sX + s * WH_X;
+        for (int q = tid; q < HT_HH * HT_HW * 4; q += 256) {
+            const int hp = q >> 2, part = q & 3;
+            const int hy = hp / HT_HW, hx = hp - (hp / HT_HW) * HT_HW;
+            const int yy = wrap(ty0 + hy - 1, a.H), xx = wrap(tx0 + hx - 1, a.W);
+            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
+            cp_async16(X + hp * CV_LD + part * 8, a.x + pix * a.xC + a.xoff + ci0 + part * 8, true);
+        }
+    };
+
+    const int wm = warp & 1, wn = warp >> 1;
+    float acc[9][4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[k][j] = 0.0f;
+    const bool do_bias = cit == 0;
+    float bsum = 0.0f;
+    const int q = lane >> 3, rr = lane & 7;
+
+    if (t_begin < t_end) {
+        load_tile(t_begin, 0);
+        cp_async_commit();
+    }
+    for (int tile = t_begin; tile < t_end; ++tile) {
+        const int s = (tile - t_begin) & 1;
+        if (tile + 1 < t_end) {
+            load_tile(tile + 1, s ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const bf16* G = sG + s * WH_G;
+        const bf16* X = sX + s * WH_X;
+        if (do_bias && tid < 32)
+#pragma unroll 8
+            for (int px = 0; px < HT_H * HT_W; ++px) bsum += __bfloat162float(G[px * CV_LD + tid]);
+#pragma unroll 1
+        for (int k0 = 0; k0 < HT_H * HT_W; k0 += 16) {
+            // A[m = co][k = pixel] from G[pixel][co] (transposed 8x8 loads)
+            uint32_t af[4];
+            ldsm_x4_t(af, G + (k0 + rr + (q >> 1) * 8) * CV_LD + wm * 16 + (q & 1) * 8);
+            // this lane's B row: pixel k0 + rr + 8 (q & 1) of the tile, at its halo position
+            const int pr = k0 + rr + (q & 1) * 8;
+            const int hc = (pr / HT_W + 1) * HT_HW + (pr % HT_W) + 1;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int off = (tap / 3 - 1) * HT_HW + (tap % 3 - 1);
+                uint32_t b0, b1;
+                ldsm_x2_t(b0, b1, X + (hc + off) * CV_LD + wn * 8);
+                mma_bf16(acc[tap], af, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    if (do_bias && tid < 32) a.bpart[(long long)blockIdx.y * a.Cout + co0 + tid] = bsum;
+    const int g = lane >> 2, t4 = lane & 3;
+    float* out = a.part + (long long)blockIdx.y * a.Cout * 9 * a.Cin;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = co0 + wm * 16 + g + h * 8;
+            const int ci = ci0 + wn * 8 + 2 * t4;
+            float* o = out + ((long long)co * 9 + tap) * a.Cin + ci;
+            o[0] = acc[tap][2 * h];
+            o[1] = acc[tap][2 * h + 1];
+        }
+}
+
 // out[i] = sum_s part[s * n + i], s = 0..splits-1 in order
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
