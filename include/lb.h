@@ -109,11 +109,6 @@ typedef struct lb_params {
     double cv;             /* specific heat at constant volume (g^eq = c_v T f^eq), > 0 */
     double T_psi;          /* temperature used by psi when psi_uses_local_T == 0       */
     double rho0, T0;       /* deviation base of the 16-bit storage modes               */
-    int32_t step_fusion;   /* 0: lb_step runs pairs of time steps as one fused launch
-                              where the two-step kernel applies (FP32 storage, strip
-                              kernel, Eq. (7) or (24)); results are bit-identical to
-                              single steps.  1: one time step per launch.             */
-    int32_t reserved;      /* 0                                                        */
 } lb_params;
 
 typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
@@ -137,10 +132,8 @@ lb_status lb_init(const lb_params* p, const double* rho0, const double* T0,
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,
                          void* stream, lb_ctx** out);
 
-/* Advance n >= 0 time steps (Eq. (1) for f; Eq. (7) or (24) for g).  Each
- * launch reads and writes every population once: one fused time step per
- * launch, or two (temporal blocking, see step_fusion) where the two-step
- * kernel applies; an odd remainder runs as a single step.
+/* Advance n >= 0 time steps (Eq. (1) for f; Eq. (7) or (24) for g), each one
+ * fused kernel launch that reads and writes every population once.
  * Asynchronous on the context's stream. */
 lb_status lb_step(lb_ctx* ctx, int64_t n);
 

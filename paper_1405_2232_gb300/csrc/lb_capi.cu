@@ -64,8 +64,6 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
     if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
-    if (p->step_fusion != 0 && p->step_fusion != 1)
-        return fail(LB_ERR_ARG, "step_fusion must be 0 or 1 (got %d)", p->step_fusion);
     if (p->thermal >= LB_THERMAL_FD26) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment stores FP64 or FP32 only");
@@ -149,9 +147,6 @@ struct lb_ctx {
     int tcur = 0;
     void *fd_h1 = nullptr, *fd_Ts = nullptr, *fd_rho = nullptr, *fd_ux = nullptr, *fd_uy = nullptr;
     double* fd_u2 = nullptr;           // [2][n] velocity scratch of lb_totals
-    // two fused time steps per launch (FP32 strip kernel)
-    bool two_ok = false;
-    int nchunks2 = 1;
 };
 
 namespace {
@@ -200,8 +195,6 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.bx = c->p.tile_x;
     L.by = c->p.tile_y;
     L.nchunks = c->nchunks;
-    L.two = 0;
-    L.nchunks2 = c->nchunks2;
     L.stream = c->stream;
     switch (c->p.precision) {
         case LB_PREC_FP64: return launch_step_fp64(L);
@@ -209,21 +202,6 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
         case LB_PREC_FP16_DEV: return launch_step_fp16(L);
         default: return launch_step_bf16(L);
     }
-}
-
-// two fused time steps src -> dst (FP32 two-step strip kernel)
-cudaError_t dispatch_step2(const lb_ctx* c, const void* src, void* dst) {
-    StepLaunch L;
-    std::memset(&L, 0, sizeof(L));
-    L.src = src;
-    L.dst = dst;
-    L.kp = c->kp;
-    L.eq24 = c->p.thermal == LB_THERMAL_EQ24;
-    L.bmode = bmode_of(c->p.beta);
-    L.two = 1;
-    L.nchunks2 = c->nchunks2;
-    L.stream = c->stream;
-    return launch_step_fp32(L);
 }
 
 cudaError_t dispatch_moments(const lb_ctx* c, MomentsLaunch& L) {
@@ -442,16 +420,6 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         int nch = (2 * sms) / strips;
         nch = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
         c->nchunks = nch;
-        // two fused steps: FP32, Eq. (7)/(24), the strip's 16-byte rule
-        if (p->precision == LB_PREC_FP32 && !c->fd && p->step_fusion == 0 && p->nx % 4 == 0 &&
-            18LL * plane < (1LL << 32)) {
-            const int sw2 = strip2_cols();
-            const int strips2 = (p->nx + sw2 - 1) / sw2;
-            int n2 = (3 * sms) / strips2;
-            n2 = n2 < 1 ? 1 : (n2 > max_ch ? max_ch : n2);
-            c->nchunks2 = n2;
-            c->two_ok = true;
-        }
     }
     *out = c;
     return LB_OK;
@@ -527,15 +495,7 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
     if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    int64_t k = 0;
-    if (c->two_ok)
-        for (; k + 2 <= n; k += 2) {
-            cudaError_t e = dispatch_step2(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
-            if (e != cudaSuccess) return cuda_fail(e, "two-step kernel launch");
-            c->cur ^= 1;
-            c->t += 2;
-        }
-    for (; k < n; ++k) {
+    for (int64_t k = 0; k < n; ++k) {
         cudaError_t e = c->fd ? dispatch_fd_step(c) : dispatch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         c->cur ^= 1;

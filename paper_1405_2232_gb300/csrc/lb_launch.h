@@ -17,14 +17,8 @@ struct StepLaunch {
     int bmode;      // BetaMode
     int bx, by;     // CTA tile; by == 0: strip kernel of width bx
     int nchunks;    // strip kernel: row chunks per strip
-    int two;        // 1: two fused time steps (FP32 two-step strip kernel)
-    int nchunks2;   // two-step kernel: row chunks per strip
     cudaStream_t stream;
 };
-
-// Two-step strip kernel (FP32): strip width and eligibility.
-constexpr int STRIP2_BX = 96;
-inline int strip2_cols() { return STRIP2_BX - 8; }
 
 struct MomentsLaunch {
     const void* src;

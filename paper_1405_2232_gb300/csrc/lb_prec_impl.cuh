@@ -6,7 +6,6 @@
 #include "lb_fd.cuh"
 #include "lb_launch.h"
 #include "lb_step_strip.cuh"
-#include "lb_step_strip2.cuh"
 
 namespace lbgb {
 
@@ -94,51 +93,7 @@ cudaError_t step_strip(const StepLaunch& L) {
 
 }  // namespace
 
-namespace {
-// two fused time steps (FP32 storage only)
-template <bool EQ24, int BM>
-cudaError_t strip2_launch(const StepLaunch& L) {
-    if constexpr (LBGB_PREC != LB_PREC_FP32) {
-        return cudaErrorNotSupported;
-    } else {
-        constexpr int BX = STRIP2_BX, ST = 3;
-        constexpr size_t smem = strip2_smem_bytes<BX, ST>();
-        auto kern = k_step_strip2<BX, ST, EQ24, BM>;
-        static unsigned long long configured = 0;
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev >= 64 || !(configured >> dev & 1ULL)) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            if (dev < 64) configured |= 1ULL << dev;
-        }
-        constexpr int W = strip2_width<BX>();
-        const dim3 grid((L.kp.nx + W - 1) / W, L.nchunks2);
-        kern<<<grid, BX + 32, smem, L.stream>>>(static_cast<const float*>(L.src), static_cast<float*>(L.dst), L.kp,
-                                                L.nchunks2);
-        return cudaGetLastError();
-    }
-}
-
-cudaError_t step_strip2(const StepLaunch& L) {
-    if (L.eq24) {
-        switch (L.bmode) {
-            case BETA_ZERO: return strip2_launch<true, BETA_ZERO>(L);
-            case BETA_ONE: return strip2_launch<true, BETA_ONE>(L);
-            default: return strip2_launch<true, BETA_MIXED>(L);
-        }
-    }
-    switch (L.bmode) {
-        case BETA_ZERO: return strip2_launch<false, BETA_ZERO>(L);
-        case BETA_ONE: return strip2_launch<false, BETA_ONE>(L);
-        default: return strip2_launch<false, BETA_MIXED>(L);
-    }
-}
-}  // namespace
-
 cudaError_t LBGB_CAT(launch_step_, LBGB_NAME)(const StepLaunch& L) {
-    if (L.two) return step_strip2(L);
     if (L.by == 0) {
         if (L.bx == 128) return step_strip<128>(L);
         // (LB_PREC_* are enum constants, invisible to the preprocessor)

@@ -54,7 +54,6 @@ class lb_params(ctypes.Structure):
         ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
         ("cv", ctypes.c_double), ("T_psi", ctypes.c_double),
         ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
-        ("step_fusion", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
