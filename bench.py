@@ -9,7 +9,7 @@ treatment Eq. (24), FP32 populations.
 
 A bench "step" is a segment of SEG fused LB time steps over the whole lattice
 (every time step is one kernel launch that reads and writes every population
-once).  The lattice state (2 x 1.21 GB ping-pong) is far larger than the
+once).  The lattice state (2 x 1.23 GB ping-pong) is far larger than the
 129 MB L2, so no L2 flush is needed between steps.
 
 Metric: MLUPS (million lattice-site updates per second); value = device time
@@ -464,7 +464,7 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
                    "nx": NX, "ny": NY, "lb_steps_per_bench_step": SEG,
                    "thermal": "Eq.24", "storage": "fp32", "tau_f": 1.0, "tau_g": 0.8, "G": -1.0,
                    "force": "Eq.4", "beta": BETA,
-                   "l2": "state 2x1.21 GB > 129 MB L2, no flush needed",
+                   "l2": "state 2x1.23 GB > 129 MB L2, no flush needed",
                    "parallelism": f"independent lattice per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),

@@ -79,10 +79,8 @@ lb_status validate(const lb_params* p) {
             return fail(LB_ERR_ARG, "strip kernel needs nx to be a multiple of %d",
                         strip_halo(p->precision));
         if (p->tile_y == 0) {
-            const long long es = (long long)elem_size(p->precision);
-            const long long pitch = ((long long)p->nx * es + 127) / 128 * 128 / es;
-            const long long plane = (pitch * p->ny * es + 255) / 256 * 256 / es;
-            if (!strip_eligible(p->precision, p->nx, plane, p->tile_x))
+            const PopLayout L = pop_layout(p->precision, p->nx, p->ny, true);
+            if (!strip_eligible(p->precision, p->nx, L.plane, p->tile_x))
                 return fail(LB_ERR_ARG, "lattice too large for the strip kernel's 32-bit offsets");
         }
     }
@@ -129,9 +127,10 @@ struct lb_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;             // every call makes this device current first
-    void* buf[2] = {nullptr, nullptr};
+    void* alloc[2] = {nullptr, nullptr};  // population buffers as allocated
+    void* buf[2] = {nullptr, nullptr};    // column 0 of row 0 of plane 0 in each
     int cur = 0;
-    size_t buf_bytes = 0;
+    size_t buf_bytes = 0;                 // bytes per allocation
     int* d_err = nullptr;
     double* d_ref = nullptr;    // [2][n]: reference rho, T of the residual
     double* d_snap = nullptr;   // [2][n]: current rho, T written by lb_totals
@@ -291,8 +290,8 @@ void release(lb_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    cudaFree(c->buf[0]);
-    cudaFree(c->buf[1]);
+    cudaFree(c->alloc[0]);
+    cudaFree(c->alloc[1]);
     cudaFree(c->d_err);
     cudaFree(c->d_ref);
     cudaFree(c->d_snap);
@@ -357,14 +356,35 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         c->own_stream = true;
     }
     const size_t es = elem_size(p->precision);
-    // rows padded to 128 bytes, planes to 256 bytes
-    const long long pitch = ((long long)p->nx * es + 127) / 128 * 128 / es;
-    const long long plane = ((long long)pitch * p->ny * es + 255) / 256 * 256 / es;
+    c->fd = p->thermal >= LB_THERMAL_FD26;
+    if (c->fd) {
+        c->p.tile_x = FD_BX;  // the FD front end has one tile shape
+        c->p.tile_y = FD_BY;
+    }
+    // kernel choice: the strip-marching TMA kernel where its alignment rules
+    // hold, else the tile kernel
+    if (c->p.tile_x == 0 && c->p.tile_y == 0) {
+        const int bx = p->precision == LB_PREC_FP64 ? 128 : 256;
+        if (strip_eligible(p->precision, p->nx, pop_layout(p->precision, p->nx, p->ny, true).plane, bx)) {
+            c->p.tile_x = bx;
+            c->p.tile_y = 0;
+        } else {
+            c->p.tile_x = 32;
+            c->p.tile_y = 8;
+        }
+    }
+    const bool strip = c->p.tile_y == 0;
+    const PopLayout lay = pop_layout(p->precision, p->nx, p->ny, strip);
+    const long long pitch = lay.pitch, plane = lay.plane;
     c->buf_bytes = (size_t)plane * 18 * es;
     const long long n = (long long)p->nx * p->ny;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&c->buf[0], c->buf_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&c->buf[1], c->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->alloc[0], c->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->alloc[1], c->buf_bytes);
+    if (e == cudaSuccess) {
+        c->buf[0] = static_cast<char*>(c->alloc[0]) + lay.origin * es;
+        c->buf[1] = static_cast<char*>(c->alloc[1]) + lay.origin * es;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ref, sizeof(double) * 2 * n);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_snap, sizeof(double) * 2 * n);
@@ -372,13 +392,12 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out8, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     // zero both buffers so the padding never holds uninitialised bits
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, c->buf_bytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, c->buf_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->alloc[0], 0, c->buf_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->alloc[1], 0, c->buf_bytes, c->stream);
     if (e != cudaSuccess) {
         release(c);
         return cuda_fail(e, "allocating context buffers");
     }
-    c->fd = p->thermal >= LB_THERMAL_FD26;
     if (c->fd) {
         const size_t fb = es * (size_t)n;
         cudaError_t e2 = cudaMalloc(&c->Tf[0], fb);
@@ -393,23 +412,10 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
             release(c);
             return cuda_fail(e2, "allocating the finite-difference fields");
         }
-        c->p.tile_x = FD_BX;  // the FD front end has one tile shape
-        c->p.tile_y = FD_BY;
     }
     c->kp = make_kparams(c->p, pitch, plane, c->d_err);
-    // kernel choice: the strip-marching TMA kernel where its alignment rules
-    // hold, else the tile kernel
-    if (c->p.tile_x == 0 && c->p.tile_y == 0) {
-        const int bx = p->precision == LB_PREC_FP64 ? 128 : 256;
-        if (strip_eligible(p->precision, p->nx, plane, bx)) {
-            c->p.tile_x = bx;
-            c->p.tile_y = 0;
-        } else {
-            c->p.tile_x = 32;
-            c->p.tile_y = 8;
-        }
-    }
-    if (c->p.tile_y == 0) {
+    c->kp.ghost = strip ? STRIP_GHOST : 0;
+    if (strip) {
         // one wave of two resident CTAs per SM: strips x chunks <= 2 x SMs
         // (chunks of at least 8 rows)
         int sms = 0;
@@ -635,7 +641,7 @@ lb_status lb_state_size(const lb_ctx* c, size_t* bytes) {
 lb_status lb_save_state(lb_ctx* c, void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
     if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
-    CU(cudaMemcpyAsync(host_blob, c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
+    CU(cudaMemcpyAsync(host_blob, c->alloc[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     CU(cudaStreamSynchronize(c->stream), "synchronize");
     std::memcpy(static_cast<char*>(host_blob) + c->buf_bytes, &c->t, sizeof(int64_t));
@@ -645,7 +651,7 @@ lb_status lb_save_state(lb_ctx* c, void* host_blob) {
 lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
     if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
-    CU(cudaMemcpyAsync(c->buf[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
+    CU(cudaMemcpyAsync(c->alloc[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     CU(cudaStreamSynchronize(c->stream), "synchronize");
     std::memcpy(&c->t, static_cast<const char*>(host_blob) + c->buf_bytes, sizeof(int64_t));

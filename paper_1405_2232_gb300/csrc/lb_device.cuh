@@ -85,6 +85,7 @@ struct KParams {
     double half_1mbeta;  // (1 - beta)/2
     int eos;
     int psi_local_T;
+    int ghost;         // periodic ghost columns kept on each side of every row (0 or 2)
     double a, b, R;
     double cv, inv_cv;
     double T_psi;
@@ -111,6 +112,22 @@ __device__ __forceinline__ real p_eos(const KParams& kp, real rho, real T) {
         const real d = (real)1 - eta;
         return rho * R * T * num / (d * d * d) - a * rho * rho;
     }
+}
+
+// Periodic ghost columns kept on each side of a row in the strip layout: the
+// column halo of a strip reaches two columns past its edge (the pull, plus
+// one more site for psi).
+constexpr int STRIP_GHOST = 2;
+
+// Periodic ghost columns of the strip layout: the value stored at column x of
+// a row is also stored at column x + nx when x < kp.ghost and at x - nx when
+// x >= nx - kp.ghost, so that a row segment with its column halo is one
+// contiguous copy even at the periodic edges.  p points at column x.
+template <class S>
+__device__ __forceinline__ void put_ghost(typename S::elem* p, int x, const KParams& kp,
+                                          typename S::real v, typename S::real base) {
+    if (x < kp.ghost) S::put(p + kp.nx, v, base);
+    if (x >= kp.nx - kp.ghost) S::put(p - kp.nx, v, base);
 }
 
 // wrap a coordinate that may lie a few tiles outside [0, n)
@@ -473,8 +490,12 @@ __global__ void k_init(typename Store<PREC>::elem* __restrict__ dst, const KPara
             const double fe = rho0[d] * wd(i);
             const double ge = kp.cv * T0[d] * fe;
             const long long off = (long long)y * kp.pitch + x;
-            S::put(dst + (long long)i * kp.plane + off, (real)fe, (real)kp.base_f[i]);
-            S::put(dst + (long long)(9 + i) * kp.plane + off, (real)ge, (real)kp.base_g[i]);
+            typename S::elem* pf = dst + (long long)i * kp.plane + off;
+            typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;
+            S::put(pf, (real)fe, (real)kp.base_f[i]);
+            S::put(pg, (real)ge, (real)kp.base_g[i]);
+            put_ghost<S>(pf, x, kp, (real)fe, (real)kp.base_f[i]);
+            put_ghost<S>(pg, x, kp, (real)ge, (real)kp.base_g[i]);
         }
     }
 }
@@ -514,10 +535,13 @@ __global__ void k_scatter(typename Store<PREC>::elem* __restrict__ dst, const KP
             // f_i(x, t) is stored at x - e_i
             const int sx = wrapc(x - ex(i), kp.nx), sy = wrapc(y - ey(i), kp.ny);
             const long long off = (long long)sy * kp.pitch + sx;
-            S::put(dst + (long long)i * kp.plane + off, (real)in[(long long)i * n + s],
-                   (real)kp.base_f[i]);
-            S::put(dst + (long long)(9 + i) * kp.plane + off, (real)in[(long long)(9 + i) * n + s],
-                   (real)kp.base_g[i]);
+            typename S::elem* pf = dst + (long long)i * kp.plane + off;
+            typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;
+            const real vf = (real)in[(long long)i * n + s], vg = (real)in[(long long)(9 + i) * n + s];
+            S::put(pf, vf, (real)kp.base_f[i]);
+            S::put(pg, vg, (real)kp.base_g[i]);
+            put_ghost<S>(pf, sx, kp, vf, (real)kp.base_f[i]);
+            put_ghost<S>(pg, sx, kp, vg, (real)kp.base_g[i]);
         }
     }
 }

@@ -72,6 +72,25 @@ inline bool strip_eligible(int prec, int nx, long long plane, int bx) {
     return nx % strip_halo(prec) == 0 && 18LL * plane < (1LL << 32);
 }
 
+// Population buffer layout, in elements: 18 planes, rows padded to 128 bytes,
+// planes to 256 bytes.  The strip layout also leaves 128 bytes on each side
+// of every row for the periodic ghost columns (STRIP_GHOST of them are kept;
+// the rest is read as halo padding and never used); `origin` is the offset
+// of column 0 of row 0 of plane 0 from the start of the allocation.
+struct PopLayout {
+    long long pitch, plane, origin;
+};
+inline PopLayout pop_layout(int prec, int nx, int ny, bool strip) {
+    const long long es = prec == LB_PREC_FP64 ? 8 : (prec == LB_PREC_FP32 ? 4 : 2);
+    const long long gh = strip ? 128 / es : 0;
+    const long long halo = strip ? strip_halo(prec) : 0;
+    PopLayout L;
+    L.pitch = ((gh + nx + halo) * es + 127) / 128 * 128 / es;
+    L.plane = (L.pitch * ny * es + 255) / 256 * 256 / es;
+    L.origin = gh;
+    return L;
+}
+
 #define LBGB_DECLARE_PREC(NAME)                                                       \
     cudaError_t launch_step_##NAME(const StepLaunch& L);                               \
     cudaError_t launch_moments_##NAME(const MomentsLaunch& L);                         \

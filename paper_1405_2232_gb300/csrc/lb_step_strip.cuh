@@ -15,9 +15,14 @@
 // psi is computed once per site (plus 2 columns per strip and 2 rows per
 // chunk), and every population is read from HBM once and written once.
 //
-// Periodic wrap: rows wrap by index; the column halo of the first/last strip
-// is fetched from the other end of the row with separate 16-byte copies, so
-// the kernel needs nx to be a multiple of HALO (checked on the host).
+// Periodic wrap: rows wrap by index.  Columns wrap through ghost columns: the
+// population buffers of a strip context keep STRIP_GHOST periodic copies of
+// the first and last columns beside every row (kp.ghost; the layout leaves
+// 128 bytes on each side), and this kernel writes them with the row, so the
+// first and last strips fetch their halo with the same single copy as every
+// other strip.  (Fetching the far end of the row with two extra 16-byte
+// copies per plane row made the two edge strips the slowest CTAs of the
+// launch.)  The kernel needs nx to be a multiple of HALO (checked on the host).
 //
 // A dedicated producer warp issues the copies; the consumer warps release a
 // stage through a second mbarrier when its last reader is done, so copy issue
@@ -191,8 +196,6 @@ __global__ void __launch_bounds__(BX + 32, 2)
     if (t >= BX) {
         // ------------------------------------------------ producer warp
         const int lane = t - BX;
-        const bool left_wrap = x0 == 0;
-        const bool right_wrap = x0 + W == nx;
         int issued = 0;
         for (int j = 0; j < njobs; ++j) {
             const int s = j % STAGES;
@@ -214,14 +217,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
                 int sy = y - ey(d);
                 sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
                 const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
-                elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
-                if (!left_wrap && !right_wrap) {
-                    bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &full[s]);
-                } else {
-                    bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &full[s]);
-                    bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &full[s]);
-                    bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &full[s]);
-                }
+                // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
+                bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW, row + (x0 - HALO),
+                              (uint32_t)((W + 2 * HALO) * ES), &full[s]);
             }
             issued = j + 1;
         }
@@ -280,11 +278,23 @@ __global__ void __launch_bounds__(BX + 32, 2)
             collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
             int y = y_start + j - 2;
             y = y >= ny ? y - ny : y;
-            const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + t);
+            const int xg = x0 + t;
+            const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
+            const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
-                S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
+                elem* pf = dst + ((uint32_t)i * plane + off);
+                elem* pg = dst + ((uint32_t)(9 + i) * plane + off);
+                S::put(pf, f[i], (real)kp.base_f[i]);
+                S::put(pg, g[i], (real)kp.base_g[i]);
+                if (ghost_lo) {
+                    S::put(pf + nx, f[i], (real)kp.base_f[i]);
+                    S::put(pg + nx, g[i], (real)kp.base_g[i]);
+                }
+                if (ghost_hi) {
+                    S::put(pf - nx, f[i], (real)kp.base_f[i]);
+                    S::put(pg - nx, g[i], (real)kp.base_g[i]);
+                }
             }
         }
         // 3. the stage of job j-1 has had its last reader (psi at j-1, collision at j)
