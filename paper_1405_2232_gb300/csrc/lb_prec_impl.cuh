@@ -70,8 +70,8 @@ cudaError_t strip_launch(const StepLaunch& L) {
         if (dev < 64) configured |= 1ULL << dev;
     }
     const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
-    kern<<<grid, BX + 32, smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
-                                            L.kp, L.nchunks);
+    kern<<<grid, strip_threads<BX>(), smem, L.stream>>>(static_cast<const E*>(L.src),
+                                                         static_cast<E*>(L.dst), L.kp, L.nchunks);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@
 // 18 row segments into a STAGES-deep shared-memory ring with cp.async.bulk,
 // completion tracked by one mbarrier per stage.  The consumer warps then
 //   1. compute rho, T and psi of row y for columns -1..W (one site of halo on
-//      each side) into a 4-row psi ring,
+//      each side, computed by a separate halo warp so that no warp does two
+//      sites) into a 4-row psi ring,
 //   2. collide row y - 1 (Eq. (1) + F_i and Eq. (7)/(24)), whose three psi
 //      rows are now complete, reading its populations back from the stage
 //      ring and storing the 18 post-collision values with coalesced stores.
@@ -24,7 +25,7 @@
 // copies per plane row made the two edge strips the slowest CTAs of the
 // launch.)  The kernel needs nx to be a multiple of HALO (checked on the host).
 //
-// A dedicated producer warp issues the copies; the consumer warps release a
+// A dedicated producer warp issues the copies; the column warps release a
 // stage through a second mbarrier when its last reader is done, so copy issue
 // never stalls the consumers' per-row synchronisation.
 //
@@ -138,21 +139,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// named barrier over the consumer warps only (the producer warp never joins)
+// named barrier over the column threads and the halo warp (the producer warp
+// never joins)
 template <int NT>
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
 }
 
-// Block: BX consumer threads (BX/32 warps) plus one producer warp.
+// Threads per block of k_step_strip: BX column threads, one halo warp, one
+// producer warp.
+template <int BX>
+__host__ __device__ constexpr int strip_threads() {
+    return BX + 64;
+}
+
+// Block: BX column threads (BX/32 warps), one halo warp and one producer warp.
 //   producer: for every job (pre-collision row) waits until its stage is
 //     released, then lane 0 arms the stage's "full" mbarrier with the byte
-//     count and lanes 0..17 each issue the copies of one plane-row segment.
-//   consumers: wait "full", compute psi of the row into the psi ring, sync
-//     among themselves (named barrier), collide the row behind, then each
-//     warp releases the stage of the row behind on its "empty" mbarrier.
+//     count and lanes 0..17 each issue the copy of one plane-row segment.
+//   column threads: wait "full", compute psi of their column of the row into
+//     the psi ring, sync with the halo warp (named barrier), collide their
+//     column of the row behind, then each warp releases the stage of the row
+//     behind on its "empty" mbarrier.
+//   halo warp: lanes 0 and 1 compute psi of the two halo columns (-1 and W),
+//     so that no warp has two psi sites per row, then join the barrier.  It
+//     reads a stage only before the barrier of that row, which the column
+//     warps pass before they release the stage, so it does not release.
 template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
-__global__ void __launch_bounds__(BX + 32, 2)
+__global__ void __launch_bounds__(strip_threads<BX>(), 2)
     k_step_strip(const typename Store<PREC>::elem* __restrict__ src,
                  typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks) {
     using S = Store<PREC>;
@@ -193,9 +207,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
     }
     __syncthreads();
 
-    if (t >= BX) {
+    if (t >= BX + 32) {
         // ------------------------------------------------ producer warp
-        const int lane = t - BX;
+        const int lane = t - BX - 32;
         int issued = 0;
         for (int j = 0; j < njobs; ++j) {
             const int s = j % STAGES;
@@ -230,17 +244,23 @@ __global__ void __launch_bounds__(BX + 32, 2)
         return;
     }
 
-    // ---------------------------------------------------- consumer warps
+    // ------------------------------------------ column threads and halo warp
+    // ring column r holds strip column r - 1: column thread t owns r = t + 1,
+    // halo lanes 0 and 1 own r = 0 and r = W + 1
+    const bool halo = t >= BX;
+    const int r_psi = halo ? ((t & 31) == 0 ? 0 : W + 1) : t + 1;
+    const bool has_psi = halo ? (t & 31) < 2 : t < W;
     int flags = 0;
     for (int j = 0; j < njobs; ++j) {
         const int s = j % STAGES;
         if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
-        // 1. rho, T, psi of pre-collision row j for ring columns r = 0..W+1 (column r-1)
-        {
+        // 1. rho, T, psi of pre-collision row j at ring column r_psi
+        if (has_psi) {
             const elem* st = stage + (size_t)s * 18 * SEGW;
             real* rp = ring_psi + (j & 3) * RW;
             real* rq = ring_psi2 + (j & 3) * RW;
-            for (int r = t; r < W + 2; r += BX) {
+            {
+                const int r = r_psi;
                 const int c = r - 1 + HALO;  // smem column of the site
                 real f[9], g[9], rho, T, psi, psi2;
 #pragma unroll
@@ -253,8 +273,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
                 if (BMODE != BETA_ONE) rq[r] = psi2;
             }
         }
-        consumer_sync<BX>();
+        consumer_sync<BX + 32>();
         if (s_abort) break;
+        if (halo) continue;
         // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
         if (j >= 2 && t < W) {
             const int sp = (j - 1) % STAGES;
