@@ -19,6 +19,7 @@
 
 #include "lb.h"
 #include "lb_batch_device.cuh"
+#include "lb_launch.h"
 
 namespace lbgb {
 lb_status record_error(lb_status st, const char* msg);
@@ -128,8 +129,8 @@ cudaError_t launch_batch_step(lb_batch* b, const void* src, void* dst) {
         };
         auto k = pick();
         if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, BX + 32, smem, b->stream>>>(static_cast<const E*>(src), static_cast<E*>(dst),
-                                              b->d_doms, b->d_items, b->d_counts);
+        k<<<grid, strip_threads<BX>(), smem, b->stream>>>(static_cast<const E*>(src), static_cast<E*>(dst),
+                                                           b->d_doms, b->d_items, b->d_counts);
         return cudaGetLastError();
     }
     return launch_batch_step_fp64(src, dst, b->d_doms, b->d_items, b->d_counts, b->eq24, b->bmode,
@@ -297,15 +298,17 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         return cuerr(e, "lb_batch_init device");
     }
     const size_t es = prec == LB_PREC_FP64 ? 8 : 4;
-    // layout: each domain's 18 planes back to back (rows padded to 128 B,
-    // planes to 256 B); dense field offsets for the reference fields
+    // layout: each domain's 18 planes back to back in the strip layout (rows
+    // padded to 128 B with periodic ghost columns, planes to 256 B); dense
+    // field offsets for the reference fields
     long long off = 0, fld = 0;
     int max_items = 0, max_tiles = 0;
     b->doms.resize(n);
     for (int d = 0; d < n; ++d) {
         const lb_params& p = params[d];
-        const long long pitch = ((long long)p.nx * es + 127) / 128 * 128 / (long long)es;
-        const long long plane = ((long long)pitch * p.ny * es + 255) / 256 * 256 / (long long)es;
+        // the strip layout with periodic ghost columns (pop_layout)
+        const PopLayout lay = pop_layout(prec, p.nx, p.ny, true);
+        const long long pitch = lay.pitch, plane = lay.plane;
         BatchDomain& D = b->doms[d];
         std::memset(&D, 0, sizeof(D));
         KParams& k = D.kp;
@@ -329,7 +332,8 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         k.cv = p.cv;
         k.inv_cv = 1.0 / p.cv;
         k.T_psi = p.T_psi;
-        D.off = off;
+        k.ghost = STRIP_GHOST;
+        D.off = off + lay.origin;
         D.fld_off = fld;
         off += 18 * plane;
         fld += (long long)p.nx * p.ny;

@@ -7,7 +7,10 @@
 // one job counter across items, so the producer streams the next item's rows
 // while the consumers still work on the current one.  The list length is read
 // from device memory at launch, so a captured CUDA graph stays valid while
-// converged domains are taken off the list.
+// converged domains are taken off the list.  As in the single-lattice kernel,
+// every domain is stored in the ghost-column layout (one bulk copy per plane
+// row, ghost copies written with the row) and a halo warp computes the two
+// halo psi columns.
 #pragma once
 
 #include "lb_step_strip.cuh"
@@ -38,7 +41,7 @@ constexpr int batch_stages() {
 }
 
 template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
-__global__ void __launch_bounds__(BX + 32, 2)
+__global__ void __launch_bounds__(strip_threads<BX>(), 2)
     k_batch_step(const typename Store<PREC>::elem* __restrict__ src_base,
                  typename Store<PREC>::elem* __restrict__ dst_base,
                  const BatchDomain* __restrict__ doms, const BatchItem* __restrict__ items,
@@ -74,9 +77,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
     }
     __syncthreads();
 
-    if (t >= BX) {
+    if (t >= BX + 32) {
         // ------------------------------------------------ producer warp
-        const int lane = t - BX;
+        const int lane = t - BX - 32;
         long long jg = 0;  // job counter across this CTA's items
         for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
             const BatchItem item = items[it];
@@ -87,7 +90,6 @@ __global__ void __launch_bounds__(BX + 32, 2)
             const int W = min(BX, nx - x0);
             const int njobs = item.y1 - item.y0 + 2;
             const elem* src = src_base + D.off;
-            const bool left_wrap = x0 == 0, right_wrap = x0 + W == nx;
             for (int j = 0; j < njobs; ++j, ++jg) {
                 const int s = (int)(jg % STAGES);
                 if (jg >= STAGES) {
@@ -106,14 +108,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
                     int sy = y - ey(d);
                     sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
                     const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
-                    elem* seg = stage + ((size_t)s * 18 + i) * SEGW;
-                    if (!left_wrap && !right_wrap) {
-                        bulk_copy_g2s(seg, row + (x0 - HALO), (uint32_t)((W + 2 * HALO) * ES), &full[s]);
-                    } else {
-                        bulk_copy_g2s(seg, row + (left_wrap ? nx - HALO : x0 - HALO), HALO * ES, &full[s]);
-                        bulk_copy_g2s(seg + HALO, row + x0, (uint32_t)(W * ES), &full[s]);
-                        bulk_copy_g2s(seg + HALO + W, row + (right_wrap ? 0 : x0 + W), HALO * ES, &full[s]);
-                    }
+                    // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
+                    bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW, row + (x0 - HALO),
+                                  (uint32_t)((W + 2 * HALO) * ES), &full[s]);
                 }
             }
         }
@@ -124,7 +121,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
         return;
     }
 
-    // ---------------------------------------------------- consumer warps
+    // ------------------------------------------ column threads and halo warp
+    // (ring column r holds strip column r - 1; see k_step_strip)
+    const bool halo = t >= BX;
     long long jg = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const BatchItem item = items[it];
@@ -136,15 +135,18 @@ __global__ void __launch_bounds__(BX + 32, 2)
         const int W = min(BX, nx - x0);
         const int njobs = item.y1 - item.y0 + 2;
         elem* dst = dst_base + D.off;
+        const int r_psi = halo ? ((t & 31) == 0 ? 0 : W + 1) : t + 1;
+        const bool has_psi = halo ? (t & 31) < 2 : t < W;
         int flags = 0;
         for (int j = 0; j < njobs; ++j, ++jg) {
             const int s = (int)(jg % STAGES);
             if (!mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort = 1;
-            {
+            if (has_psi) {
                 const elem* st = stage + (size_t)s * 18 * SEGW;
                 real* rp = ring_psi + (int)(jg & 3) * RW;
                 real* rq = ring_psi2 + (int)(jg & 3) * RW;
-                for (int r = t; r < W + 2; r += BX) {
+                {
+                    const int r = r_psi;
                     const int c = r - 1 + HALO;
                     real f[9], g[9], rho, T, psi, psi2;
 #pragma unroll
@@ -157,8 +159,9 @@ __global__ void __launch_bounds__(BX + 32, 2)
                     if (BMODE != BETA_ONE) rq[r] = psi2;
                 }
             }
-            consumer_sync<BX>();
+            consumer_sync<BX + 32>();
             if (s_abort) break;
+            if (halo) continue;
             if (j >= 2 && t < W) {
                 const int sp = (int)((jg - 1) % STAGES);
                 const elem* st = stage + (size_t)sp * 18 * SEGW;
@@ -180,11 +183,23 @@ __global__ void __launch_bounds__(BX + 32, 2)
                     ring_psi2 + (int)((jg - 1) & 3) * RW + r, ring_psi2 + (int)(jg & 3) * RW + r, Fx, Fy);
                 collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
                 const int y = item.y0 + j - 2;
-                const uint32_t off = (uint32_t)y * pitch + (uint32_t)(x0 + t);
+                const int xg = x0 + t;
+                const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
+                const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
-                    S::put(dst + ((uint32_t)(9 + i) * plane + off), g[i], (real)kp.base_g[i]);
+                    elem* pf = dst + ((uint32_t)i * plane + off);
+                    elem* pg = dst + ((uint32_t)(9 + i) * plane + off);
+                    S::put(pf, f[i], (real)kp.base_f[i]);
+                    S::put(pg, g[i], (real)kp.base_g[i]);
+                    if (ghost_lo) {
+                        S::put(pf + nx, f[i], (real)kp.base_f[i]);
+                        S::put(pg + nx, g[i], (real)kp.base_g[i]);
+                    }
+                    if (ghost_hi) {
+                        S::put(pf - nx, f[i], (real)kp.base_f[i]);
+                        S::put(pg - nx, g[i], (real)kp.base_g[i]);
+                    }
                 }
             }
             // the job before this one has had its last reader in this warp
@@ -195,9 +210,10 @@ __global__ void __launch_bounds__(BX + 32, 2)
         }
         if (s_abort) break;
         // the item's last job (a halo row, never collided) is released too, so
-        // the producer may reuse its stage for the next item
+        // the producer may reuse its stage for the next item (column warps
+        // only: the halo warp never releases)
         __syncwarp();
-        if ((t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
+        if (!halo && (t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
         if (flags) atomicOr(kp.err, flags);
     }
     if (s_abort && t == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);

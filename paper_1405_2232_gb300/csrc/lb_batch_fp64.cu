@@ -25,8 +25,8 @@ cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain
                                 : k_batch_step<LB_PREC_FP64, BX, ST, false, BETA_MIXED>;
     // src == nullptr: set the shared-memory attribute only (once, outside capture)
     if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, BX + 32, smem, stream>>>(static_cast<const E*>(src), static_cast<E*>(dst), doms, items,
-                                       counts);
+    k<<<grid, strip_threads<BX>(), smem, stream>>>(static_cast<const E*>(src), static_cast<E*>(dst), doms,
+                                                   items, counts);
     return cudaGetLastError();
 }
 
