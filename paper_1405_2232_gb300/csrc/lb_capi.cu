@@ -67,8 +67,10 @@ lb_status validate(const lb_params* p) {
     if (p->thermal >= LB_THERMAL_FD26) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment stores FP64 or FP32 only");
-        if ((p->tile_x || p->tile_y) && p->tile_y == 0)
-            return fail(LB_ERR_ARG, "the finite-difference treatment runs the tile kernel (tile_y != 0)");
+        if ((p->tile_x || p->tile_y) && p->tile_y == 0 && p->tile_x != (p->precision == LB_PREC_FP64 ? 128 : 256))
+            return fail(LB_ERR_ARG, "the finite-difference strip kernel is 256 (FP32) or 128 (FP64) columns wide");
+        if ((p->tile_x || p->tile_y) && p->tile_y == 0 && p->nx < FD_STRIP_MIN_NX)
+            return fail(LB_ERR_ARG, "the finite-difference strip kernel needs nx >= %d", FD_STRIP_MIN_NX);
     }
     if (p->tile_x || p->tile_y) {
         if (!step_tile_supported(p->tile_x, p->tile_y))
@@ -142,9 +144,10 @@ struct lb_ctx {
     int nchunks = 1;            // strip kernel: row chunks per strip
     // finite-difference temperature treatment (Eqs. 26-27)
     bool fd = false;
-    void* Tf[2] = {nullptr, nullptr};  // T^n, T^{n+1} (storage real)
+    void* Tf_alloc[2] = {nullptr, nullptr};  // T^n, T^{n+1}: one population plane each
+    void* Tf[2] = {nullptr, nullptr};        // (storage real), column 0 of row 0 in each
     int tcur = 0;
-    void *fd_h1 = nullptr, *fd_Ts = nullptr, *fd_rho = nullptr, *fd_ux = nullptr, *fd_uy = nullptr;
+    void *fd_rho = nullptr, *fd_ux = nullptr, *fd_uy = nullptr;  // rho^n, u^n, dense
     double* fd_u2 = nullptr;           // [2][n] velocity scratch of lb_totals
 };
 
@@ -256,6 +259,8 @@ FdLaunch fd_launch(const lb_ctx* c) {
     L.stream = c->stream;
     L.src = c->buf[c->cur];
     L.T = c->Tf[c->tcur];
+    L.strip = c->p.tile_y == 0;
+    L.nchunks = c->nchunks;
     return L;
 }
 
@@ -263,8 +268,6 @@ cudaError_t dispatch_fd_step(lb_ctx* c) {
     FdLaunch L = fd_launch(c);
     L.dst = c->buf[c->cur ^ 1];
     L.T_next = c->Tf[c->tcur ^ 1];
-    L.h1 = c->fd_h1;
-    L.Ts = c->fd_Ts;
     L.rho = c->fd_rho;
     L.ux = c->fd_ux;
     L.uy = c->fd_uy;
@@ -281,9 +284,8 @@ cudaError_t dispatch_fd_moments(lb_ctx* c, double* rho, double* ux, double* uy, 
 }
 
 cudaError_t dispatch_fd_set_T(lb_ctx* c, const double* d_T0) {
-    const long long n = (long long)c->p.nx * c->p.ny;
-    return c->p.precision == LB_PREC_FP64 ? launch_fd_set_T_fp64(c->Tf[c->tcur], d_T0, n, c->stream)
-                                          : launch_fd_set_T_fp32(c->Tf[c->tcur], d_T0, n, c->stream);
+    return c->p.precision == LB_PREC_FP64 ? launch_fd_set_T_fp64(c->Tf[c->tcur], d_T0, c->kp, c->stream)
+                                          : launch_fd_set_T_fp32(c->Tf[c->tcur], d_T0, c->kp, c->stream);
 }
 
 void release(lb_ctx* c) {
@@ -297,10 +299,8 @@ void release(lb_ctx* c) {
     cudaFree(c->d_snap);
     cudaFree(c->d_part);
     cudaFree(c->d_out8);
-    cudaFree(c->Tf[0]);
-    cudaFree(c->Tf[1]);
-    cudaFree(c->fd_h1);
-    cudaFree(c->fd_Ts);
+    cudaFree(c->Tf_alloc[0]);
+    cudaFree(c->Tf_alloc[1]);
     cudaFree(c->fd_rho);
     cudaFree(c->fd_ux);
     cudaFree(c->fd_uy);
@@ -357,15 +357,18 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     }
     const size_t es = elem_size(p->precision);
     c->fd = p->thermal >= LB_THERMAL_FD26;
-    if (c->fd) {
-        c->p.tile_x = FD_BX;  // the FD front end has one tile shape
+    if (c->fd && c->p.tile_y != 0) {
+        c->p.tile_x = FD_BX;  // the FD tile front end has one tile shape
         c->p.tile_y = FD_BY;
     }
     // kernel choice: the strip-marching TMA kernel where its alignment rules
     // hold, else the tile kernel
     if (c->p.tile_x == 0 && c->p.tile_y == 0) {
         const int bx = p->precision == LB_PREC_FP64 ? 128 : 256;
-        if (strip_eligible(p->precision, p->nx, pop_layout(p->precision, p->nx, p->ny, true).plane, bx)) {
+        // (the FP64 finite-difference step, ALU-bound on the FP64 units, runs
+        // faster as the tile front + fused RK2 pair than as the fused strip)
+        if (strip_eligible(p->precision, p->nx, pop_layout(p->precision, p->nx, p->ny, true).plane, bx) &&
+            (!c->fd || (p->nx >= FD_STRIP_MIN_NX && p->precision == LB_PREC_FP32))) {
             c->p.tile_x = bx;
             c->p.tile_y = 0;
         } else {
@@ -400,10 +403,15 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     }
     if (c->fd) {
         const size_t fb = es * (size_t)n;
-        cudaError_t e2 = cudaMalloc(&c->Tf[0], fb);
-        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->Tf[1], fb);
-        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_h1, fb);
-        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_Ts, fb);
+        const size_t tb = es * (size_t)plane;  // T in the population plane layout
+        cudaError_t e2 = cudaMalloc(&c->Tf_alloc[0], tb);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&c->Tf_alloc[1], tb);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(c->Tf_alloc[0], 0, tb, c->stream);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(c->Tf_alloc[1], 0, tb, c->stream);
+        if (e2 == cudaSuccess) {
+            c->Tf[0] = static_cast<char*>(c->Tf_alloc[0]) + lay.origin * es;
+            c->Tf[1] = static_cast<char*>(c->Tf_alloc[1]) + lay.origin * es;
+        }
         if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_rho, fb);
         if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_ux, fb);
         if (e2 == cudaSuccess) e2 = cudaMalloc(&c->fd_uy, fb);
@@ -414,7 +422,7 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         }
     }
     c->kp = make_kparams(c->p, pitch, plane, c->d_err);
-    c->kp.ghost = strip ? STRIP_GHOST : 0;
+    c->kp.ghost = strip ? (c->fd ? FD_GHOST : STRIP_GHOST) : 0;
     if (strip) {
         // one wave of two resident CTAs per SM: strips x chunks <= 2 x SMs
         // (chunks of at least 8 rows)

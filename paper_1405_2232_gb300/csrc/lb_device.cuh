@@ -118,6 +118,13 @@ __device__ __forceinline__ real p_eos(const KParams& kp, real rho, real T) {
 // column halo of a strip reaches two columns past its edge (the pull, plus
 // one more site for psi).
 constexpr int STRIP_GHOST = 2;
+// The finite-difference step on strip contexts (k_fd_fused) reaches further:
+// its second RK2 stage needs K one column out, K needs rho two columns out,
+// and rho there needs the pull from three columns out.  Column halo of its
+// row copies (elements: 16 or 32 bytes) and ghost columns kept on FD strip
+// contexts.
+constexpr int FD_HALO = 4;
+constexpr int FD_GHOST = 3;
 
 // Periodic ghost columns of the strip layout: the value stored at column x of
 // a row is also stored at column x + nx when x < kp.ghost and at x - nx when

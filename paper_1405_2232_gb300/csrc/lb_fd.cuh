@@ -14,9 +14,11 @@
 // a = 1 (Heun) or 1/2 (the form printed with Eq. 27).
 //
 // Kernels: k_fd_front (tile + one-site psi ring, as k_step; STEP collides and
-// stores f and writes rho^n, u^n; MOMENTS writes rho, u, T), k_fd_stage (one
-// RK2 stage per launch, neighbours through L1/L2), k_fd_partials (FP64
-// totals of dense fields).  The FP64 mode evaluates every formula in the
+// stores f and writes rho^n, u^n; MOMENTS writes rho, u, T), and in
+// lb_fd_strip.cuh k_fd_fused (the whole step in one pass on strip contexts)
+// and k_fd_rk2 (both RK2 stages in one launch, after the tile front);
+// k_fd_partials (FP64 totals of dense fields).  T is stored like one population plane (row pitch kp.pitch, ghost
+// columns on strip contexts).  The FP64 mode evaluates every formula in the
 // order of its printed form (compiled without contraction).
 #pragma once
 
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
         real r = f[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) r += f[i];
-        site_psi_T<real, BMODE>(kp, r, Tf[(long long)gy * kp.nx + gx], psi, psi2, flags);
+        site_psi_T<real, BMODE>(kp, r, Tf[(long long)gy * kp.pitch + gx], psi, psi2, flags);
         if (BMODE != BETA_ZERO) s_psi[s] = psi;
         if (BMODE != BETA_ONE) s_psi2[s] = psi2;
     }
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
             if (m_rho) m_rho[c] = (double)rho;
             if (m_ux) m_ux[c] = (double)ux;
             if (m_uy) m_uy[c] = (double)uy;
-            if (m_T) m_T[c] = (double)Tf[c];
+            if (m_T) m_T[c] = (double)Tf[(long long)gy * kp.pitch + gx];
         }
     } else {
         flags = 0;
@@ -125,64 +127,19 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
     if (flags) atomicOr(kp.err, flags);
 }
 
-// K(X) of Eq. (26) at (x, y) from the field X and rho, u at time n.
+// T field (storage real, row pitch kp.pitch, ghost columns when kp.ghost)
+// <- T0 (FP64, dense [ny][nx])
 template <typename real>
-__device__ __forceinline__ real fd_K(const real* __restrict__ X, const real* __restrict__ rho,
-                                     const real* __restrict__ ux, const real* __restrict__ uy, int nx, int ny,
-                                     int x, int y, real chi) {
-    const long long c = (long long)y * nx + x;
-    const int xe = x == nx - 1 ? 0 : x + 1, xw = x == 0 ? nx - 1 : x - 1;
-    const int yn = y == ny - 1 ? 0 : y + 1, ys = y == 0 ? ny - 1 : y - 1;
-    real gTx = 0, gTy = 0, grx = 0, gry = 0, lap = 0;
-    const real Xc = X[c];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const int nxi = ex(i) == 1 ? xe : (ex(i) == -1 ? xw : x);
-        const int nyi = ey(i) == 1 ? yn : (ey(i) == -1 ? ys : y);
-        const long long n = (long long)nyi * nx + nxi;
-        const real w = (real)wd(i);
-        const real Xn = X[n], rn = rho[n];
-        gTx += w * (real)ex(i) * Xn;
-        gTy += w * (real)ey(i) * Xn;
-        grx += w * (real)ex(i) * rn;
-        gry += w * (real)ey(i) * rn;
-        lap += w * (Xn - Xc);
+__global__ void k_fd_set_T(real* __restrict__ T, const double* __restrict__ T0, const KParams kp) {
+    const long long n = (long long)kp.nx * kp.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % kp.nx), y = (int)(i / kp.nx);
+        const real v = (real)T0[i];
+        real* p = T + (long long)y * kp.pitch + x;
+        *p = v;
+        if (x < kp.ghost) p[kp.nx] = v;
+        if (x >= kp.nx - kp.ghost) p[-kp.nx] = v;
     }
-    const real cs2 = (real)(1.0 / 3.0);
-    gTx /= cs2;
-    gTy /= cs2;
-    grx /= cs2;
-    gry /= cs2;
-    lap *= (real)2 / cs2;
-    return -(ux[c] * gTx + uy[c] * gTy) + chi * (lap + (grx * gTx + gry * gTy) / rho[c]);
-}
-
-// STAGE 1: h1 = K(T), Ts = T + a h1.  STAGE 2: T_next = T + (h1 + K(Ts)) / 2.
-template <typename real, int STAGE>
-__global__ void k_fd_stage(const real* __restrict__ T, const real* __restrict__ Ts_in,
-                           const real* __restrict__ rho, const real* __restrict__ ux,
-                           const real* __restrict__ uy, real* __restrict__ h1, real* __restrict__ out, int nx,
-                           int ny, real chi, real a, int* err) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= nx || y >= ny) return;
-    const long long c = (long long)y * nx + x;
-    if (STAGE == 1) {
-        const real K = fd_K<real>(T, rho, ux, uy, nx, ny, x, y, chi);
-        h1[c] = K;
-        out[c] = T[c] + a * K;
-    } else {
-        const real K = fd_K<real>(Ts_in, rho, ux, uy, nx, ny, x, y, chi);
-        const real v = T[c] + (real)0.5 * (h1[c] + K);
-        out[c] = v;
-        if (!isfinite(v)) atomicOr(err, 1 << LB_ERR_NONFINITE);
-    }
-}
-
-// T field (storage real) <- T0 (FP64)
-template <typename real>
-__global__ void k_fd_set_T(real* __restrict__ T, const double* __restrict__ T0, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        T[i] = (real)T0[i];
 }
 
 }  // namespace lbgb

@@ -38,13 +38,14 @@ struct FdLaunch {
     void* dst;            // f, post-collision (step)
     const void* T;        // T^n
     void* T_next;         // T^{n+1} (step)
-    void *h1, *Ts;        // RK2 scratch
     void *rho, *ux, *uy;  // rho^n, u^n (step)
     double *m_rho, *m_ux, *m_uy, *m_T;  // moments outputs (any may be null)
     KParams kp;
     int bmode;
     double chi;           // (tau_g - 1/2) c_s^2
     double a;             // RK2 stage factor: 1 (Heun) or 1/2 (printed form)
+    int strip;            // strip context: the step is k_fd_fused
+    int nchunks;          // row chunks per strip (strip contexts)
     cudaStream_t stream;
 };
 
@@ -72,20 +73,24 @@ inline bool strip_eligible(int prec, int nx, long long plane, int bx) {
     return nx % strip_halo(prec) == 0 && 18LL * plane < (1LL << 32);
 }
 
+// Smallest nx of a finite-difference strip context: the FD_GHOST ghost
+// columns on each side must be distinct columns of the row.
+constexpr int FD_STRIP_MIN_NX = 8;
+
 // Population buffer layout, in elements: 18 planes, rows padded to 128 bytes,
 // planes to 256 bytes.  The strip layout also leaves 128 bytes on each side
-// of every row for the periodic ghost columns (STRIP_GHOST of them are kept;
-// the rest is read as halo padding and never used); `origin` is the offset
-// of column 0 of row 0 of plane 0 from the start of the allocation.
+// of every row for the periodic ghost columns (STRIP_GHOST of them are kept,
+// FD_GHOST on finite-difference contexts; the rest is read as halo padding
+// and never used); `origin` is the offset of column 0 of row 0 of plane 0
+// from the start of the allocation.
 struct PopLayout {
     long long pitch, plane, origin;
 };
 inline PopLayout pop_layout(int prec, int nx, int ny, bool strip) {
     const long long es = prec == LB_PREC_FP64 ? 8 : (prec == LB_PREC_FP32 ? 4 : 2);
     const long long gh = strip ? 128 / es : 0;
-    const long long halo = strip ? strip_halo(prec) : 0;
     PopLayout L;
-    L.pitch = ((gh + nx + halo) * es + 127) / 128 * 128 / es;
+    L.pitch = ((2 * gh + nx) * es + 127) / 128 * 128 / es;
     L.plane = (L.pitch * ny * es + 255) / 256 * 256 / es;
     L.origin = gh;
     return L;
@@ -102,7 +107,7 @@ inline PopLayout pop_layout(int prec, int nx, int ny, bool strip) {
                                       cudaStream_t st);                                \
     cudaError_t launch_fd_step_##NAME(const FdLaunch& L);                              \
     cudaError_t launch_fd_moments_##NAME(const FdLaunch& L);                           \
-    cudaError_t launch_fd_set_T_##NAME(void* T, const double* T0, long long n, cudaStream_t st);
+    cudaError_t launch_fd_set_T_##NAME(void* T, const double* T0, const KParams& kp, cudaStream_t st);
 
 LBGB_DECLARE_PREC(fp64)
 LBGB_DECLARE_PREC(fp32)

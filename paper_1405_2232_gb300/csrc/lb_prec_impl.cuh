@@ -4,6 +4,7 @@
 #pragma once
 
 #include "lb_fd.cuh"
+#include "lb_fd_strip.cuh"
 #include "lb_launch.h"
 #include "lb_step_strip.cuh"
 
@@ -163,6 +164,33 @@ cudaError_t LBGB_CAT(launch_scatter_, LBGB_NAME)(void* dst, const KParams& kp, c
 namespace {
 constexpr bool kFdSupported = LBGB_PREC == LB_PREC_FP64 || LBGB_PREC == LB_PREC_FP32;
 
+// The whole FD step on a strip context (k_fd_fused).
+template <int BM>
+cudaError_t fd_fused_launch(const FdLaunch& L) {
+    using S = Store<LBGB_PREC>;
+    using E = typename S::elem;
+    using R = typename S::real;
+    constexpr int BX = LBGB_PREC == LB_PREC_FP64 ? 128 : 256;
+    constexpr int ST = fd_fused_stages<LBGB_PREC, BX>();
+    static_assert(ST >= 3, "FD strip kernel needs at least three stages");
+    constexpr size_t smem = fd_fused_smem_bytes<LBGB_PREC, BX, ST>();
+    auto kern = k_fd_fused<LBGB_PREC, BX, ST, BM>;
+    static unsigned long long configured = 0;  // per instantiation, one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured >> dev & 1ULL)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ULL << dev;
+    }
+    const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
+    kern<<<grid, strip_threads<BX>(), smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
+                                                         static_cast<const R*>(L.T), static_cast<R*>(L.T_next),
+                                                         L.kp, L.nchunks, (R)L.chi, (R)L.a);
+    return cudaGetLastError();
+}
+
 template <bool STEP>
 cudaError_t fd_front(const FdLaunch& L) {
     if constexpr (!kFdSupported) {
@@ -201,30 +229,34 @@ cudaError_t LBGB_CAT(launch_fd_step_, LBGB_NAME)(const FdLaunch& L) {
         return cudaErrorNotSupported;
     } else {
         using R = typename Store<LBGB_PREC>::real;
+        if (L.strip) {
+            switch (L.bmode) {
+                case BETA_ZERO: return fd_fused_launch<BETA_ZERO>(L);
+                case BETA_ONE: return fd_fused_launch<BETA_ONE>(L);
+                default: return fd_fused_launch<BETA_MIXED>(L);
+            }
+        }
         cudaError_t e = fd_front<true>(L);
         if (e != cudaSuccess) return e;
-        const dim3 block(32, 8);
-        const dim3 grid((L.kp.nx + 31) / 32, (L.kp.ny + 7) / 8);
-        const R *T = static_cast<const R*>(L.T), *rho = static_cast<const R*>(L.rho);
-        const R *ux = static_cast<const R*>(L.ux), *uy = static_cast<const R*>(L.uy);
-        R *h1 = static_cast<R*>(L.h1), *Ts = static_cast<R*>(L.Ts), *Tn = static_cast<R*>(L.T_next);
-        k_fd_stage<R, 1><<<grid, block, 0, L.stream>>>(T, nullptr, rho, ux, uy, h1, Ts, L.kp.nx, L.kp.ny, (R)L.chi,
-                                                      (R)L.a, L.kp.err);
-        k_fd_stage<R, 2><<<grid, block, 0, L.stream>>>(T, Ts, rho, ux, uy, h1, Tn, L.kp.nx, L.kp.ny, (R)L.chi,
-                                                      (R)L.a, L.kp.err);
+        const dim3 block(FDR_BX, FDR_BY);
+        const dim3 grid((L.kp.nx + FDR_BX - 1) / FDR_BX, (L.kp.ny + FDR_BY * FDR_ROWS - 1) / (FDR_BY * FDR_ROWS));
+        k_fd_rk2<R><<<grid, block, 0, L.stream>>>(static_cast<const R*>(L.T), static_cast<const R*>(L.rho),
+                                                  static_cast<const R*>(L.ux), static_cast<const R*>(L.uy),
+                                                  static_cast<R*>(L.T_next), L.kp, (R)L.chi, (R)L.a);
         return cudaGetLastError();
     }
 }
 
 cudaError_t LBGB_CAT(launch_fd_moments_, LBGB_NAME)(const FdLaunch& L) { return fd_front<false>(L); }
 
-cudaError_t LBGB_CAT(launch_fd_set_T_, LBGB_NAME)(void* T, const double* T0, long long n, cudaStream_t st) {
+cudaError_t LBGB_CAT(launch_fd_set_T_, LBGB_NAME)(void* T, const double* T0, const KParams& kp, cudaStream_t st) {
     if constexpr (!kFdSupported) {
         return cudaErrorNotSupported;
     } else {
         using R = typename Store<LBGB_PREC>::real;
+        const long long n = (long long)kp.nx * kp.ny;
         long long b = (n + 255) / 256;
-        k_fd_set_T<R><<<(int)(b < 2432 ? (b < 1 ? 1 : b) : 2432), 256, 0, st>>>(static_cast<R*>(T), T0, n);
+        k_fd_set_T<R><<<(int)(b < 2432 ? (b < 1 ? 1 : b) : 2432), 256, 0, st>>>(static_cast<R*>(T), T0, kp);
         return cudaGetLastError();
     }
 }

@@ -35,13 +35,16 @@ def oracle_run(P, rho, T, n, printed):
     return r, ux, uy, Tn, st
 
 
-def gpu_run(lb, P, rho, T, n, thermal, prec):
+def gpu_run(lb, P, rho, T, n, thermal, prec, tile=None):
+    extra = {} if tile is None else dict(tile_x=tile[0], tile_y=tile[1])
     with lb.Lattice(rho, T, nx=P.nx, ny=P.ny, precision=prec, tau_f=P.tau_f, tau_g=P.tau_g, G=P.G,
-                    beta=P.beta, thermal=thermal, psi_uses_local_T=P.psi_uses_local_T, T_psi=P.T_psi) as L:
+                    beta=P.beta, thermal=thermal, psi_uses_local_T=P.psi_uses_local_T, T_psi=P.T_psi,
+                    **extra) as L:
         L.step(n)
         m = L.moments()
         tot = L.totals()
-    return m, tot
+        shape = (lb.lb_get_params(L.ctx).tile_x, lb.lb_get_params(L.ctx).tile_y)
+    return m, tot, shape
 
 
 def rel(a, b):
@@ -55,7 +58,7 @@ def test_fd_fp64_matches_oracle(lb, printed):
     thermal = lb.LB_THERMAL_FD26_PRINTED if printed else lb.LB_THERMAL_FD26
     r, ux, uy, Tn, st = oracle_run(P, rho, T, 300, printed)
     assert st == 0
-    (gr, gux, guy, gT), _ = gpu_run(lb, P, rho, T, 300, thermal, "fp64")
+    (gr, gux, guy, gT), _, _ = gpu_run(lb, P, rho, T, 300, thermal, "fp64")
     assert rel(gr, r) <= 1e-12 and rel(gT, Tn) <= 1e-12
     assert np.abs(gux - ux).max() <= 1e-12 * np.abs(ux).max()
     assert np.abs(guy - uy).max() <= 1e-12 * max(np.abs(uy).max(), 1e-300) or np.abs(guy - uy).max() < 1e-15
@@ -66,7 +69,7 @@ def test_fd_fp64_matches_oracle(lb, printed):
 def test_fd_fp64_ragged(lb, nx, ny):
     rho, T, P = setup(nx, ny, local_T=0)
     r, ux, uy, Tn, st = oracle_run(P, rho, T, 60, False)
-    (gr, gux, guy, gT), _ = gpu_run(lb, P, rho, T, 60, lb.LB_THERMAL_FD26, "fp64")
+    (gr, gux, guy, gT), _, _ = gpu_run(lb, P, rho, T, 60, lb.LB_THERMAL_FD26, "fp64")
     assert rel(gr, r) <= 1e-12 and rel(gT, Tn) <= 1e-12
 
 
@@ -74,7 +77,7 @@ def test_fd_fp64_ragged(lb, nx, ny):
 def test_fd_fp32_within_tolerance(lb):
     rho, T, P = setup()
     r, ux, uy, Tn, st = oracle_run(P, rho, T, 1000, False)
-    (gr, gux, guy, gT), _ = gpu_run(lb, P, rho, T, 1000, lb.LB_THERMAL_FD26, "fp32")
+    (gr, gux, guy, gT), _, _ = gpu_run(lb, P, rho, T, 1000, lb.LB_THERMAL_FD26, "fp32")
     e_rho, e_T = rel(gr, r), rel(gT, Tn)
     assert e_rho <= 2e-5 and e_T <= 2e-5, (e_rho, e_T)
 
@@ -83,7 +86,7 @@ def test_fd_fp32_within_tolerance(lb):
 def test_fd_totals(lb):
     rho, T, P = setup()
     r, ux, uy, Tn, st = oracle_run(P, rho, T, 100, False)
-    (gr, gux, guy, gT), tot = gpu_run(lb, P, rho, T, 100, lb.LB_THERMAL_FD26, "fp64")
+    (gr, gux, guy, gT), tot, _ = gpu_run(lb, P, rho, T, 100, lb.LB_THERMAL_FD26, "fp64")
     assert tot[0] == pytest.approx(rho.sum(), rel=1e-13)              # mass of the density LBE
     assert tot[1] == pytest.approx(np.sum(r * Tn), rel=1e-12)         # sum rho c_v T (c_v = 1)
     assert tot[2] == pytest.approx(np.sum(r * ux), rel=1e-9, abs=1e-15)
@@ -104,3 +107,24 @@ def test_fd_rejects_what_does_not_apply(lb):
         assert ei.value.status == lb.LB_ERR_UNSUPPORTED
         L.step(5)
         L.synchronize()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,nx,ny,strip", [("fp64", 64, 64, (128, 0)), ("fp64", 300, 40, (128, 0)),
+                                              ("fp32", 64, 64, (256, 0)), ("fp32", 260, 24, (256, 0))])
+def test_fd_strip_front_matches_tile_front(lb, prec, nx, ny, strip):
+    """The fused strip kernel (whole FD step in one pass, ghost-column
+    layout) and the tile front + fused RK2 give the same bits in FP64, which
+    also match the oracle to 1e-12; FP32 agrees to 1e-6; the lattices include
+    partial last strips."""
+    rho, T, P = setup(nx, ny)
+    (sr, sux, suy, sT), _, shape_s = gpu_run(lb, P, rho, T, 40, lb.LB_THERMAL_FD26, prec, tile=strip)
+    (tr, tux, tuy, tT), _, shape_t = gpu_run(lb, P, rho, T, 40, lb.LB_THERMAL_FD26, prec, tile=(32, 8))
+    assert shape_s == strip and shape_t == (32, 8)
+    if prec == "fp64":
+        for a, b in ((sr, tr), (sux, tux), (suy, tuy), (sT, tT)):
+            assert np.array_equal(a, b)
+        r, ux, uy, Tn, st = oracle_run(P, rho, T, 40, False)
+        assert rel(sr, r) <= 1e-12 and rel(sT, Tn) <= 1e-12
+    else:
+        assert rel(sr, tr) <= 1e-6 and rel(sT, tT) <= 1e-6
