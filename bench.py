@@ -283,6 +283,9 @@ def main():
     ap.add_argument("--seg", type=int, default=SEG, help="LB time steps per bench step")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep run to steady state")
     ap.add_argument("--sweep-cap", type=int, default=60000, help="step cap of the batched sweep")
+    ap.add_argument("--thermal", default="eq24", choices=["eq24", "fd26"],
+                    help="temperature treatment of the timed lattice: Eq. (24) (the headline) "
+                         "or the finite-difference Eqs. (26)-(27) (profiling)")
     ap.add_argument("--sweep-domains", type=int, default=256,
                     help="domains of the batched sweep (profiling: a smaller case)")
     args = ap.parse_args()
@@ -305,7 +308,8 @@ def main():
     args.dist = dist
     stream = torch.cuda.Stream()
     rho, T = I.spinodal_fields(NX, NY)
-    p = workload_params(lb)
+    fd = args.thermal == "fd26"
+    p = workload_params(lb, thermal=lb.LB_THERMAL_FD26 if fd else None)
 
     # ---- device-resident timing
     d_rho = torch.from_numpy(rho).cuda()
@@ -326,7 +330,7 @@ def main():
     updates = sites * SEG * args.steps
     value = world * updates / t / 1e6
     launch_s = t / (SEG * args.steps)
-    alg_bytes = BYTES_PER_SITE["fp32"] * sites
+    alg_bytes = (BYTES_PER_SITE_FD if fd else BYTES_PER_SITE)["fp32"] * sites
     tot = lb.lb_totals(ctx)
     lb.lb_free(ctx)
     del d_rho, d_T
@@ -453,16 +457,18 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
                "sample": f"FP64 oracle steps of a {CPU_SAMPLE}x{CPU_SAMPLE} lattice of the same "
                          f"spinodal recipe ({dt:.1f} s)"}
 
-    traffic = ncu_traffic()
+    fd = getattr(args, "thermal", "eq24") == "fd26"
+    traffic = None if fd else ncu_traffic()
     clocks = clk.summary()
     out = {
         "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"spinodal_{NX}x{NY}_CS_T0.75Tc_rho0.12pm0.01_eq24_fp32",
+        "config": {"workload": f"spinodal_{NX}x{NY}_CS_T0.75Tc_rho0.12pm0.01_{'fd26' if fd else 'eq24'}_fp32",
                    "nx": NX, "ny": NY, "lb_steps_per_bench_step": SEG,
-                   "thermal": "Eq.24", "storage": "fp32", "tau_f": 1.0, "tau_g": 0.8, "G": -1.0,
+                   "thermal": "Eqs.26-27" if fd else "Eq.24", "storage": "fp32", "tau_f": 1.0, "tau_g": 0.8,
+                   "G": -1.0,
                    "force": "Eq.4", "beta": BETA,
                    "l2": "state 2x1.23 GB > 129 MB L2, no flush needed",
                    "parallelism": f"independent lattice per GPU x{world}"},
