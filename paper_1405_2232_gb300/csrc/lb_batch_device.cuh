@@ -3,11 +3,13 @@
 //
 // The fused step is the strip-marching kernel of lb_step_strip.cuh made
 // persistent: a fixed grid of CTAs walks a device-side list of work items
-// (domain, strip, row chunk).  The producer warp and the consumer warps keep
-// one job counter across items, so the producer streams the next item's rows
-// while the consumers still work on the current one.  The list length is read
-// from device memory at launch, so a captured CUDA graph stays valid while
-// converged domains are taken off the list.  As in the single-lattice kernel,
+// (domain, strip, row chunk), each CTA its own contiguous range of the list
+// (the host deals items longest first to the least loaded CTA).  The producer
+// warp and the consumer warps keep one job counter across items, so the
+// producer streams the next item's rows while the consumers still work on the
+// current one.  The ranges are read from device memory at launch, so a
+// captured CUDA graph stays valid while converged domains are taken off the
+// list.  As in the single-lattice kernel,
 // every domain is stored in the ghost-column layout (one bulk copy per plane
 // row, ghost copies written with the row) and a halo warp computes the two
 // halo psi columns.
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     k_batch_step(const typename Store<PREC>::elem* __restrict__ src_base,
                  typename Store<PREC>::elem* __restrict__ dst_base,
                  const BatchDomain* __restrict__ doms, const BatchItem* __restrict__ items,
-                 const int* __restrict__ n_items_ptr) {
+                 const int* __restrict__ cta_off) {
     using S = Store<PREC>;
     using C = StripCfg<PREC>;
     using elem = typename C::elem;
@@ -66,7 +68,9 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
-    const int n_items = *n_items_ptr;
+    // this CTA's work items (contiguous; the lists are read at launch, so a
+    // captured graph stays valid while the host rebuilds them)
+    const int it_begin = cta_off[blockIdx.x], it_end = cta_off[blockIdx.x + 1];
     if (t == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         // ------------------------------------------------ producer warp
         const int lane = t - BX - 32;
         long long jg = 0;  // job counter across this CTA's items
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        for (int it = it_begin; it < it_end; ++it) {
             const BatchItem item = items[it];
             const BatchDomain& D = doms[item.domain];
             const int nx = D.kp.nx, ny = D.kp.ny;
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     // (ring column r holds strip column r - 1; see k_step_strip)
     const bool halo = t >= BX;
     long long jg = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    for (int it = it_begin; it < it_end; ++it) {
         const BatchItem item = items[it];
         const BatchDomain& D = doms[item.domain];
         const KParams kp = D.kp;

@@ -9,7 +9,7 @@
 namespace lbgb {
 
 cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain* doms,
-                                   const BatchItem* items, const int* counts, int eq24, int bmode,
+                                   const BatchItem* items, const int* cta_off, int eq24, int bmode,
                                    int grid, cudaStream_t stream) {
     using E = double;
     constexpr int BX = 128, ST = batch_stages<LB_PREC_FP64, BX>();
@@ -26,7 +26,7 @@ cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain
     // src == nullptr: set the shared-memory attribute only (once, outside capture)
     if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, strip_threads<BX>(), smem, stream>>>(static_cast<const E*>(src), static_cast<E*>(dst), doms,
-                                                   items, counts);
+                                                   items, cta_off);
     return cudaGetLastError();
 }
 

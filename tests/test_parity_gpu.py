@@ -251,7 +251,7 @@ def test_fp32_eq7_local_T_first_steps(lb):
                                         ((64, 64), (128, 0))])
 def test_fp64_strip_kernel_ragged(lb, shape, tile):
     """Strip kernel on partial strips, one-strip lattices and few-row chunks: still bit
-    for bit with the oracle (periodic halo copies at both ends of every row)."""
+    for bit with the oracle (the periodic ghost columns at both ends of every row)."""
     ny, nx = shape
     rho, T = I.slab_fields(nx, ny, width=max(2, nx // 2), noise=1e-3)
     P = oracle_params(O.THERMAL_EQ24, nx=nx, ny=ny)
@@ -260,6 +260,23 @@ def test_fp64_strip_kernel_ragged(lb, shape, tile):
     with gpu_lattice(lb, rho, T, O.THERMAL_EQ24, "fp64", tile_x=tile[0], tile_y=tile[1]) as L:
         assert lb.lb_get_params(L.ctx).tile_y == 0
         L.step(25)
+        f, g = L.populations()
+    assert np.array_equal(f, f_ref, equal_nan=True) and np.array_equal(g, g_ref, equal_nan=True)
+
+
+@pytest.mark.parametrize("shape", [(24, 200), (9, 130), (16, 4)])
+def test_fp64_strip_set_populations_then_step(lb, shape):
+    """Populations written through lb_set_populations (which also writes the
+    strip layout's ghost columns) step on bit for bit with the oracle."""
+    ny, nx = shape
+    rho, T = I.slab_fields(nx, ny, width=max(2, nx // 2), noise=1e-3)
+    P = oracle_params(O.THERMAL_EQ24, nx=nx, ny=ny)
+    f0, g0 = O.init_equilibrium(P, rho, T)
+    f1, g1, _ = O.step(P, f0, g0, n=20, check=False)
+    f_ref, g_ref, _ = O.step(P, f1, g1, n=10, check=False)
+    with gpu_lattice(lb, rho * 0 + 0.2, T, O.THERMAL_EQ24, "fp64", tile_x=128, tile_y=0) as L:
+        L.set_populations(f1, g1)
+        L.step(10)
         f, g = L.populations()
     assert np.array_equal(f, f_ref, equal_nan=True) and np.array_equal(g, g_ref, equal_nan=True)
 
