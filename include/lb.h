@@ -72,9 +72,13 @@ enum {
      * and rho, u (with F/2) of the density LBE at time n in both stages.
      * FD26: Heun, h2 = K(T^n + dt h1); FD26_PRINTED: h2 = K(T^n + dt/2 h1) as
      * printed with Eq. (27).  Storage FP64 or FP32 only (else
-     * LB_ERR_UNSUPPORTED); tile kernel only (tile_y == 0 is LB_ERR_ARG);
-     * not available in the batched solver; lb_get/set_populations and the
-     * state calls return LB_ERR_UNSUPPORTED (there is no g). */
+     * LB_ERR_UNSUPPORTED).  Kernels: the whole step in one strip pass
+     * (tile (256, 0) in FP32, (128, 0) in FP64; nx >= 8; the FP32 default
+     * where the strip rules hold), or the 32x8 tile front followed by one
+     * launch of both RK2 stages (any other tile_y != 0 request runs 32x8;
+     * the FP64 default); another strip width is LB_ERR_ARG.  Not available
+     * in the batched solver; lb_get/set_populations and the state calls
+     * return LB_ERR_UNSUPPORTED (there is no g). */
     LB_THERMAL_FD26 = 2,
     LB_THERMAL_FD26_PRINTED = 3
 };
