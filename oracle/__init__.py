@@ -71,6 +71,12 @@ class OracleParams(ctypes.Structure):
     ]
 
 
+class OracleCavity(ctypes.Structure):
+    """Side-wall temperatures and gravity of the cavity (Sec. III B)."""
+    _fields_ = [("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("g_grav", ctypes.c_double)]
+
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off, OpenMP on)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -163,6 +169,13 @@ def _bind(lib):
     lib.or_fd_rk2.restype = ctypes.c_int
     lib.or_step_fd.argtypes = [P, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
     lib.or_step_fd.restype = ctypes.c_int
+    Cv = ctypes.POINTER(OracleCavity)
+    lib.or_step_cavity.argtypes = [P, Cv, dp, dp, dp, dp, ctypes.c_int]
+    lib.or_step_cavity.restype = ctypes.c_int
+    lib.or_nusselt_hot.argtypes = [P, Cv, dp]
+    lib.or_nusselt_hot.restype = ctypes.c_double
+    lib.or_nusselt_hot_flux.argtypes = [P, Cv, dp, dp]
+    lib.or_nusselt_hot_flux.restype = ctypes.c_double
     return lib
 
 
@@ -338,3 +351,61 @@ def critical_point(P):
 
 def threads_available():
     return _load().or_num_threads_available()
+
+
+# ------------------------------------------------------------------ cavity
+def cavity(T_hot=1.03, T_cold=0.97, g_grav=0.0):
+    return OracleCavity(float(T_hot), float(T_cold), float(g_grav))
+
+
+def cavity_setup(Ra, L, thermal=THERMAL_EQ24, T_hot=1.03, T_cold=0.97, mu=0.1, Pr=0.71, rho0=1.0):
+    """Parameters of the natural-convection cavity of Sec. III B on an L x L
+    lattice: ideal EOS with R = 1/3 (c = sqrt(3 R T_c) = 1 at T_c = 1), the
+    pseudopotential in the beta = 0 form of Eq. (4), tau_f from mu = rho0 cs^2
+    (tau_f - 1/2), tau_g from Pr = nu / chi with chi = cs^2 (tau_g - 1/2), and g
+    from Eq. (28) with beta_T = 1/T_c.  Returns (P, Cv)."""
+    Tc = 0.5 * (T_hot + T_cold)
+    R = 1.0 / (3.0 * Tc)
+    nu = mu / rho0
+    tau_f = 0.5 + 3.0 * nu
+    tau_g = 0.5 + 3.0 * nu / Pr
+    g = Ra * mu * mu / ((1.0 / Tc) * rho0 * rho0 * (T_hot - T_cold) * L ** 3 * Pr)
+    P = params(L, L, tau_f=tau_f, tau_g=tau_g, G=-1.0, beta=0.0, eos=EOS_IDEAL, R=R, cv=1.0,
+               thermal=thermal, psi_uses_local_T=1)
+    return P, cavity(T_hot, T_cold, g)
+
+
+def step_cavity(P, Cv, f, g, n=1, threads=1, check=True):
+    """Advance the cavity state (f, g) by n steps; returns (f, g, status)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    fn = np.empty_like(f)
+    gn = np.empty_like(g)
+    lib = _load()
+    worst = OK
+    for _ in range(int(n)):
+        rc = lib.or_step_cavity(ctypes.byref(P), ctypes.byref(Cv), _ptr(f), _ptr(g), _ptr(fn), _ptr(gn),
+                                int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step_cavity: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        g, gn = gn, g
+    if check and worst:
+        raise FloatingPointError(f"oracle cavity step reported status {worst}")
+    return f, g, worst
+
+
+def nusselt_hot(P, Cv, T):
+    """Average Nusselt number at the hot wall from the temperature gradient
+    (as Table II), T [ny, nx]."""
+    T = _field(T, P)
+    return _load().or_nusselt_hot(ctypes.byref(P), ctypes.byref(Cv), _ptr(T))
+
+
+def nusselt_hot_flux(P, Cv, f, g):
+    """Average Nusselt number at the hot wall from the energy flux through the
+    wall links of the pre-collision state."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return _load().or_nusselt_hot_flux(ctypes.byref(P), ctypes.byref(Cv), _ptr(f), _ptr(g))

@@ -11,7 +11,8 @@
  *
  * State convention: the arrays hold the PRE-collision populations f_i(x,t)
  * and g_i(x,t) in structure-of-arrays order, index  i*ny*nx + y*nx + x,
- * on a periodic nx-by-ny lattice.  One step applies, at every site, the
+ * on a periodic nx-by-ny lattice (the cavity of Sec. III B: or_step_cavity).
+ * One step applies, at every site, the
  * collision of Eq. (1) (density) and Eq. (7) or Eq. (24) (temperature) and
  * then streams the post-collision value to x + e_i, giving f_i(x,t+1).
  *
@@ -186,19 +187,11 @@ static int macroscopic_fields(const or_params* P, const double* f, const double*
  * F = -G [ beta psi(x) sum_i w ψ(x+e_i) e_i + (1-beta)/2 sum_i w ψ^2(x+e_i) e_i ]
  * with w(1) = 1/3 on the axes and w(2) = 1/12 on the diagonals.  Each sum is
  * grouped into the pairs of opposite directions.                           */
-static void force_at(const or_params* P, const double* psi, const double* psi2,
-                     int x, int y, double* Fx, double* Fy)
+static void force_sum(const or_params* P, const double* psi, const double* psi2, int64_t C,
+                      int64_t E, int64_t W, int64_t N_, int64_t S, int64_t NE, int64_t NW,
+                      int64_t SW, int64_t SE, double* Fx, double* Fy)
 {
-    const int nx = P->nx, ny = P->ny;
     const double w1 = 1.0 / 3.0, w2 = 1.0 / 12.0;
-    int xe = wrap(x + 1, nx), xw = wrap(x - 1, nx);
-    int yn = wrap(y + 1, ny), ys = wrap(y - 1, ny);
-    int64_t E = (int64_t)y * nx + xe, W = (int64_t)y * nx + xw;
-    int64_t N_ = (int64_t)yn * nx + x, S = (int64_t)ys * nx + x;
-    int64_t NE = (int64_t)yn * nx + xe, NW = (int64_t)yn * nx + xw;
-    int64_t SW = (int64_t)ys * nx + xw, SE = (int64_t)ys * nx + xe;
-    int64_t C = (int64_t)y * nx + x;
-
     double fx = 0.0, fy = 0.0;
     if (P->beta != 0.0) {
         double s1x = w1 * (psi[E] - psi[W]) + w2 * ((psi[NE] - psi[SW]) + (psi[SE] - psi[NW]));
@@ -214,6 +207,17 @@ static void force_at(const or_params* P, const double* psi, const double* psi2,
     }
     *Fx = -P->G * fx;
     *Fy = -P->G * fy;
+}
+
+static void force_at(const or_params* P, const double* psi, const double* psi2,
+                     int x, int y, double* Fx, double* Fy)
+{
+    const int nx = P->nx, ny = P->ny;
+    int xe = wrap(x + 1, nx), xw = wrap(x - 1, nx);
+    int yn = wrap(y + 1, ny), ys = wrap(y - 1, ny);
+    force_sum(P, psi, psi2, (int64_t)y * nx + x, (int64_t)y * nx + xe, (int64_t)y * nx + xw,
+              (int64_t)yn * nx + x, (int64_t)ys * nx + x, (int64_t)yn * nx + xe,
+              (int64_t)yn * nx + xw, (int64_t)ys * nx + xw, (int64_t)ys * nx + xe, Fx, Fy);
 }
 
 /* Collision of one site: Eq. (1) with F_i for f, and Eq. (7) (or Eq. (24)
@@ -253,6 +257,148 @@ static int check_params(const or_params* P)
         return OR_ERR_ARG;
     if (P->eos < 0 || P->eos > 2 || P->thermal < 0 || P->thermal > 1) return OR_ERR_ARG;
     return OR_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Natural convection in a square cavity (Sec. III B).  nx-by-ny fluid
+ * nodes enclosed by walls half a lattice spacing outside the outermost
+ * nodes (so the distance between the side walls is L = nx).  The paper
+ * does not state its boundary treatment; readings (listed in the design
+ * notes):
+ *   - f: halfway bounce-back on every wall (no slip): a population that
+ *     would stream into a wall returns to its node with the opposite
+ *     direction, f_{-i}(x, t+1) = f*_i(x, t).
+ *   - g on the adiabatic bottom and top walls: the same bounce-back (no
+ *     energy flux through the wall).
+ *   - g on the isothermal side walls (T_h at x = -1/2, T_l at x = nx - 1/2):
+ *     anti-bounce-back, g_{-i}(x, t+1) = -g*_i(x, t) + 2 w_i rho(x) c_v T_w,
+ *     which holds rho c_v T = rho c_v T_w at the wall to second order.  A
+ *     population that reaches a corner (outside in both x and y) takes the
+ *     side-wall rule.
+ *   - the pseudopotential at a wall node is that of the nearest fluid node
+ *     (the force stencil reads psi^2 at clamped coordinates).
+ *   - buoyancy: G = (0, -rho g) is added to the pseudopotential force
+ *     (Sec. III B: with the ideal EOS no Boussinesq assumption is needed).
+ * The step otherwise is or_step: same fields, force, collision.           */
+typedef struct or_cavity {
+    double T_hot, T_cold; /* side-wall temperatures (left, right) */
+    double g_grav;        /* gravity acceleration along -y        */
+} or_cavity;
+
+static int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
+
+static void force_at_clamped(const or_params* P, const double* psi, const double* psi2,
+                             int x, int y, double* Fx, double* Fy)
+{
+    const int nx = P->nx, ny = P->ny;
+    int xe = clampi(x + 1, nx), xw = clampi(x - 1, nx);
+    int yn = clampi(y + 1, ny), ys = clampi(y - 1, ny);
+    force_sum(P, psi, psi2, (int64_t)y * nx + x, (int64_t)y * nx + xe, (int64_t)y * nx + xw,
+              (int64_t)yn * nx + x, (int64_t)ys * nx + x, (int64_t)yn * nx + xe,
+              (int64_t)yn * nx + xw, (int64_t)ys * nx + xw, (int64_t)ys * nx + xe, Fx, Fy);
+}
+
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+/* One cavity step, t -> t+1 (state convention as or_step, walls as above). */
+int or_step_cavity(const or_params* P, const or_cavity* Cv, const double* f, const double* g,
+                   double* fn, double* gn, int nthreads)
+{
+    int err = check_params(P);
+    if (err) return err;
+    if (!Cv) return OR_ERR_ARG;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* T = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    if (!rho || !T || !psi || !psi2) {
+        free(rho); free(T); free(psi); free(psi2);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    err = macroscopic_fields(P, f, g, rho, T, psi, psi2, nthreads);
+
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = g[i * N + s];
+            }
+            force_at_clamped(P, psi, psi2, x, y, &Fx, &Fy);
+            Fy += -rho[s] * Cv->g_grav;
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, NULL, NULL);
+            for (int i = 0; i < 9; ++i) {
+                int xd = x + EX[i], yd = y + EY[i];
+                int out_x = xd < 0 || xd >= nx, out_y = yd < 0 || yd >= ny;
+                if (!out_x && !out_y) {
+                    int64_t d = (int64_t)yd * nx + xd;
+                    fn[i * N + d] = fs[i];
+                    gn[i * N + d] = gs[i];
+                } else {
+                    int o = OPP[i];
+                    fn[o * N + s] = fs[i];
+                    if (out_x) {
+                        double Tw = xd < 0 ? Cv->T_hot : Cv->T_cold;
+                        gn[o * N + s] = -gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Tw;
+                    } else {
+                        gn[o * N + s] = gs[i];
+                    }
+                }
+            }
+        }
+    }
+    free(rho); free(T); free(psi); free(psi2);
+    return err;
+}
+
+/* Average Nusselt number at the hot wall (x = -1/2), as Table II reports it:
+ * Nu = (L / (T_h - T_l)) < -dT/dx >_y at the wall, L = nx, with dT/dx at the
+ * wall from the quadratic through the first three nodes (distances 1/2, 3/2,
+ * 5/2 from the wall): dT/dx = -2 T(0) + 3 T(1) - T(2).                     */
+double or_nusselt_hot(const or_params* P, const or_cavity* Cv, const double* T)
+{
+    const int nx = P->nx, ny = P->ny;
+    double acc = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const int64_t s = (int64_t)y * nx;
+        acc += -(-2.0 * T[s] + 3.0 * T[s + 1] - T[s + 2]);
+    }
+    return (double)nx / (Cv->T_hot - Cv->T_cold) * (acc / ny);
+}
+
+/* The same from the energy that crosses the hot-wall links in one step (the
+ * method's own flux; it sees lambda_eff of Eq. (23), not lambda): a
+ * population g*_i (i = 3, 6, 7, pointing into the wall) leaves node (0, y)
+ * and g_{-i} = -g*_i + 2 w_i rho c_v T_h comes back, so the energy entering
+ * the fluid is sum_i 2 (g_{-i}(0, y) - w_i rho c_v T_h) over the
+ * pre-collision state at steady state.  Nu = <q>_y / (lambda0 (T_h - T_l) / L)
+ * with lambda0 = rho0 c_v cs^2 (tau_g - 1/2), rho0 the mean density.      */
+double or_nusselt_hot_flux(const or_params* P, const or_cavity* Cv, const double* f, const double* g)
+{
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    static const int IN_WALL[3] = {3, 6, 7};
+    double mass = 0.0;
+    for (int i = 0; i < 9; ++i)
+        for (int64_t s = 0; s < N; ++s) mass += f[i * N + s];
+    const double rho0 = mass / (double)N;
+    double q = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const int64_t s = (int64_t)y * nx;
+        double rho = 0.0;
+        for (int i = 0; i < 9; ++i) rho += f[i * N + s];
+        for (int k = 0; k < 3; ++k) {
+            const int i = IN_WALL[k];
+            q += 2.0 * (g[OPP[i] * N + s] - OMEGA[i] * rho * P->cv * Cv->T_hot);
+        }
+    }
+    const double lambda0 = rho0 * P->cv * CS2 * (P->tau_g - 0.5);
+    return (q / ny) / (lambda0 * (Cv->T_hot - Cv->T_cold) / (double)nx);
 }
 
 /* ---------------------------------------------------------------------- */
