@@ -93,6 +93,20 @@ enum {
     LB_PREC_BF16_DEV = 3
 };
 
+/* Boundaries (Sec. III B).  PERIODIC: the periodic lattice.  CAVITY: the
+ * natural-convection cavity: nx-by-ny fluid nodes inside walls half a
+ * lattice spacing outside the outermost nodes (side-wall distance L = nx);
+ * f bounces back on every wall (no slip); g bounces back on the adiabatic
+ * bottom and top walls and anti-bounces back on the side walls, which hold
+ * T_hot (left) and T_cold (right): g_{-i}(x, t+1) = -g*_i(x, t) + 2 w_i
+ * rho(x, t) c_v T_w (a link that leaves through a corner takes the side-wall
+ * rule); psi at a wall node is that of the nearest fluid node; the buoyancy
+ * (0, -rho g_grav) is added to the force.  The populations are then stored
+ * pre-collision at their site and pushed after the collision.  Cavity
+ * contexts: Eq. (7) or (24), FP64 or FP32, the 32x8 tile kernel (tile_y == 0
+ * is LB_ERR_ARG), not in the batched solver. */
+enum { LB_WALLS_PERIODIC = 0, LB_WALLS_CAVITY = 1 };
+
 /* Numbers of lb_totals outputs. */
 enum { LB_TOTALS_N = 5 };
 enum { LB_TUNE_N = 5 };        /* step shapes lb_autotune tries        */
@@ -113,13 +127,18 @@ typedef struct lb_params {
     double cv;             /* specific heat at constant volume (g^eq = c_v T f^eq), > 0 */
     double T_psi;          /* temperature used by psi when psi_uses_local_T == 0       */
     double rho0, T0;       /* deviation base of the 16-bit storage modes               */
+    int32_t walls;         /* LB_WALLS_PERIODIC or LB_WALLS_CAVITY                     */
+    int32_t reserved;      /* 0                                                        */
+    double T_hot, T_cold;  /* cavity: left (x = -1/2) and right (x = nx - 1/2) walls   */
+    double g_grav;         /* cavity: gravity along -y, buoyancy (0, -rho g) added to F */
 } lb_params;
 
 typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
 
 /* Fill *p with the defaults: 64x64, CS EOS a=1 b=4 R=1, G=-1, beta=1,
  * tau_f=1, tau_g=0.8, c_v=1, Eq. (24), FP32, psi from the local T,
- * rho0 = 0.12, T0 = 0.075. */
+ * rho0 = 0.12, T0 = 0.075, periodic (cavity fields T_hot = 1.03,
+ * T_cold = 0.97, g_grav = 0). */
 void lb_params_default(lb_params* p);
 
 /* Create a context whose initial state is f = f^eq(rho0, u = 0) and

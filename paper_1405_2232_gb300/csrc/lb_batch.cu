@@ -294,6 +294,8 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
             return err(LB_ERR_ARG, "domain %d: precision, thermal treatment and force form must match domain 0", d);
         if (p.nx < 3 || p.ny < 3 || p.nx % halo != 0)
             return err(LB_ERR_ARG, "domain %d: nx must be >= 3 and a multiple of %d, ny >= 3", d, halo);
+        if (p.walls != LB_WALLS_PERIODIC)
+            return err(LB_ERR_UNSUPPORTED, "domain %d: the batched solver runs periodic domains", d);
         if (!(p.tau_f > 0.5) || !(p.tau_g > 0.5) || p.G == 0.0 || !(p.cv > 0.0) || p.eos < 0 || p.eos > 2 ||
             p.thermal < 0 || p.thermal > 1)
             return err(LB_ERR_ARG, "domain %d: invalid parameters", d);

@@ -64,6 +64,18 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
     if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
+    if (p->walls != LB_WALLS_PERIODIC && p->walls != LB_WALLS_CAVITY)
+        return fail(LB_ERR_ARG, "unknown boundary kind %d", p->walls);
+    if (p->walls == LB_WALLS_CAVITY) {
+        if (p->thermal != LB_THERMAL_EQ7 && p->thermal != LB_THERMAL_EQ24)
+            return fail(LB_ERR_UNSUPPORTED, "the cavity runs Eq. (7) or Eq. (24)");
+        if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
+            return fail(LB_ERR_UNSUPPORTED, "the cavity stores FP64 or FP32");
+        if ((p->tile_x || p->tile_y) && !(p->tile_x == 32 && p->tile_y == 8))
+            return fail(LB_ERR_ARG, "the cavity runs the 32x8 tile kernel");
+        if (!std::isfinite(p->T_hot) || !std::isfinite(p->T_cold) || !std::isfinite(p->g_grav))
+            return fail(LB_ERR_ARG, "cavity wall temperatures and gravity must be finite");
+    }
     if (p->thermal >= LB_THERMAL_FD26) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment stores FP64 or FP32 only");
@@ -178,6 +190,10 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
     k.cv = p.cv;
     k.inv_cv = 1.0 / p.cv;
     k.T_psi = p.T_psi;
+    k.walls = p.walls == LB_WALLS_CAVITY ? 1 : 0;
+    k.T_hot = p.T_hot;
+    k.T_cold = p.T_cold;
+    k.g_grav = p.g_grav;
     const bool dev = p.precision == LB_PREC_FP16_DEV || p.precision == LB_PREC_BF16_DEV;
     for (int i = 0; i < 9; ++i) {
         k.base_f[i] = dev ? (float)(wd(i) * p.rho0) : 0.0f;
@@ -198,6 +214,8 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.by = c->p.tile_y;
     L.nchunks = c->nchunks;
     L.stream = c->stream;
+    if (c->kp.walls)
+        return c->p.precision == LB_PREC_FP64 ? launch_step_cavity_fp64(L) : launch_step_cavity_fp32(L);
     switch (c->p.precision) {
         case LB_PREC_FP64: return launch_step_fp64(L);
         case LB_PREC_FP32: return launch_step_fp32(L);
@@ -361,6 +379,10 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         c->p.tile_x = FD_BX;  // the FD tile front end has one tile shape
         c->p.tile_y = FD_BY;
     }
+    if (p->walls == LB_WALLS_CAVITY) {
+        c->p.tile_x = 32;  // the cavity kernel's tile
+        c->p.tile_y = 8;
+    }
     // kernel choice: the strip-marching TMA kernel where its alignment rules
     // hold, else the tile kernel
     if (c->p.tile_x == 0 && c->p.tile_y == 0) {
@@ -465,6 +487,10 @@ void lb_params_default(lb_params* p) {
     p->T_psi = 0.0;
     p->rho0 = 0.12;
     p->T0 = 0.075;
+    p->walls = LB_WALLS_PERIODIC;
+    p->T_hot = 1.03;
+    p->T_cold = 0.97;
+    p->g_grav = 0.0;
 }
 
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,

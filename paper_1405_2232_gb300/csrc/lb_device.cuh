@@ -86,6 +86,8 @@ struct KParams {
     int eos;
     int psi_local_T;
     int ghost;         // periodic ghost columns kept on each side of every row (0 or 2)
+    int walls;         // 0 periodic; 1 cavity (populations stored pre-collision at their site)
+    double T_hot, T_cold, g_grav;  // cavity side walls and gravity
     double a, b, R;
     double cv, inv_cv;
     double T_psi;
@@ -144,11 +146,28 @@ __device__ __forceinline__ int wrapc(int v, int n) {
     return v;
 }
 
+// clamp a coordinate into [0, n) (cavity: a wall node takes its nearest fluid node)
+__device__ __forceinline__ int clampc(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
+
+// ring coordinate of a halo site: periodic wrap, or the nearest fluid node in a cavity
+__device__ __forceinline__ int ringc(const KParams& kp, int v, int n) {
+    return kp.walls ? clampc(v, n) : wrapc(v, n);
+}
+
 // Pull the 18 pre-collision populations of site (x, y).
 template <class S>
 __device__ __forceinline__ void pull18(const typename S::elem* __restrict__ src,
                                        const KParams& kp, int x, int y,
                                        typename S::real f[9], typename S::real g[9]) {
+    if (kp.walls) {  // cavity: populations stored pre-collision at their own site
+        const long long off = (long long)y * kp.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            f[i] = S::load(src + (long long)i * kp.plane + off, (typename S::real)kp.base_f[i]);
+            g[i] = S::load(src + (long long)(9 + i) * kp.plane + off, (typename S::real)kp.base_g[i]);
+        }
+        return;
+    }
     const int xm = x == 0 ? kp.nx - 1 : x - 1;
     const int xp = x == kp.nx - 1 ? 0 : x + 1;
     const long long r0 = (long long)y * kp.pitch;
@@ -411,7 +430,7 @@ __global__ void __launch_bounds__(BX* BY)
     int flags = 0;
     for (int s = tid; s < WX * WY; s += NT) {
         const int ly = s / WX, lx = s - ly * WX;
-        const int gx = wrapc(x0 + lx - 1, kp.nx), gy = wrapc(y0 + ly - 1, kp.ny);
+        const int gx = ringc(kp, x0 + lx - 1, kp.nx), gy = ringc(kp, y0 + ly - 1, kp.ny);
         real f[9], g[9], rho, T, psi, psi2;
         pull18<S>(src, kp, gx, gy, f, g);
         site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
@@ -436,6 +455,7 @@ __global__ void __launch_bounds__(BX* BY)
         real Fx, Fy, ux, uy, T;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1,
                                        WX, Fx, Fy);
+        if (kp.walls) Fy += -rho * (real)kp.g_grav;  // cavity buoyancy
         collide<real, false>(kp, f, g, rho, Fx, Fy, ux, uy, T);
         const long long idx = (long long)gy * kp.nx + gx;
         if (o_rho) o_rho[idx] = (double)rho;
@@ -492,7 +512,8 @@ __global__ void k_init(typename Store<PREC>::elem* __restrict__ dst, const KPara
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             // the value stored at (x, y) is pulled by site (x + e_i, y + e_i)
-            const int dx = wrapc(x + ex(i), kp.nx), dy = wrapc(y + ey(i), kp.ny);
+            // (cavity: stored pre-collision at its own site)
+            const int dx = kp.walls ? x : wrapc(x + ex(i), kp.nx), dy = kp.walls ? y : wrapc(y + ey(i), kp.ny);
             const long long d = (long long)dy * kp.nx + dx;
             const double fe = rho0[d] * wd(i);
             const double ge = kp.cv * T0[d] * fe;
@@ -539,8 +560,8 @@ __global__ void k_scatter(typename Store<PREC>::elem* __restrict__ dst, const KP
         const int x = (int)(s % kp.nx), y = (int)(s / kp.nx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            // f_i(x, t) is stored at x - e_i
-            const int sx = wrapc(x - ex(i), kp.nx), sy = wrapc(y - ey(i), kp.ny);
+            // f_i(x, t) is stored at x - e_i (cavity: at x)
+            const int sx = kp.walls ? x : wrapc(x - ex(i), kp.nx), sy = kp.walls ? y : wrapc(y - ey(i), kp.ny);
             const long long off = (long long)sy * kp.pitch + sx;
             typename S::elem* pf = dst + (long long)i * kp.plane + off;
             typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;

@@ -3,6 +3,7 @@
 // value) and LBGB_NAME (the suffix of the launch functions).
 #pragma once
 
+#include "lb_cavity.cuh"
 #include "lb_fd.cuh"
 #include "lb_fd_strip.cuh"
 #include "lb_launch.h"
@@ -158,6 +159,33 @@ cudaError_t LBGB_CAT(launch_scatter_, LBGB_NAME)(void* dst, const KParams& kp, c
     using E = typename Store<LBGB_PREC>::elem;
     k_scatter<LBGB_PREC><<<elementwise_blocks(kp), 256, 0, st>>>(static_cast<E*>(dst), kp, in);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ cavity (Sec. III B)
+cudaError_t LBGB_CAT(launch_step_cavity_, LBGB_NAME)(const StepLaunch& L) {
+    if constexpr (LBGB_PREC != LB_PREC_FP64 && LBGB_PREC != LB_PREC_FP32) {
+        return cudaErrorNotSupported;
+    } else {
+        using E = typename Store<LBGB_PREC>::elem;
+        const dim3 block(CAV_BX, CAV_BY);
+        const dim3 grid((L.kp.nx + CAV_BX - 1) / CAV_BX, (L.kp.ny + CAV_BY - 1) / CAV_BY);
+        const E* src = static_cast<const E*>(L.src);
+        E* dst = static_cast<E*>(L.dst);
+        if (L.eq24) {
+            switch (L.bmode) {
+                case BETA_ZERO: k_step_cavity<LBGB_PREC, true, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                case BETA_ONE: k_step_cavity<LBGB_PREC, true, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                default: k_step_cavity<LBGB_PREC, true, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            }
+        } else {
+            switch (L.bmode) {
+                case BETA_ZERO: k_step_cavity<LBGB_PREC, false, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                case BETA_ONE: k_step_cavity<LBGB_PREC, false, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                default: k_step_cavity<LBGB_PREC, false, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            }
+        }
+        return cudaGetLastError();
+    }
 }
 
 // ------------------------------------------------ finite-difference T (Eqs. 26-27)
