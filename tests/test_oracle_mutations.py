@@ -79,3 +79,41 @@ def test_planted_mistake_is_caught(name, old, new):
                 caught = exc
                 break
     assert caught is not None, f"no pin catches the planted mistake {name}"
+
+
+# ---------------------------------------------------------------- cavity
+import test_oracle_cavity as cav  # noqa: E402
+
+CAVITY_MUTATIONS = [
+    ("cavity_gravity_dropped", "Fy += -rho[s] * Cv->g_grav;", ""),
+    ("cavity_isothermal_wall_adiabatic",
+     "gn[o * N + s] = -gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Tw;", "gn[o * N + s] = gs[i];"),
+    ("cavity_wall_temperatures_swapped", "double Tw = xd < 0 ? Cv->T_hot : Cv->T_cold;",
+     "double Tw = xd < 0 ? Cv->T_cold : Cv->T_hot;"),
+    ("cavity_anti_bounce_weight", "-gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Tw;",
+     "-gs[i] + 2.0 * OMEGA[o] * rho[s] * P->cv * Tw + (i > 4 ? 1e-3 : 0.0);"),
+    ("cavity_psi_wraps", "int xe = clampi(x + 1, nx), xw = clampi(x - 1, nx);",
+     "int xe = wrap(x + 1, nx), xw = wrap(x - 1, nx);"),
+]
+
+CAVITY_PINS = [
+    cav.test_uniform_state_at_wall_temperature_is_steady,
+    cav.test_mass_conserved_and_gravity_stratifies,
+    cav.test_conduction_nusselt_is_one,
+]
+
+
+@pytest.mark.parametrize("name,old,new", CAVITY_MUTATIONS, ids=[m[0] for m in CAVITY_MUTATIONS])
+def test_planted_cavity_mistake_is_caught(name, old, new):
+    src = O.source_text()
+    assert src.count(old) == 1, f"mutation anchor not unique/present: {old}"
+    lib = O.build_variant(src.replace(old, new), name)
+    caught = None
+    with O.using(lib):
+        for pin in CAVITY_PINS:
+            try:
+                pin()
+            except (AssertionError, FloatingPointError, ValueError) as exc:
+                caught = exc
+                break
+    assert caught is not None, f"no cavity pin catches the planted mistake {name}"
