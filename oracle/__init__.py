@@ -176,6 +176,10 @@ def _bind(lib):
     lib.or_nusselt_hot.restype = ctypes.c_double
     lib.or_nusselt_hot_flux.argtypes = [P, Cv, dp, dp]
     lib.or_nusselt_hot_flux.restype = ctypes.c_double
+    lib.or_step_fd_cavity.argtypes = [P, Cv, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    lib.or_step_fd_cavity.restype = ctypes.c_int
+    lib.or_nusselt_hot_wall.argtypes = [P, Cv, dp, dp]
+    lib.or_nusselt_hot_wall.restype = ctypes.c_double
     return lib
 
 
@@ -409,3 +413,34 @@ def nusselt_hot_flux(P, Cv, f, g):
     f = np.ascontiguousarray(f, dtype=np.float64)
     g = np.ascontiguousarray(g, dtype=np.float64)
     return _load().or_nusselt_hot_flux(ctypes.byref(P), ctypes.byref(Cv), _ptr(f), _ptr(g))
+
+
+def step_fd_cavity(P, Cv, f, T, n=1, printed=False, threads=1, check=True):
+    """n steps of the hybrid scheme in the cavity; returns (f, T, status, (rho, ux, uy))."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    T = _field(T, P).copy()
+    fn, Tn = np.empty_like(f), np.empty_like(T)
+    rho, ux, uy = (np.zeros((P.ny, P.nx)) for _ in range(3))
+    worst = OK
+    for _ in range(int(n)):
+        rc = _load().or_step_fd_cavity(ctypes.byref(P), ctypes.byref(Cv), _ptr(f), _ptr(T), _ptr(fn), _ptr(Tn),
+                                       int(bool(printed)), _ptr(rho), _ptr(ux), _ptr(uy), int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step_fd_cavity: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        T, Tn = Tn, T
+    if check and worst:
+        raise FloatingPointError(f"oracle FD cavity step reported status {worst}")
+    return f, T, worst, (rho, ux, uy)
+
+
+def nusselt_hot_wall(P, Cv, T, rho=None):
+    """Nusselt number at the hot wall from the central difference across it
+    (T at the wall imposed through the reflected ghost, the FD treatment);
+    with rho, the conductive flux lambda(rho) dT/dx normalised by lambda0."""
+    T = _field(T, P)
+    if rho is None:
+        return _load().or_nusselt_hot_wall(ctypes.byref(P), ctypes.byref(Cv), _ptr(T), None)
+    rho = _field(rho, P)
+    return _load().or_nusselt_hot_wall(ctypes.byref(P), ctypes.byref(Cv), _ptr(T), _ptr(rho))

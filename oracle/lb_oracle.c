@@ -300,6 +300,16 @@ static void force_at_clamped(const or_params* P, const double* psi, const double
 
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
+/* Force at a cavity node: the pseudopotential force with psi at a wall node
+ * taken from its nearest fluid node, plus the buoyancy (0, -rho g).       */
+static void cavity_force(const or_params* P, const or_cavity* Cv, const double* psi,
+                         const double* psi2, const double* rho, int x, int y, double* Fx,
+                         double* Fy)
+{
+    force_at_clamped(P, psi, psi2, x, y, Fx, Fy);
+    *Fy += -rho[(int64_t)y * P->nx + x] * Cv->g_grav;
+}
+
 /* One cavity step, t -> t+1 (state convention as or_step, walls as above). */
 int or_step_cavity(const or_params* P, const or_cavity* Cv, const double* f, const double* g,
                    double* fn, double* gn, int nthreads)
@@ -329,8 +339,7 @@ int or_step_cavity(const or_params* P, const or_cavity* Cv, const double* f, con
                 fl[i] = f[i * N + s];
                 gl[i] = g[i * N + s];
             }
-            force_at_clamped(P, psi, psi2, x, y, &Fx, &Fy);
-            Fy += -rho[s] * Cv->g_grav;
+            cavity_force(P, Cv, psi, psi2, rho, x, y, &Fx, &Fy);
             collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, NULL, NULL);
             for (int i = 0; i < 9; ++i) {
                 int xd = x + EX[i], yd = y + EY[i];
@@ -694,6 +703,29 @@ int or_num_threads_available(void)
  * Eq. (27): T^{n+1} = T^n + (dt/2)(h1 + h2), h1 = K(T^n), h2 = K(T^n + a dt h1)
  * with a = 1/2 as printed, or a = 1 (Heun's second-order method, which the
  * printed form is not); dt = 1.                                            */
+/* K of Eq. (26) at one site from the values at its 8 neighbours (index i =
+ * 1..8 in the lattice order) and at the site itself:
+ *   grad phi = (1/cs^2) sum_i w_i e_i phi(x + e_i),
+ *   lap phi  = (2/cs^2) sum_i w_i (phi(x + e_i) - phi(x)).                  */
+static double fd_K_site(const double Tn[9], const double rn[9], double Tc, double rc, double ux,
+                        double uy, double chi)
+{
+    double gTx = 0.0, gTy = 0.0, grx = 0.0, gry = 0.0, lap = 0.0;
+    for (int i = 1; i < 9; ++i) {
+        gTx += OMEGA[i] * EX[i] * Tn[i];
+        gTy += OMEGA[i] * EY[i] * Tn[i];
+        grx += OMEGA[i] * EX[i] * rn[i];
+        gry += OMEGA[i] * EY[i] * rn[i];
+        lap += OMEGA[i] * (Tn[i] - Tc);
+    }
+    gTx /= CS2;
+    gTy /= CS2;
+    grx /= CS2;
+    gry /= CS2;
+    lap *= 2.0 / CS2;
+    return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / rc);
+}
+
 void or_fd_rhs(const or_params* P, const double* T, const double* rho, const double* ux,
                const double* uy, double* K)
 {
@@ -702,21 +734,13 @@ void or_fd_rhs(const or_params* P, const double* T, const double* rho, const dou
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
             const int64_t c = (int64_t)y * nx + x;
-            double gTx = 0.0, gTy = 0.0, grx = 0.0, gry = 0.0, lap = 0.0;
+            double Tn[9], rn[9];
             for (int i = 1; i < 9; ++i) {
                 const int64_t n = (int64_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
-                gTx += OMEGA[i] * EX[i] * T[n];
-                gTy += OMEGA[i] * EY[i] * T[n];
-                grx += OMEGA[i] * EX[i] * rho[n];
-                gry += OMEGA[i] * EY[i] * rho[n];
-                lap += OMEGA[i] * (T[n] - T[c]);
+                Tn[i] = T[n];
+                rn[i] = rho[n];
             }
-            gTx /= CS2;
-            gTy /= CS2;
-            grx /= CS2;
-            gry /= CS2;
-            lap *= 2.0 / CS2;
-            K[c] = -(ux[c] * gTx + uy[c] * gTy) + chi * (lap + (grx * gTx + gry * gTy) / rho[c]);
+            K[c] = fd_K_site(Tn, rn, T[c], rho[c], ux[c], uy[c], chi);
         }
     }
 }
@@ -810,4 +834,139 @@ int or_step_fd(const or_params* P, const double* f, const double* T, double* fn,
     if (uy_out) memcpy(uy_out, uy, sizeof(double) * N);
     free(rho); free(psi); free(psi2); free(ux); free(uy);
     return err;
+}
+
+/* ---------------------------------------------------------------------- */
+/* The hybrid scheme (Eqs. 26-27) in the cavity of Sec. III B.  The density
+ * LBE takes the cavity rules of or_step_cavity (bounce-back, clamped psi,
+ * buoyancy); K of Eq. (26) reads its neighbours through the walls as ghost
+ * values (reading listed in the design notes): across a side wall the
+ * temperature is reflected about the wall value, 2 T_w - X(mirror node),
+ * which puts X = T_w at the wall to second order; across the adiabatic
+ * bottom and top walls X(mirror node) (zero normal gradient); rho is
+ * mirrored everywhere; a neighbour outside in x takes the side-wall rule.
+ * The intermediate temperature of the second stage uses the same rule.     */
+static void fd_rhs_cavity(const or_params* P, const or_cavity* Cv, const double* X,
+                          const double* rho, const double* ux, const double* uy, double* K)
+{
+    const int nx = P->nx, ny = P->ny;
+    const double chi = (P->tau_g - 0.5) * CS2;
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t c = (int64_t)y * nx + x;
+            double Xn[9], rn[9];
+            for (int i = 1; i < 9; ++i) {
+                const int xn = x + EX[i], yn = y + EY[i];
+                const int64_t m = (int64_t)clampi(yn, ny) * nx + clampi(xn, nx);
+                rn[i] = rho[m];
+                if (xn < 0 || xn >= nx) {
+                    const double Tw = xn < 0 ? Cv->T_hot : Cv->T_cold;
+                    Xn[i] = 2.0 * Tw - X[m];
+                } else {
+                    Xn[i] = X[m];
+                }
+            }
+            K[c] = fd_K_site(Xn, rn, X[c], rho[c], ux[c], uy[c], chi);
+        }
+    }
+}
+
+int or_step_fd_cavity(const or_params* P, const or_cavity* Cv, const double* f, const double* T,
+                      double* fn, double* Tn, int printed, double* rho_out, double* ux_out,
+                      double* uy_out, int nthreads)
+{
+    if (!P || !Cv || P->nx < 3 || P->ny < 3 || !(P->tau_f > 0.5) || !(P->tau_g > 0.5) ||
+        P->G == 0.0 || !(P->cv > 0.0) || P->eos < 0 || P->eos > 2)
+        return OR_ERR_ARG;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* h1 = (double*)malloc(sizeof(double) * N);
+    double* h2 = (double*)malloc(sizeof(double) * N);
+    double* Ts = (double*)malloc(sizeof(double) * N);
+    if (!rho || !psi || !psi2 || !ux || !uy || !h1 || !h2 || !Ts) {
+        free(rho); free(psi); free(psi2); free(ux); free(uy); free(h1); free(h2); free(Ts);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    int err = OR_OK;
+    for (int64_t s = 0; s < N; ++s) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[i * N + s];
+        rho[s] = r;
+        const double Te = P->psi_uses_local_T ? T[s] : P->T_psi;
+        psi2[s] = or_psi_sq(P, r, Te);
+        psi[s] = 0.0;
+        if (!isfinite(r) || !isfinite(T[s])) err = err < OR_ERR_NONFINITE ? OR_ERR_NONFINITE : err;
+        if (P->beta != 0.0) {
+            if (psi2[s] < 0.0) {
+                err = OR_ERR_PSI_DOMAIN;
+                psi[s] = NAN;
+            } else {
+                psi[s] = sqrt(psi2[s]);
+            }
+        }
+    }
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = 0.0;
+            }
+            cavity_force(P, Cv, psi, psi2, rho, x, y, &Fx, &Fy);
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, &ux[s], &uy[s]);
+            for (int i = 0; i < 9; ++i) {
+                const int xd = x + EX[i], yd = y + EY[i];
+                if (xd >= 0 && xd < nx && yd >= 0 && yd < ny)
+                    fn[i * N + (int64_t)yd * nx + xd] = fs[i];
+                else
+                    fn[OPP[i] * N + s] = fs[i];
+            }
+        }
+    }
+    const double a = printed ? 0.5 : 1.0;
+    fd_rhs_cavity(P, Cv, T, rho, ux, uy, h1);
+    for (int64_t s = 0; s < N; ++s) Ts[s] = T[s] + a * h1[s];
+    fd_rhs_cavity(P, Cv, Ts, rho, ux, uy, h2);
+    for (int64_t s = 0; s < N; ++s) {
+        Tn[s] = T[s] + 0.5 * (h1[s] + h2[s]);
+        if (!isfinite(Tn[s])) err = err < OR_ERR_NONFINITE ? OR_ERR_NONFINITE : err;
+    }
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * N);
+    if (ux_out) memcpy(ux_out, ux, sizeof(double) * N);
+    if (uy_out) memcpy(uy_out, uy, sizeof(double) * N);
+    free(rho); free(psi); free(psi2); free(ux); free(uy); free(h1); free(h2); free(Ts);
+    return err;
+}
+
+/* Nusselt number at the hot wall of a temperature field with the wall value
+ * imposed through the reflected ghost (the FD treatment).  The conductive
+ * flux through the wall is lambda dT/dx with lambda = rho c_v cs^2 (tau_g -
+ * 1/2) at the first node (the ghost mirrors rho) and dT/dx the central
+ * difference across the wall, T(0) - (2 T_h - T(0)); it is normalised by
+ * lambda0 (T_h - T_l) / L with the mean density, like or_nusselt_hot_flux.
+ * rho may be NULL: the gradient alone (lambda = lambda0).                  */
+double or_nusselt_hot_wall(const or_params* P, const or_cavity* Cv, const double* T,
+                           const double* rho)
+{
+    const int nx = P->nx, ny = P->ny;
+    double rho0 = 1.0;
+    if (rho) {
+        double m = 0.0;
+        for (int64_t s = 0; s < (int64_t)nx * ny; ++s) m += rho[s];
+        rho0 = m / ((double)nx * ny);
+    }
+    double acc = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const double w = rho ? rho[(int64_t)y * nx] / rho0 : 1.0;
+        acc += -2.0 * w * (T[(int64_t)y * nx] - Cv->T_hot);
+    }
+    return (double)nx / (Cv->T_hot - Cv->T_cold) * (acc / ny);
 }

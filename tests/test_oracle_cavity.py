@@ -78,3 +78,21 @@ def test_table2_ra1e3_eq24_and_eq7(L, steps):
     # Eq. (7): the forcing-term effect flattens lambda_eff near the side walls and
     # steepens the wall gradient (Table II: 4.884 against 1.118)
     assert nu7_grad > 2.5 * TABLE_II_EQ24_RA1E3, nu7_grad
+
+
+TABLE_II_FD_RA1E3 = 1.118  # Table II, finite-difference Eq. (26), Ra = 10^3
+
+
+def test_fd_cavity_table2_ra1e3():
+    """The hybrid scheme (Eqs. 26-27) in the cavity: Table II's FD column at
+    Ra = 10^3 on a 40 x 40 lattice (the wall temperature enters through the
+    reflected ghost, so the wall gradient is the central difference across it)."""
+    L = 40
+    P, Cv = O.cavity_setup(1e3, L)
+    f, _ = _start(P, L)
+    T = np.ones((L, L))
+    f, T, st, _ = O.step_fd_cavity(P, Cv, f, T, n=40000, threads=8)
+    assert st == O.OK
+    rho = O.moments(P, f, np.zeros_like(f))[0]
+    nu = O.nusselt_hot_wall(P, Cv, T, rho)      # conductive wall flux, lambda(rho) dT/dx
+    assert nu == pytest.approx(TABLE_II_FD_RA1E3, rel=0.02), nu

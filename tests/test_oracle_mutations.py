@@ -85,7 +85,7 @@ def test_planted_mistake_is_caught(name, old, new):
 import test_oracle_cavity as cav  # noqa: E402
 
 CAVITY_MUTATIONS = [
-    ("cavity_gravity_dropped", "Fy += -rho[s] * Cv->g_grav;", ""),
+    ("cavity_gravity_dropped", "*Fy += -rho[(int64_t)y * P->nx + x] * Cv->g_grav;", ""),
     ("cavity_isothermal_wall_adiabatic",
      "gn[o * N + s] = -gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Tw;", "gn[o * N + s] = gs[i];"),
     ("cavity_wall_temperatures_swapped", "double Tw = xd < 0 ? Cv->T_hot : Cv->T_cold;",
