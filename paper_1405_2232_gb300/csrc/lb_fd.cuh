@@ -22,6 +22,7 @@
 // order of its printed form (compiled without contraction).
 #pragma once
 
+#include "lb_cavity.cuh"
 #include "lb_device.cuh"
 
 namespace lbgb {
@@ -32,6 +33,13 @@ constexpr int FD_BX = 32, FD_BY = 8;
 template <class S>
 __device__ __forceinline__ void pull9(const typename S::elem* __restrict__ src, const KParams& kp, int x,
                                       int y, typename S::real f[9]) {
+    if (kp.walls) {  // cavity: stored pre-collision at the site
+        const long long off = (long long)y * kp.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = S::load(src + (long long)i * kp.plane + off, (typename S::real)kp.base_f[i]);
+        return;
+    }
     const int xm = x == 0 ? kp.nx - 1 : x - 1;
     const int xp = x == kp.nx - 1 ? 0 : x + 1;
     const long long r0 = (long long)y * kp.pitch;
@@ -64,7 +72,8 @@ __device__ __forceinline__ void site_psi_T(const KParams& kp, real r, real T, re
 
 // Density step (STEP) or moments (!STEP) of the FD treatment.
 //   STEP:  f (src, pre-collision at n) -> dst (post-collision, stored at the
-//          source site); rho_n, ux_n, uy_n <- rho^n, u^n.
+//          source site; cavity: pushed, bounced back at the walls);
+//          rho_n, ux_n, uy_n <- rho^n, u^n.
 //   !STEP: m_rho, m_ux, m_uy, m_T (FP64, any may be null) <- rho, u, T at n.
 template <int PREC, int BMODE, bool STEP>
 __global__ void __launch_bounds__(FD_BX* FD_BY)
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
     int flags = 0;
     for (int s = tid; s < WX * WY; s += NT) {
         const int ly = s / WX, lx = s - ly * WX;
-        const int gx = wrapc(x0 + lx - 1, kp.nx), gy = wrapc(y0 + ly - 1, kp.ny);
+        const int gx = ringc(kp, x0 + lx - 1, kp.nx), gy = ringc(kp, y0 + ly - 1, kp.ny);
         real f[9], psi, psi2;
         pull9<S>(src, kp, gx, gy, f);
         real r = f[0];
@@ -105,13 +114,27 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
         for (int i = 1; i < 9; ++i) rho += f[i];
         real Fx, Fy, ux, uy, Tg;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1, WX, Fx, Fy);
+        if (kp.walls) Fy += -rho * (real)kp.g_grav;  // cavity buoyancy
         // the f half of the collision; g (zero here) is not used
         collide<real, false>(kp, f, g, rho, Fx, Fy, ux, uy, Tg);
         const long long c = (long long)gy * kp.nx + gx;
         if (STEP) {
             const long long off = (long long)gy * kp.pitch + gx;
+            if (kp.walls) {
+                // cavity: push to x + e_i, bounce back from the walls
 #pragma unroll
-            for (int i = 0; i < 9; ++i) S::put(dst + (long long)i * kp.plane + off, f[i], (real)kp.base_f[i]);
+                for (int i = 0; i < 9; ++i) {
+                    const int xd = gx + ex(i), yd = gy + ey(i);
+                    if (xd >= 0 && xd < kp.nx && yd >= 0 && yd < kp.ny)
+                        S::put(dst + (long long)i * kp.plane + (long long)yd * kp.pitch + xd, f[i],
+                               (real)kp.base_f[i]);
+                    else
+                        S::put(dst + (long long)opp(i) * kp.plane + off, f[i], (real)kp.base_f[opp(i)]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) S::put(dst + (long long)i * kp.plane + off, f[i], (real)kp.base_f[i]);
+            }
             rho_n[c] = rho;
             ux_n[c] = ux;
             uy_n[c] = uy;

@@ -365,15 +365,26 @@ __global__ void __launch_bounds__(FDR_BX* FDR_BY)
     const long long pitch = kp.pitch;
     const int tid = threadIdx.x + threadIdx.y * FDR_BX;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    // cavity (kp.walls): a neighbour across a side wall reads the temperature
+    // reflected about the wall value, 2 T_w - T(mirror node); across the
+    // adiabatic walls T(mirror node); rho and u the mirror node's
+    const bool walls = kp.walls != 0;
     for (int s = tid; s < H2 * W2; s += NT) {
         const int ly = s / W2, lx = s - ly * W2;
-        const int gx = wrapc(x0 + lx - 2, nx), gy = wrapc(y0 + ly - 2, ny);
-        sT[s] = T[(long long)gy * pitch + gx];
+        const int rx = x0 + lx - 2, ry = y0 + ly - 2;
+        const int gx = ringc(kp, rx, nx), gy = ringc(kp, ry, ny);
+        const real Tv = T[(long long)gy * pitch + gx];
+        if (walls && (rx < 0 || rx >= nx)) {
+            const real Tw = rx < 0 ? (real)kp.T_hot : (real)kp.T_cold;
+            sT[s] = (real)2.0 * Tw - Tv;
+        } else {
+            sT[s] = Tv;
+        }
         sR[s] = rho[(long long)gy * nx + gx];
     }
     for (int s = tid; s < H1 * W1; s += NT) {
         const int ly = s / W1, lx = s - ly * W1;
-        const int gx = wrapc(x0 + lx - 1, nx), gy = wrapc(y0 + ly - 1, ny);
+        const int gx = ringc(kp, x0 + lx - 1, nx), gy = ringc(kp, y0 + ly - 1, ny);
         sUx[s] = ux[(long long)gy * nx + gx];
         sUy[s] = uy[(long long)gy * nx + gx];
     }
@@ -381,12 +392,31 @@ __global__ void __launch_bounds__(FDR_BX* FDR_BY)
     // stage 1 on the tile and its ring: h1 = K(T^n), Ts = T^n + a h1
     for (int s = tid; s < H1 * W1; s += NT) {
         const int ly = s / W1, lx = s - ly * W1;
+        const int rx = x0 + lx - 1, ry = y0 + ly - 1;
+        if (walls && (rx < 0 || rx >= nx || ry < 0 || ry >= ny)) continue;  // ghost: filled below
         const int c2 = (ly + 1) * W2 + lx + 1;
         const real K = fd_K_tile<real>(sT, W2, c2, sR, W2, c2, sUx[s], sUy[s], chi);
         sH1[s] = K;
         sTs[s] = sT[c2] + a * K;
     }
     __syncthreads();
+    if (walls) {
+        // intermediate temperature at the ghost sites of the ring, by the same rule
+        for (int s = tid; s < H1 * W1; s += NT) {
+            const int ly = s / W1, lx = s - ly * W1;
+            const int rx = x0 + lx - 1, ry = y0 + ly - 1;
+            if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) continue;
+            const int mx = clampc(rx, nx) - x0 + 1, my = clampc(ry, ny) - y0 + 1;
+            const real Tm = sTs[my * W1 + mx];
+            if (rx < 0 || rx >= nx) {
+                const real Tw = rx < 0 ? (real)kp.T_hot : (real)kp.T_cold;
+                sTs[s] = (real)2.0 * Tw - Tm;
+            } else {
+                sTs[s] = Tm;
+            }
+        }
+        __syncthreads();
+    }
     // stage 2 on the tile: T^{n+1} = T^n + (h1 + K(Ts)) / 2
     int flags = 0;
 #pragma unroll
