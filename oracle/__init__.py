@@ -71,6 +71,12 @@ class OracleParams(ctypes.Structure):
     ]
 
 
+class OracleChannel(ctypes.Structure):
+    """Inlet and plate conditions of the channel (Sec. III A)."""
+    _fields_ = [("T_in", ctypes.c_double), ("T_w", ctypes.c_double), ("U_in", ctypes.c_double),
+                ("adiabatic_bottom", ctypes.c_int32)]
+
+
 class OracleCavity(ctypes.Structure):
     """Side-wall temperatures and gravity of the cavity (Sec. III B)."""
     _fields_ = [("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("g_grav", ctypes.c_double)]
@@ -180,6 +186,13 @@ def _bind(lib):
     lib.or_step_fd_cavity.restype = ctypes.c_int
     lib.or_nusselt_hot_wall.argtypes = [P, Cv, dp, dp]
     lib.or_nusselt_hot_wall.restype = ctypes.c_double
+    Ch = ctypes.POINTER(OracleChannel)
+    lib.or_step_channel.argtypes = [P, Ch, dp, dp, dp, dp, ctypes.c_int]
+    lib.or_step_channel.restype = ctypes.c_int
+    lib.or_channel_nusselt.argtypes = [P, Ch, dp, dp, dp, dp, ctypes.c_int]
+    lib.or_channel_nusselt.restype = ctypes.c_double
+    lib.or_channel_nusselt_grad.argtypes = [P, Ch, dp, dp, dp, ctypes.c_int]
+    lib.or_channel_nusselt_grad.restype = ctypes.c_double
     return lib
 
 
@@ -444,3 +457,53 @@ def nusselt_hot_wall(P, Cv, T, rho=None):
         return _load().or_nusselt_hot_wall(ctypes.byref(P), ctypes.byref(Cv), _ptr(T), None)
     rho = _field(rho, P)
     return _load().or_nusselt_hot_wall(ctypes.byref(P), ctypes.byref(Cv), _ptr(T), _ptr(rho))
+
+
+# ------------------------------------------------------------------ channel
+def channel_setup(nx, ny, case="A", thermal=THERMAL_EQ24, T_in=1.03, T_w=0.97, U_in=0.05, mu=0.1, Pr=0.71,
+                  rho0=1.0):
+    """Parameters of the plate-channel test of Sec. III A on an nx x ny
+    lattice: ideal EOS with R = 1/3 (c = sqrt(3 R T_c) = 1 at T_c = (T_in +
+    T_w)/2 = 1), the pseudopotential in the beta = 0 form of Eq. (4), tau_f
+    from mu = rho0 cs^2 (tau_f - 1/2), tau_g from Pr.  Case A: both plates at
+    T_w; Case B: the lower plate adiabatic.  Returns (P, Ch)."""
+    Tc = 0.5 * (T_in + T_w)
+    nu = mu / rho0
+    P = params(nx, ny, tau_f=0.5 + 3.0 * nu, tau_g=0.5 + 3.0 * nu / Pr, G=-1.0, beta=0.0, eos=EOS_IDEAL,
+               R=1.0 / (3.0 * Tc), cv=1.0, thermal=thermal, psi_uses_local_T=1)
+    return P, OracleChannel(float(T_in), float(T_w), float(U_in), 1 if case == "B" else 0)
+
+
+def step_channel(P, Ch, f, g, n=1, threads=1, check=True):
+    """Advance the channel state (f, g) by n steps; returns (f, g, status)."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    g = np.ascontiguousarray(g, dtype=np.float64).copy()
+    fn = np.empty_like(f)
+    gn = np.empty_like(g)
+    lib = _load()
+    worst = OK
+    for _ in range(int(n)):
+        rc = lib.or_step_channel(ctypes.byref(P), ctypes.byref(Ch), _ptr(f), _ptr(g), _ptr(fn), _ptr(gn),
+                                 int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step_channel: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        g, gn = gn, g
+    if check and worst:
+        raise FloatingPointError(f"oracle channel step reported status {worst}")
+    return f, g, worst
+
+
+def channel_nusselt(P, Ch, g, rho, ux, T, x):
+    """Local Nusselt number at column x from the upper plate's heat flux."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    rho, ux, T = (_field(a, P) for a in (rho, ux, T))
+    return _load().or_channel_nusselt(ctypes.byref(P), ctypes.byref(Ch), _ptr(g), _ptr(rho), _ptr(ux), _ptr(T),
+                                      int(x))
+
+
+def channel_nusselt_grad(P, Ch, rho, ux, T, x):
+    """Local Nusselt number at column x from the temperature gradient at the upper plate."""
+    rho, ux, T = (_field(a, P) for a in (rho, ux, T))
+    return _load().or_channel_nusselt_grad(ctypes.byref(P), ctypes.byref(Ch), _ptr(rho), _ptr(ux), _ptr(T), int(x))

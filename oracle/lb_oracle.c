@@ -970,3 +970,166 @@ double or_nusselt_hot_wall(const or_params* P, const or_cavity* Cv, const double
     }
     return (double)nx / (Cv->T_hot - Cv->T_cold) * (acc / ny);
 }
+
+/* ---------------------------------------------------------------------- */
+/* Thermal flow between parallel plates (Sec. III A): nx-by-ny fluid nodes,
+ * plates half a lattice spacing below y = 0 and above y = ny - 1 (gap
+ * H = ny), inlet plane half a spacing left of x = 0, outlet plane half a
+ * spacing right of x = nx - 1.  The paper gives no boundary scheme;
+ * readings (listed in the design notes):
+ *   - plates: f halfway bounce-back (no slip); g anti-bounce-back at T_w on
+ *     the upper plate and, in Case A, on the lower plate; in Case B the
+ *     lower plate is adiabatic (g bounce-back).  A link through a corner
+ *     takes the plate rule.
+ *   - inlet (uniform U_in, T_in): f bounce-back with the wall velocity,
+ *     f_{-i} = f*_i - 2 w_i rho (e_i . u_in) / cs^2; g anti-bounce-back at
+ *     T_in with the symmetric part of the equilibrium at u_in,
+ *     g_{-i} = -g*_i + 2 w_i rho c_v T_in (1 + (e_i.u_in)^2 / (2 cs^4)
+ *     - |u_in|^2 / (2 cs^2)).
+ *   - outlet (fully developed, pressure level rho0 = 1): f anti-bounce-back
+ *     at the outlet density with the velocity of the node,
+ *     f_{-i} = -f*_i + 2 w_i rho0 (1 + (e_i.u)^2 / (2 cs^4) - |u|^2 / (2 cs^2));
+ *     g: after streaming, the populations that would come from beyond the
+ *     outlet are copied from the column nx - 2 (zero gradient).
+ *   - psi at a node outside is that of the nearest fluid node; no gravity.
+ * State convention as or_step (pre-collision at the node).                 */
+typedef struct or_channel {
+    double T_in, T_w, U_in;
+    int32_t adiabatic_bottom; /* 0: Case A, 1: Case B */
+} or_channel;
+
+int or_step_channel(const or_params* P, const or_channel* Ch, const double* f, const double* g,
+                    double* fn, double* gn, int nthreads)
+{
+    int err = check_params(P);
+    if (err) return err;
+    if (!Ch || P->nx < 3) return OR_ERR_ARG;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* T = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    if (!rho || !T || !psi || !psi2) {
+        free(rho); free(T); free(psi); free(psi2);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    err = macroscopic_fields(P, f, g, rho, T, psi, psi2, nthreads);
+    const double uin = Ch->U_in;
+
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = g[i * N + s];
+            }
+            force_at_clamped(P, psi, psi2, x, y, &Fx, &Fy);
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, NULL, NULL);
+            for (int i = 0; i < 9; ++i) {
+                const int xd = x + EX[i], yd = y + EY[i];
+                const int o = OPP[i];
+                if (yd < 0 || yd >= ny) {
+                    /* plate */
+                    fn[o * N + s] = fs[i];
+                    if (yd < 0 && Ch->adiabatic_bottom)
+                        gn[o * N + s] = gs[i];
+                    else
+                        gn[o * N + s] = -gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Ch->T_w;
+                } else if (xd < 0) {
+                    /* inlet */
+                    const double eu = EX[i] * uin;
+                    fn[o * N + s] = fs[i] - 2.0 * OMEGA[i] * rho[s] * eu / CS2;
+                    gn[o * N + s] = -gs[i] + 2.0 * OMEGA[i] * rho[s] * P->cv * Ch->T_in *
+                                                 (1.0 + 0.5 * eu * eu / (CS2 * CS2) - 0.5 * uin * uin / CS2);
+                } else if (xd < nx) {
+                    const int64_t d = (int64_t)yd * nx + xd;
+                    fn[i * N + d] = fs[i];
+                    gn[i * N + d] = gs[i];
+                } else {
+                    /* outlet: f at the outlet density; g replaced below */
+                    double ux, uy;
+                    {
+                        double mx = 0.0, my = 0.0;
+                        for (int k = 0; k < 9; ++k) {
+                            mx += EX[k] * fl[k];
+                            my += EY[k] * fl[k];
+                        }
+                        ux = (mx + 0.5 * Fx) / rho[s];
+                        uy = (my + 0.5 * Fy) / rho[s];
+                    }
+                    const double eu = EX[i] * ux + EY[i] * uy;
+                    fn[o * N + s] = -fs[i] + 2.0 * OMEGA[i] * 1.0 *
+                                                 (1.0 + 0.5 * eu * eu / (CS2 * CS2) - 0.5 * (ux * ux + uy * uy) / CS2);
+                }
+            }
+        }
+    }
+    /* outlet: g arriving from beyond x = nx - 1 (source right of the outlet
+     * and inside the plates) copies column nx - 2 */
+    for (int y = 0; y < ny; ++y) {
+        for (int i = 0; i < 9; ++i) {
+            if (EX[i] != -1) continue;
+            const int ys = y - EY[i];
+            if (ys < 0 || ys >= ny) continue; /* set by the plate rule */
+            const int64_t a = (int64_t)y * nx + (nx - 1), b = (int64_t)y * nx + (nx - 2);
+            gn[i * N + a] = gn[i * N + b];
+        }
+    }
+    free(rho); free(T); free(psi); free(psi2);
+    return err;
+}
+
+/* Local Nusselt number along the channel at column x (Sec. III A):
+ * Nu(x) = D_h q_w / (lambda (T_w - T_b)), D_h = 2 H = 2 ny, T_b the bulk
+ * temperature sum(rho u_x T) / sum(rho u_x) over the column, q_w the heat
+ * the upper plate's links pass into the fluid per step (as
+ * or_nusselt_hot_flux) and lambda = rho c_v cs^2 (tau_g - 1/2) with the
+ * density of the node next to the plate.  rho, ux, T: moments [ny][nx]. */
+double or_channel_nusselt(const or_params* P, const or_channel* Ch, const double* g,
+                          const double* rho, const double* ux, const double* T, int x)
+{
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    static const int IN_TOP[3] = {2, 5, 6};
+    double num = 0.0, den = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const int64_t s = (int64_t)y * nx + x;
+        num += rho[s] * ux[s] * T[s];
+        den += rho[s] * ux[s];
+    }
+    const double Tb = num / den;
+    const int64_t s = (int64_t)(ny - 1) * nx + x;
+    double q = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int i = IN_TOP[k];
+        q += 2.0 * (g[OPP[i] * N + s] - OMEGA[i] * rho[s] * P->cv * Ch->T_w);
+    }
+    const double lambda = rho[s] * P->cv * CS2 * (P->tau_g - 0.5);
+    return 2.0 * ny * q / (lambda * (Ch->T_w - Tb));
+}
+
+/* The same with q_w / lambda replaced by the temperature gradient at the
+ * upper plate, from the quadratic through the three nodes next to it
+ * (distances 1/2, 3/2, 5/2): dT/dn = -2 T(ny-1) + 3 T(ny-2) - T(ny-3) toward
+ * the fluid.  This is the reading under which Eq. (7) reads high.          */
+double or_channel_nusselt_grad(const or_params* P, const or_channel* Ch, const double* rho,
+                               const double* ux, const double* T, int x)
+{
+    const int nx = P->nx, ny = P->ny;
+    double num = 0.0, den = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const int64_t s = (int64_t)y * nx + x;
+        num += rho[s] * ux[s] * T[s];
+        den += rho[s] * ux[s];
+    }
+    const double Tb = num / den;
+    const double T0 = T[(int64_t)(ny - 1) * nx + x], T1 = T[(int64_t)(ny - 2) * nx + x];
+    const double T2 = T[(int64_t)(ny - 3) * nx + x];
+    const double dTdn = -2.0 * T0 + 3.0 * T1 - T2; /* d T / d(distance from the plate) */
+    /* heat into the fluid per lambda: -dT/dn at the plate (flux along -n) */
+    return 2.0 * ny * (-dTdn) / (Ch->T_w - Tb);
+}

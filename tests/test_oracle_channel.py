@@ -1,0 +1,51 @@
+"""The oracle's plate channel (Sec. III A) pinned to what the paper and the
+mathematics fix: a uniform state at rest (inlet, outlet and plates at one
+temperature, no inflow) stays put; with inflow and no heating the fully
+developed flow is plane Poiseuille flow carrying the inlet flux; with the
+plates cooling the flow the thermally fully developed Nusselt numbers are the
+analytical 7.54 (Case A, both plates at T_w) and 4.86 (Case B, lower plate
+adiabatic) quoted with Table I (the paper's corrected LB gives 7.51, 4.91)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+NU_ANALYTICAL = {"A": 7.54, "B": 4.86}  # Table I, analytical [28]
+
+
+def _start(P):
+    return O.init_equilibrium(P, np.ones((P.ny, P.nx)), np.ones((P.ny, P.nx)))
+
+
+def test_uniform_state_at_rest_is_steady():
+    P, Ch = O.channel_setup(24, 10, "A", T_in=1.0, T_w=1.0, U_in=0.0)
+    f0, g0 = _start(P)
+    f, g, st = O.step_channel(P, Ch, f0, g0, n=50)
+    assert st == O.OK
+    assert np.abs(f - f0).max() < 1e-15 and np.abs(g - g0).max() < 1e-15
+
+
+def test_isothermal_inflow_is_poiseuille():
+    P, Ch = O.channel_setup(120, 20, "A", T_in=1.0, T_w=1.0)
+    f, g = _start(P)
+    f, g, _ = O.step_channel(P, Ch, f, g, n=12000, threads=8)
+    rho, ux, uy, T, _, _ = O.moments(P, f, g)
+    col = ux[:, 80]
+    H = P.ny
+    y = np.arange(H) + 0.5                  # distance from the lower plate (halfway walls)
+    mean = col.mean()
+    parab = 6.0 * mean * y * (H - y) / H**2
+    assert np.abs(col - parab).max() < 0.02 * col.max()
+    assert (rho[:, 80] * ux[:, 80]).sum() == pytest.approx(H * Ch.U_in * rho[:, 0].mean(), rel=0.03)
+    assert np.abs(uy[:, 80]).max() < 1e-3 * Ch.U_in
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_table1_fully_developed_nusselt(case):
+    P, Ch = O.channel_setup(250, 30, case)
+    f, g = _start(P)
+    f, g, _ = O.step_channel(P, Ch, f, g, n=20000, threads=8)
+    rho, ux, uy, T, _, _ = O.moments(P, f, g)
+    nus = [O.channel_nusselt(P, Ch, g, rho, ux, T, x) for x in range(100, 201, 20)]
+    assert np.ptp(nus) < 0.02 * np.mean(nus)              # fully developed: flat in x
+    assert np.mean(nus) == pytest.approx(NU_ANALYTICAL[case], rel=0.04), nus
