@@ -105,7 +105,18 @@ enum {
  * pre-collision at their site and pushed after the collision.  Cavity
  * contexts: Eq. (7) or (24), FP64 or FP32, the 32x8 tile kernel (tile_y == 0
  * is LB_ERR_ARG), not in the batched solver. */
-enum { LB_WALLS_PERIODIC = 0, LB_WALLS_CAVITY = 1 };
+/* CHANNEL (Sec. III A): flow between parallel plates half a spacing below
+ * y = 0 and above y = ny - 1 (gap H = ny); f bounces back on the plates; g
+ * anti-bounces back at T_w on the upper plate and, in Case A, on the lower
+ * one (Case B: lower plate adiabatic, g bounces back); the inlet (half a
+ * spacing left of x = 0) bounces f back with the wall velocity (U_in, 0),
+ * f_{-i} = f*_i - 2 w_i rho (e_i.u_in)/cs^2, and g anti-bounces back at T_in
+ * with the symmetric equilibrium at u_in; the outlet (half a spacing right of
+ * x = nx - 1) anti-bounces f back at density 1 with the node's velocity, and
+ * copies g from column nx - 2 (zero gradient); psi outside = psi of the
+ * nearest node; no gravity.  Eq. (7) or (24), FP64 or FP32, the 32x8 tile
+ * kernel, not in the batched solver, nx >= 3. */
+enum { LB_WALLS_PERIODIC = 0, LB_WALLS_CAVITY = 1, LB_WALLS_CHANNEL = 2 };
 
 /* Numbers of lb_totals outputs. */
 enum { LB_TOTALS_N = 5 };
@@ -127,10 +138,11 @@ typedef struct lb_params {
     double cv;             /* specific heat at constant volume (g^eq = c_v T f^eq), > 0 */
     double T_psi;          /* temperature used by psi when psi_uses_local_T == 0       */
     double rho0, T0;       /* deviation base of the 16-bit storage modes               */
-    int32_t walls;         /* LB_WALLS_PERIODIC or LB_WALLS_CAVITY                     */
-    int32_t reserved;      /* 0                                                        */
+    int32_t walls;         /* LB_WALLS_PERIODIC, LB_WALLS_CAVITY or LB_WALLS_CHANNEL   */
+    int32_t adiabatic_bottom; /* channel: 0 Case A (both plates at T_w), 1 Case B      */
     double T_hot, T_cold;  /* cavity: left (x = -1/2) and right (x = nx - 1/2) walls   */
     double g_grav;         /* cavity: gravity along -y, buoyancy (0, -rho g) added to F */
+    double T_in, T_w, U_in; /* channel: inlet temperature and velocity, plate temperature */
 } lb_params;
 
 typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
@@ -138,7 +150,8 @@ typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
 /* Fill *p with the defaults: 64x64, CS EOS a=1 b=4 R=1, G=-1, beta=1,
  * tau_f=1, tau_g=0.8, c_v=1, Eq. (24), FP32, psi from the local T,
  * rho0 = 0.12, T0 = 0.075, periodic (cavity fields T_hot = 1.03,
- * T_cold = 0.97, g_grav = 0). */
+ * T_cold = 0.97, g_grav = 0; channel fields T_in = 1.03, T_w = 0.97,
+ * U_in = 0.05, Case A). */
 void lb_params_default(lb_params* p);
 
 /* Create a context whose initial state is f = f^eq(rho0, u = 0) and

@@ -64,8 +64,18 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "unknown thermal treatment %d", p->thermal);
     if (p->precision < LB_PREC_FP64 || p->precision > LB_PREC_BF16_DEV)
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
-    if (p->walls != LB_WALLS_PERIODIC && p->walls != LB_WALLS_CAVITY)
+    if (p->walls != LB_WALLS_PERIODIC && p->walls != LB_WALLS_CAVITY && p->walls != LB_WALLS_CHANNEL)
         return fail(LB_ERR_ARG, "unknown boundary kind %d", p->walls);
+    if (p->walls == LB_WALLS_CHANNEL) {
+        if (p->thermal != LB_THERMAL_EQ7 && p->thermal != LB_THERMAL_EQ24)
+            return fail(LB_ERR_UNSUPPORTED, "the channel runs Eq. (7) or Eq. (24)");
+        if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
+            return fail(LB_ERR_UNSUPPORTED, "the channel stores FP64 or FP32");
+        if ((p->tile_x || p->tile_y) && !(p->tile_x == 32 && p->tile_y == 8))
+            return fail(LB_ERR_ARG, "the channel runs the 32x8 tile kernel");
+        if (!std::isfinite(p->T_in) || !std::isfinite(p->T_w) || !std::isfinite(p->U_in) || p->g_grav != 0.0)
+            return fail(LB_ERR_ARG, "channel inlet and plate values must be finite, g_grav 0");
+    }
     if (p->walls == LB_WALLS_CAVITY) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the cavity stores FP64 or FP32");
@@ -188,10 +198,14 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
     k.cv = p.cv;
     k.inv_cv = 1.0 / p.cv;
     k.T_psi = p.T_psi;
-    k.walls = p.walls == LB_WALLS_CAVITY ? 1 : 0;
+    k.walls = p.walls;
+    k.adiabatic_bottom = p.adiabatic_bottom ? 1 : 0;
     k.T_hot = p.T_hot;
     k.T_cold = p.T_cold;
     k.g_grav = p.g_grav;
+    k.T_in = p.T_in;
+    k.T_w = p.T_w;
+    k.U_in = p.U_in;
     const bool dev = p.precision == LB_PREC_FP16_DEV || p.precision == LB_PREC_BF16_DEV;
     for (int i = 0; i < 9; ++i) {
         k.base_f[i] = dev ? (float)(wd(i) * p.rho0) : 0.0f;
@@ -212,6 +226,8 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.by = c->p.tile_y;
     L.nchunks = c->nchunks;
     L.stream = c->stream;
+    if (c->p.walls == LB_WALLS_CHANNEL)
+        return c->p.precision == LB_PREC_FP64 ? launch_step_channel_fp64(L) : launch_step_channel_fp32(L);
     if (c->kp.walls)
         return c->p.precision == LB_PREC_FP64 ? launch_step_cavity_fp64(L) : launch_step_cavity_fp32(L);
     switch (c->p.precision) {
@@ -377,8 +393,8 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         c->p.tile_x = FD_BX;  // the FD tile front end has one tile shape
         c->p.tile_y = FD_BY;
     }
-    if (p->walls == LB_WALLS_CAVITY) {
-        c->p.tile_x = 32;  // the cavity kernel's tile
+    if (p->walls != LB_WALLS_PERIODIC) {
+        c->p.tile_x = 32;  // the cavity and channel kernels' tile
         c->p.tile_y = 8;
     }
     // kernel choice: the strip-marching TMA kernel where its alignment rules
@@ -489,6 +505,10 @@ void lb_params_default(lb_params* p) {
     p->T_hot = 1.03;
     p->T_cold = 0.97;
     p->g_grav = 0.0;
+    p->T_in = 1.03;
+    p->T_w = 0.97;
+    p->U_in = 0.05;
+    p->adiabatic_bottom = 0;
 }
 
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,

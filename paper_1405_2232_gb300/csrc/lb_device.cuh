@@ -86,8 +86,10 @@ struct KParams {
     int eos;
     int psi_local_T;
     int ghost;         // periodic ghost columns kept on each side of every row (0 or 2)
-    int walls;         // 0 periodic; 1 cavity (populations stored pre-collision at their site)
+    int walls;         // 0 periodic; 1 cavity, 2 channel (populations stored pre-collision at their site)
+    int adiabatic_bottom;          // channel Case B
     double T_hot, T_cold, g_grav;  // cavity side walls and gravity
+    double T_in, T_w, U_in;        // channel inlet and plates
     double a, b, R;
     double cv, inv_cv;
     double T_psi;

@@ -106,6 +106,7 @@ inline PopLayout pop_layout(int prec, int nx, int ny, bool strip) {
     cudaError_t launch_scatter_##NAME(void* dst, const KParams& kp, const double* in,  \
                                       cudaStream_t st);                                \
     cudaError_t launch_step_cavity_##NAME(const StepLaunch& L);                        \
+    cudaError_t launch_step_channel_##NAME(const StepLaunch& L);                       \
     cudaError_t launch_fd_step_##NAME(const FdLaunch& L);                              \
     cudaError_t launch_fd_moments_##NAME(const FdLaunch& L);                           \
     cudaError_t launch_fd_set_T_##NAME(void* T, const double* T0, const KParams& kp, cudaStream_t st);

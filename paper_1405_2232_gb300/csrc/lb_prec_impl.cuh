@@ -188,6 +188,36 @@ cudaError_t LBGB_CAT(launch_step_cavity_, LBGB_NAME)(const StepLaunch& L) {
     }
 }
 
+// ------------------------------------------------ channel (Sec. III A)
+cudaError_t LBGB_CAT(launch_step_channel_, LBGB_NAME)(const StepLaunch& L) {
+    if constexpr (LBGB_PREC != LB_PREC_FP64 && LBGB_PREC != LB_PREC_FP32) {
+        return cudaErrorNotSupported;
+    } else {
+        using E = typename Store<LBGB_PREC>::elem;
+        const dim3 block(CAV_BX, CAV_BY);
+        const dim3 grid((L.kp.nx + CAV_BX - 1) / CAV_BX, (L.kp.ny + CAV_BY - 1) / CAV_BY);
+        const E* src = static_cast<const E*>(L.src);
+        E* dst = static_cast<E*>(L.dst);
+        if (L.eq24) {
+            switch (L.bmode) {
+                case BETA_ZERO: k_step_channel<LBGB_PREC, true, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                case BETA_ONE: k_step_channel<LBGB_PREC, true, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                default: k_step_channel<LBGB_PREC, true, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            }
+        } else {
+            switch (L.bmode) {
+                case BETA_ZERO: k_step_channel<LBGB_PREC, false, BETA_ZERO><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                case BETA_ONE: k_step_channel<LBGB_PREC, false, BETA_ONE><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+                default: k_step_channel<LBGB_PREC, false, BETA_MIXED><<<grid, block, 0, L.stream>>>(src, dst, L.kp); break;
+            }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_channel_outlet<LBGB_PREC><<<(L.kp.ny + 127) / 128, 128, 0, L.stream>>>(dst, L.kp);
+        return cudaGetLastError();
+    }
+}
+
 // ------------------------------------------------ finite-difference T (Eqs. 26-27)
 namespace {
 constexpr bool kFdSupported = LBGB_PREC == LB_PREC_FP64 || LBGB_PREC == LB_PREC_FP32;

@@ -25,7 +25,7 @@ LB_ERR_NOT_CONVERGED = 8
 LB_EOS_CS, LB_EOS_VDW, LB_EOS_IDEAL = 0, 1, 2
 LB_THERMAL_EQ7, LB_THERMAL_EQ24, LB_THERMAL_FD26, LB_THERMAL_FD26_PRINTED = 0, 1, 2, 3
 LB_PREC_FP64, LB_PREC_FP32, LB_PREC_FP16_DEV, LB_PREC_BF16_DEV = 0, 1, 2, 3
-LB_WALLS_PERIODIC, LB_WALLS_CAVITY = 0, 1
+LB_WALLS_PERIODIC, LB_WALLS_CAVITY, LB_WALLS_CHANNEL = 0, 1, 2
 LB_TOTALS_N = 5
 LB_TUNE_N = 5
 LB_BATCH_TUNE_N = 4
@@ -55,8 +55,9 @@ class lb_params(ctypes.Structure):
         ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
         ("cv", ctypes.c_double), ("T_psi", ctypes.c_double),
         ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
-        ("walls", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("walls", ctypes.c_int32), ("adiabatic_bottom", ctypes.c_int32),
         ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("g_grav", ctypes.c_double),
+        ("T_in", ctypes.c_double), ("T_w", ctypes.c_double), ("U_in", ctypes.c_double),
     ]
 
 
