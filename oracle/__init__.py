@@ -193,6 +193,10 @@ def _bind(lib):
     lib.or_channel_nusselt.restype = ctypes.c_double
     lib.or_channel_nusselt_grad.argtypes = [P, Ch, dp, dp, dp, ctypes.c_int]
     lib.or_channel_nusselt_grad.restype = ctypes.c_double
+    lib.or_step_fd_channel.argtypes = [P, Ch, dp, dp, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    lib.or_step_fd_channel.restype = ctypes.c_int
+    lib.or_channel_nusselt_wall.argtypes = [P, Ch, dp, dp, dp, ctypes.c_int]
+    lib.or_channel_nusselt_wall.restype = ctypes.c_double
     return lib
 
 
@@ -507,3 +511,29 @@ def channel_nusselt_grad(P, Ch, rho, ux, T, x):
     """Local Nusselt number at column x from the temperature gradient at the upper plate."""
     rho, ux, T = (_field(a, P) for a in (rho, ux, T))
     return _load().or_channel_nusselt_grad(ctypes.byref(P), ctypes.byref(Ch), _ptr(rho), _ptr(ux), _ptr(T), int(x))
+
+
+def step_fd_channel(P, Ch, f, T, n=1, printed=False, threads=1, check=True):
+    """n steps of the hybrid scheme in the channel; returns (f, T, status, (rho, ux, uy))."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    T = _field(T, P).copy()
+    fn, Tn = np.empty_like(f), np.empty_like(T)
+    rho, ux, uy = (np.zeros((P.ny, P.nx)) for _ in range(3))
+    worst = OK
+    for _ in range(int(n)):
+        rc = _load().or_step_fd_channel(ctypes.byref(P), ctypes.byref(Ch), _ptr(f), _ptr(T), _ptr(fn), _ptr(Tn),
+                                        int(bool(printed)), _ptr(rho), _ptr(ux), _ptr(uy), int(threads))
+        if rc == ERR_ARG:
+            raise ValueError("or_step_fd_channel: invalid parameters")
+        worst = max(worst, rc)
+        f, fn = fn, f
+        T, Tn = Tn, T
+    if check and worst:
+        raise FloatingPointError(f"oracle FD channel step reported status {worst}")
+    return f, T, worst, (rho, ux, uy)
+
+
+def channel_nusselt_wall(P, Ch, rho, ux, T, x):
+    """Local Nusselt number at column x, plate gradient across the plate (FD)."""
+    rho, ux, T = (_field(a, P) for a in (rho, ux, T))
+    return _load().or_channel_nusselt_wall(ctypes.byref(P), ctypes.byref(Ch), _ptr(rho), _ptr(ux), _ptr(T), int(x))

@@ -1133,3 +1133,151 @@ double or_channel_nusselt_grad(const or_params* P, const or_channel* Ch, const d
     /* heat into the fluid per lambda: -dT/dn at the plate (flux along -n) */
     return 2.0 * ny * (-dTdn) / (Ch->T_w - Tb);
 }
+
+
+/* ---------------------------------------------------------------------- */
+/* The hybrid scheme (Eqs. 26-27) in the plate channel.  The density LBE
+ * takes the channel rules of or_step_channel for f; K of Eq. (26) reads its
+ * neighbours through the boundaries as ghosts (reading listed in the design
+ * notes): across a plate at T_w (or the inlet at T_in) the temperature is
+ * reflected about the boundary value, 2 T_b - X(mirror node); across the
+ * adiabatic lower plate of Case B and across the outlet X(mirror node)
+ * (zero gradient); rho is mirrored; a neighbour outside in y takes the plate
+ * rule.  The intermediate temperature of the second stage takes the same
+ * rule.                                                                   */
+static double channel_ghost_T(const or_channel* Ch, int xn, int yn, int ny, double Xm)
+{
+    if (yn < 0 || yn >= ny) {
+        if (yn < 0 && Ch->adiabatic_bottom) return Xm;
+        return 2.0 * Ch->T_w - Xm;
+    }
+    if (xn < 0) return 2.0 * Ch->T_in - Xm;
+    return Xm; /* outlet */
+}
+
+static void fd_rhs_channel(const or_params* P, const or_channel* Ch, const double* X,
+                           const double* rho, const double* ux, const double* uy, double* K)
+{
+    const int nx = P->nx, ny = P->ny;
+    const double chi = (P->tau_g - 0.5) * CS2;
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t c = (int64_t)y * nx + x;
+            double Xn[9], rn[9];
+            for (int i = 1; i < 9; ++i) {
+                const int xn = x + EX[i], yn = y + EY[i];
+                const int64_t m = (int64_t)clampi(yn, ny) * nx + clampi(xn, nx);
+                rn[i] = rho[m];
+                if (xn < 0 || xn >= nx || yn < 0 || yn >= ny)
+                    Xn[i] = channel_ghost_T(Ch, xn, yn, ny, X[m]);
+                else
+                    Xn[i] = X[m];
+            }
+            K[c] = fd_K_site(Xn, rn, X[c], rho[c], ux[c], uy[c], chi);
+        }
+    }
+}
+
+int or_step_fd_channel(const or_params* P, const or_channel* Ch, const double* f, const double* T,
+                       double* fn, double* Tn, int printed, double* rho_out, double* ux_out,
+                       double* uy_out, int nthreads)
+{
+    if (!P || !Ch || P->nx < 3 || P->ny < 3 || !(P->tau_f > 0.5) || !(P->tau_g > 0.5) ||
+        P->G == 0.0 || !(P->cv > 0.0) || P->eos < 0 || P->eos > 2)
+        return OR_ERR_ARG;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* h1 = (double*)malloc(sizeof(double) * N);
+    double* h2 = (double*)malloc(sizeof(double) * N);
+    double* Ts = (double*)malloc(sizeof(double) * N);
+    if (!rho || !psi || !psi2 || !ux || !uy || !h1 || !h2 || !Ts) {
+        free(rho); free(psi); free(psi2); free(ux); free(uy); free(h1); free(h2); free(Ts);
+        return OR_ERR_ARG;
+    }
+    if (nthreads < 1) nthreads = 1;
+    int err = OR_OK;
+    for (int64_t s = 0; s < N; ++s) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[i * N + s];
+        rho[s] = r;
+        const double Te = P->psi_uses_local_T ? T[s] : P->T_psi;
+        psi2[s] = or_psi_sq(P, r, Te);
+        psi[s] = 0.0;
+        if (!isfinite(r) || !isfinite(T[s])) err = err < OR_ERR_NONFINITE ? OR_ERR_NONFINITE : err;
+        if (P->beta != 0.0) {
+            if (psi2[s] < 0.0) {
+                err = OR_ERR_PSI_DOMAIN;
+                psi[s] = NAN;
+            } else {
+                psi[s] = sqrt(psi2[s]);
+            }
+        }
+    }
+    const double uin = Ch->U_in;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            const int64_t s = (int64_t)y * nx + x;
+            double fl[9], gl[9], fs[9], gs[9], Fx, Fy;
+            for (int i = 0; i < 9; ++i) {
+                fl[i] = f[i * N + s];
+                gl[i] = 0.0;
+            }
+            force_at_clamped(P, psi, psi2, x, y, &Fx, &Fy);
+            collide_site(P, fl, gl, rho[s], T[s], Fx, Fy, fs, gs, &ux[s], &uy[s]);
+            for (int i = 0; i < 9; ++i) {
+                const int xd = x + EX[i], yd = y + EY[i];
+                const int o = OPP[i];
+                if (yd < 0 || yd >= ny) {
+                    fn[o * N + s] = fs[i];
+                } else if (xd < 0) {
+                    const double eu = EX[i] * uin;
+                    fn[o * N + s] = fs[i] - 2.0 * OMEGA[i] * rho[s] * eu / CS2;
+                } else if (xd < nx) {
+                    fn[i * N + (int64_t)yd * nx + xd] = fs[i];
+                } else {
+                    const double eu = EX[i] * ux[s] + EY[i] * uy[s];
+                    fn[o * N + s] = -fs[i] + 2.0 * OMEGA[i] * 1.0 *
+                                                 (1.0 + 0.5 * eu * eu / (CS2 * CS2) -
+                                                  0.5 * (ux[s] * ux[s] + uy[s] * uy[s]) / CS2);
+                }
+            }
+        }
+    }
+    const double a = printed ? 0.5 : 1.0;
+    fd_rhs_channel(P, Ch, T, rho, ux, uy, h1);
+    for (int64_t s = 0; s < N; ++s) Ts[s] = T[s] + a * h1[s];
+    fd_rhs_channel(P, Ch, Ts, rho, ux, uy, h2);
+    for (int64_t s = 0; s < N; ++s) {
+        Tn[s] = T[s] + 0.5 * (h1[s] + h2[s]);
+        if (!isfinite(Tn[s])) err = err < OR_ERR_NONFINITE ? OR_ERR_NONFINITE : err;
+    }
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * N);
+    if (ux_out) memcpy(ux_out, ux, sizeof(double) * N);
+    if (uy_out) memcpy(uy_out, uy, sizeof(double) * N);
+    free(rho); free(psi); free(psi2); free(ux); free(uy); free(h1); free(h2); free(Ts);
+    return err;
+}
+
+/* Local Nusselt number of a temperature field whose plate value enters
+ * through the reflected ghost (the FD treatment): q_w / lambda is the
+ * central difference across the upper plate, 2 (T_w - T(ny - 1)).         */
+double or_channel_nusselt_wall(const or_params* P, const or_channel* Ch, const double* rho,
+                               const double* ux, const double* T, int x)
+{
+    const int nx = P->nx, ny = P->ny;
+    double num = 0.0, den = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const int64_t s = (int64_t)y * nx + x;
+        num += rho[s] * ux[s] * T[s];
+        den += rho[s] * ux[s];
+    }
+    const double Tb = num / den;
+    const double q = 2.0 * (Ch->T_w - T[(int64_t)(ny - 1) * nx + x]);
+    return 2.0 * ny * q / (Ch->T_w - Tb);
+}

@@ -49,3 +49,19 @@ def test_table1_fully_developed_nusselt(case):
     nus = [O.channel_nusselt(P, Ch, g, rho, ux, T, x) for x in range(100, 201, 20)]
     assert np.ptp(nus) < 0.02 * np.mean(nus)              # fully developed: flat in x
     assert np.mean(nus) == pytest.approx(NU_ANALYTICAL[case], rel=0.04), nus
+
+
+@pytest.mark.parametrize("case", ["A", "B"])
+def test_fd_table1_fully_developed_nusselt(case):
+    """The hybrid scheme (Eqs. 26-27) in the channel (ghosts reflected about
+    the plate and inlet temperatures): Table I's FD column (7.51, 4.91) and
+    the analytical values, on 150 x 20."""
+    P, Ch = O.channel_setup(150, 20, case)
+    f, _ = _start(P)
+    T = np.ones((P.ny, P.nx))
+    f, T, st, _ = O.step_fd_channel(P, Ch, f, T, n=10000, threads=8)
+    assert st == O.OK
+    _, _, _, (rho, ux, uy) = O.step_fd_channel(P, Ch, f, T, n=1, check=False)
+    nus = [O.channel_nusselt_wall(P, Ch, rho, ux, T, x) for x in range(60, 121, 15)]
+    assert np.ptp(nus) < 0.01 * np.mean(nus)
+    assert np.mean(nus) == pytest.approx(NU_ANALYTICAL[case], rel=0.02), nus
