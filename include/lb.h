@@ -103,8 +103,8 @@ enum {
  * rule); psi at a wall node is that of the nearest fluid node; the buoyancy
  * (0, -rho g_grav) is added to the force.  The populations are then stored
  * pre-collision at their site and pushed after the collision.  Cavity
- * contexts: Eq. (7) or (24), FP64 or FP32, the 32x8 tile kernel (tile_y == 0
- * is LB_ERR_ARG), not in the batched solver. */
+ * contexts: FP64 or FP32, the 32x8 tile kernel (tile_y == 0 is LB_ERR_ARG),
+ * not in the batched solver; the finite-difference treatment as below. */
 /* CHANNEL (Sec. III A): flow between parallel plates half a spacing below
  * y = 0 and above y = ny - 1 (gap H = ny); f bounces back on the plates; g
  * anti-bounces back at T_w on the upper plate and, in Case A, on the lower
@@ -114,8 +114,12 @@ enum {
  * with the symmetric equilibrium at u_in; the outlet (half a spacing right of
  * x = nx - 1) anti-bounces f back at density 1 with the node's velocity, and
  * copies g from column nx - 2 (zero gradient); psi outside = psi of the
- * nearest node; no gravity.  Eq. (7) or (24), FP64 or FP32, the 32x8 tile
- * kernel, not in the batched solver, nx >= 3. */
+ * nearest node; no gravity.  FP64 or FP32, the 32x8 tile kernel, not in the
+ * batched solver.  With the finite-difference treatment (cavity and channel)
+ * K of Eq. (26) reads ghosts outside: the temperature reflected about the
+ * boundary value (2 T_b - T of the mirror node) across an isothermal
+ * boundary, the mirror node's across an adiabatic one or the outlet; rho
+ * mirrored. */
 enum { LB_WALLS_PERIODIC = 0, LB_WALLS_CAVITY = 1, LB_WALLS_CHANNEL = 2 };
 
 /* Numbers of lb_totals outputs. */

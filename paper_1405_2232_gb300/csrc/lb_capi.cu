@@ -67,8 +67,6 @@ lb_status validate(const lb_params* p) {
     if (p->walls != LB_WALLS_PERIODIC && p->walls != LB_WALLS_CAVITY && p->walls != LB_WALLS_CHANNEL)
         return fail(LB_ERR_ARG, "unknown boundary kind %d", p->walls);
     if (p->walls == LB_WALLS_CHANNEL) {
-        if (p->thermal != LB_THERMAL_EQ7 && p->thermal != LB_THERMAL_EQ24)
-            return fail(LB_ERR_UNSUPPORTED, "the channel runs Eq. (7) or Eq. (24)");
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the channel stores FP64 or FP32");
         if ((p->tile_x || p->tile_y) && !(p->tile_x == 32 && p->tile_y == 8))

@@ -121,15 +121,29 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
         if (STEP) {
             const long long off = (long long)gy * kp.pitch + gx;
             if (kp.walls) {
-                // cavity: push to x + e_i, bounce back from the walls
+                // cavity and channel: push to x + e_i; bounce back from the walls
+                // and plates; channel inlet: with the wall velocity; channel
+                // outlet: anti-bounce-back at density 1 with the node's velocity
+                const real cs2 = (real)(1.0 / 3.0);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const int xd = gx + ex(i), yd = gy + ey(i);
-                    if (xd >= 0 && xd < kp.nx && yd >= 0 && yd < kp.ny)
+                    typename S::elem* pfo = dst + (long long)opp(i) * kp.plane + off;
+                    if (xd >= 0 && xd < kp.nx && yd >= 0 && yd < kp.ny) {
                         S::put(dst + (long long)i * kp.plane + (long long)yd * kp.pitch + xd, f[i],
                                (real)kp.base_f[i]);
-                    else
-                        S::put(dst + (long long)opp(i) * kp.plane + off, f[i], (real)kp.base_f[opp(i)]);
+                    } else if (kp.walls != 2 || yd < 0 || yd >= kp.ny) {
+                        S::put(pfo, f[i], (real)kp.base_f[opp(i)]);
+                    } else if (xd < 0) {
+                        const real eu = (real)ex(i) * (real)kp.U_in;
+                        S::put(pfo, f[i] - (real)2.0 * (real)wd(i) * rho * eu / cs2, (real)kp.base_f[opp(i)]);
+                    } else {
+                        const real eu = (real)ex(i) * ux + (real)ey(i) * uy;
+                        const real fb = -f[i] + (real)2.0 * (real)wd(i) * (real)1.0 *
+                                                    ((real)1.0 + (real)0.5 * eu * eu / (cs2 * cs2) -
+                                                     (real)0.5 * (ux * ux + uy * uy) / cs2);
+                        S::put(pfo, fb, (real)kp.base_f[opp(i)]);
+                    }
                 }
             } else {
 #pragma unroll

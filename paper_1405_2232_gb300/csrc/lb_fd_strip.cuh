@@ -347,6 +347,30 @@ __device__ __forceinline__ real fd_K_tile(const real* X, int xs, int xc, const r
     return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / R[rc]);
 }
 
+// Ghost value of a temperature-like field X at (rx, ry) outside the lattice
+// of a cavity (walls 1) or channel (walls 2) context, from the value Xm at the
+// mirror node (the clamped position): reflected about the boundary value,
+// 2 T_b - Xm, across an isothermal boundary (cavity side walls; channel
+// plates at T_w and inlet at T_in); Xm across an adiabatic one (cavity bottom
+// and top, channel lower plate in Case B, channel outlet).  A position outside
+// in both directions takes the side-wall rule in the cavity and the plate
+// rule in the channel.
+template <typename real>
+__device__ __forceinline__ real fd_ghost(const KParams& kp, int rx, int ry, real Xm) {
+    const int nx = kp.nx, ny = kp.ny;
+    if (kp.walls == 1) {
+        if (rx < 0) return (real)2.0 * (real)kp.T_hot - Xm;
+        if (rx >= nx) return (real)2.0 * (real)kp.T_cold - Xm;
+        return Xm;
+    }
+    if (ry < 0 || ry >= ny) {
+        if (ry < 0 && kp.adiabatic_bottom) return Xm;
+        return (real)2.0 * (real)kp.T_w - Xm;
+    }
+    if (rx < 0) return (real)2.0 * (real)kp.T_in - Xm;
+    return Xm;
+}
+
 // tile of k_fd_rk2: FDR_BX x FDR_BY threads, FDR_ROWS rows of sites per thread
 constexpr int FDR_BX = 32, FDR_BY = 8, FDR_ROWS = 2;
 
@@ -365,21 +389,16 @@ __global__ void __launch_bounds__(FDR_BX* FDR_BY)
     const long long pitch = kp.pitch;
     const int tid = threadIdx.x + threadIdx.y * FDR_BX;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    // cavity (kp.walls): a neighbour across a side wall reads the temperature
-    // reflected about the wall value, 2 T_w - T(mirror node); across the
-    // adiabatic walls T(mirror node); rho and u the mirror node's
+    // cavity and channel (kp.walls): a neighbour outside reads the ghost of
+    // fd_ghost (reflected about an isothermal boundary, mirrored across an
+    // adiabatic one); rho and u the mirror node's
     const bool walls = kp.walls != 0;
     for (int s = tid; s < H2 * W2; s += NT) {
         const int ly = s / W2, lx = s - ly * W2;
         const int rx = x0 + lx - 2, ry = y0 + ly - 2;
         const int gx = ringc(kp, rx, nx), gy = ringc(kp, ry, ny);
         const real Tv = T[(long long)gy * pitch + gx];
-        if (walls && (rx < 0 || rx >= nx)) {
-            const real Tw = rx < 0 ? (real)kp.T_hot : (real)kp.T_cold;
-            sT[s] = (real)2.0 * Tw - Tv;
-        } else {
-            sT[s] = Tv;
-        }
+        sT[s] = walls && (rx < 0 || rx >= nx || ry < 0 || ry >= ny) ? fd_ghost<real>(kp, rx, ry, Tv) : Tv;
         sR[s] = rho[(long long)gy * nx + gx];
     }
     for (int s = tid; s < H1 * W1; s += NT) {
@@ -407,13 +426,7 @@ __global__ void __launch_bounds__(FDR_BX* FDR_BY)
             const int rx = x0 + lx - 1, ry = y0 + ly - 1;
             if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) continue;
             const int mx = clampc(rx, nx) - x0 + 1, my = clampc(ry, ny) - y0 + 1;
-            const real Tm = sTs[my * W1 + mx];
-            if (rx < 0 || rx >= nx) {
-                const real Tw = rx < 0 ? (real)kp.T_hot : (real)kp.T_cold;
-                sTs[s] = (real)2.0 * Tw - Tm;
-            } else {
-                sTs[s] = Tm;
-            }
+            sTs[s] = fd_ghost<real>(kp, rx, ry, sTs[my * W1 + mx]);
         }
         __syncthreads();
     }
