@@ -41,16 +41,21 @@ def force_form(beta: float) -> str:
     return "b0" if beta == 0.0 else ("b1" if beta == 1.0 else "bmix")
 
 
+TREATMENTS = {lb.LB_THERMAL_EQ7: "eq7", lb.LB_THERMAL_EQ24: "eq24", lb.LB_THERMAL_FD26: "fd26",
+              lb.LB_THERMAL_FD26_PRINTED: "fd26p"}
+BOUNDARIES = {lb.LB_WALLS_PERIODIC: "periodic", lb.LB_WALLS_CAVITY: "cavity", lb.LB_WALLS_CHANNEL: "channel"}
+
+
 def tune_key(p, device_name: str) -> str:
     aligned = "a" if p.nx % STRIP_HALO[p.precision] == 0 else "u"
-    return "|".join([device_name, PREC_NAMES[p.precision], "eq24" if p.thermal else "eq7",
+    return "|".join([device_name, PREC_NAMES[p.precision], TREATMENTS[p.thermal], BOUNDARIES[p.walls],
                      force_form(p.beta), f"{_pow2(p.nx)}x{_pow2(p.ny)}{aligned}"])
 
 
 def batch_key(params, device_name: str) -> str:
     p = params[0]
     sites = sum(q.nx * q.ny for q in params)
-    return "|".join([device_name, "batch", PREC_NAMES[p.precision], "eq24" if p.thermal else "eq7",
+    return "|".join([device_name, "batch", PREC_NAMES[p.precision], TREATMENTS[p.thermal],
                      force_form(p.beta), f"n{_pow2(len(params))}", f"s{_pow2(sites)}"])
 
 

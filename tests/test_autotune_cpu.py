@@ -38,6 +38,8 @@ def test_keys_separate_what_changes_the_choice():
     k0 = A.tune_key(lb.lb_params_default(**base), "GB300")
     assert k0 == A.tune_key(lb.lb_params_default(nx=500, ny=256, precision="fp32"), "GB300")
     differ = [dict(base, precision="fp64"), dict(base, thermal=lb.LB_THERMAL_EQ7),
+              dict(base, thermal=lb.LB_THERMAL_FD26), dict(base, thermal=lb.LB_THERMAL_FD26_PRINTED),
+              dict(base, walls=lb.LB_WALLS_CAVITY), dict(base, walls=lb.LB_WALLS_CHANNEL),
               dict(base, beta=1.3), dict(base, beta=0.0), dict(base, nx=600),
               dict(base, ny=257), dict(base, nx=302)]  # 302: not a multiple of 4
     keys = {A.tune_key(lb.lb_params_default(**d), "GB300") for d in differ}
