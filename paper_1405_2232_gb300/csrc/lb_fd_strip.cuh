@@ -52,7 +52,8 @@ constexpr int fd_fused_stages() {
 // K(X) of Eq. (26) at one site from three row pointers (south, centre, north,
 // each at the site's column) of X and of rho.  FP64: the stencil and order of
 // operations of the printed form (divisions by c_s^2 included); FP32: the
-// same sums with the divisions by c_s^2 = 1/3 taken as products by 3.
+// same sums with the divisions by c_s^2 = 1/3 taken as products by 3 and the
+// division by rho as the fast division.
 template <typename real>
 __device__ __forceinline__ real fd_K_rows(const real* Xs, const real* Xc, const real* Xn, const real* Rs,
                                           const real* Rc, const real* Rn, real ux, real uy, real chi) {
@@ -84,7 +85,10 @@ __device__ __forceinline__ real fd_K_rows(const real* Xs, const real* Xc, const 
         gry *= (real)3;
         lap *= (real)6;
     }
-    return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / Rc[0]);
+    if constexpr (sizeof(real) == 8)
+        return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / Rc[0]);
+    else  // FP32: the fast division (a few ulp; +3% on the issue-bound fused step)
+        return -(ux * gTx + uy * gTy) + chi * (lap + __fdividef(grx * gTx + gry * gTy, Rc[0]));
 }
 
 // One whole FD step (Eqs. 1, 26, 27) on a strip context, one pass over HBM:
@@ -314,7 +318,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
 // K(X) of Eq. (26) from shared-memory tiles: X and R (rho) with row strides
 // xs and rs, centre indices xc and rc.  FP64: the stencil and order of
 // operations of the printed form (divisions by c_s^2 included); FP32:
-// the same sums with the divisions by c_s^2 = 1/3 taken as products by 3.
+// the same sums with the divisions by c_s^2 = 1/3 taken as products by 3 and
+// the division by rho as the fast division.
 template <typename real>
 __device__ __forceinline__ real fd_K_tile(const real* X, int xs, int xc, const real* R, int rs, int rc, real ux,
                                           real uy, real chi) {
@@ -344,7 +349,10 @@ __device__ __forceinline__ real fd_K_tile(const real* X, int xs, int xc, const r
         gry *= (real)3;
         lap *= (real)6;
     }
-    return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / R[rc]);
+    if constexpr (sizeof(real) == 8)
+        return -(ux * gTx + uy * gTy) + chi * (lap + (grx * gTx + gry * gTy) / R[rc]);
+    else
+        return -(ux * gTx + uy * gTy) + chi * (lap + __fdividef(grx * gTx + gry * gTy, R[rc]));
 }
 
 // Ghost value of a temperature-like field X at (rx, ry) outside the lattice
