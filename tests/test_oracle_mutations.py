@@ -117,3 +117,34 @@ def test_planted_cavity_mistake_is_caught(name, old, new):
                 caught = exc
                 break
     assert caught is not None, f"no cavity pin catches the planted mistake {name}"
+
+
+# ------------------------------------------------- FD treatment with walls
+import test_oracle_channel as chan  # noqa: E402
+
+WALL_FD_MUTATIONS = [
+    ("fd_cavity_side_wall_not_reflected", "Xn[i] = 2.0 * Tw - X[m];", "Xn[i] = X[m];"),
+    ("fd_channel_inlet_ghost_mirrored", "if (xn < 0) return 2.0 * Ch->T_in - Xm;", "if (xn < 0) return Xm;"),
+    ("fd_channel_plate_ghost_sign", "return 2.0 * Ch->T_w - Xm;", "return 2.0 * Ch->T_w + Xm;"),
+]
+
+WALL_FD_PINS = [
+    lambda: chan.test_fd_table1_fully_developed_nusselt("A"),
+    cav.test_fd_cavity_table2_ra1e3,
+]
+
+
+@pytest.mark.parametrize("name,old,new", WALL_FD_MUTATIONS, ids=[m[0] for m in WALL_FD_MUTATIONS])
+def test_planted_wall_fd_mistake_is_caught(name, old, new):
+    src = O.source_text()
+    assert src.count(old) == 1, f"mutation anchor not unique/present: {old}"
+    lib = O.build_variant(src.replace(old, new), name)
+    caught = None
+    with O.using(lib):
+        for pin in WALL_FD_PINS:
+            try:
+                pin()
+            except (AssertionError, FloatingPointError, ValueError) as exc:
+                caught = exc
+                break
+    assert caught is not None, f"no pin catches the planted mistake {name}"
