@@ -159,6 +159,8 @@ def _bind(lib):
     lib.or_moments.restype = ctypes.c_int
     lib.or_init_equilibrium.argtypes = [P, dp, dp, dp, dp]
     lib.or_init_equilibrium.restype = ctypes.c_int
+    lib.or_init_balanced.argtypes = [P, dp, dp, dp, dp]
+    lib.or_init_balanced.restype = ctypes.c_int
     lib.or_step_sites.argtypes = [P, dp, dp, ctypes.c_int64,
                                   ctypes.POINTER(ctypes.c_int64), dp, dp]
     lib.or_step_sites.restype = ctypes.c_int
@@ -252,6 +254,21 @@ def init_equilibrium(P, rho0, T0):
     if rc:
         raise ValueError(f"or_init_equilibrium failed: {rc}")
     return f, g
+
+
+def init_balanced(P, rho0, T0):
+    """State at rest under the force: f = f^eq(rho0, v), g = c_v T0 f^eq(rho0, v)
+    with v = -F/(2 rho0), F the Eq. (4) force of psi(rho0, T0); returns
+    (f, g, status), status ERR_PSI_DOMAIN where psi is undefined."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    assert rho0.shape == (P.ny, P.nx) and T0.shape == (P.ny, P.nx)
+    f = np.zeros((9, P.ny, P.nx))
+    g = np.zeros((9, P.ny, P.nx))
+    rc = _load().or_init_balanced(ctypes.byref(P), _ptr(rho0), _ptr(T0), _ptr(f), _ptr(g))
+    if rc == ERR_ARG:
+        raise ValueError("or_init_balanced: invalid parameters")
+    return f, g, rc
 
 
 def step(P, f, g, n=1, threads=1, check=True):

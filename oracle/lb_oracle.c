@@ -513,6 +513,57 @@ int or_init_equilibrium(const or_params* P, const double* rho0, const double* T0
     return OR_OK;
 }
 
+/* Initial state at rest under the pseudopotential force.  The paper states no
+ * initial condition; this start is a reading of the velocity definition of
+ * the forcing scheme of Eq. (1): u = (sum_i e_i f_i + F/2) / rho, so a state
+ * whose velocity is zero carries the first moment sum_i e_i f_i = -F/2.
+ *   psi from rho0 and T0 (Sec. II A), F of Eq. (4) (Eq. (2) when beta = 1),
+ *   v = -F / (2 rho0),  f = f^eq(rho0, v),  g = c_v T0 f^eq(rho0, v).
+ * Returns OR_ERR_PSI_DOMAIN (state still written, NaN where psi is undefined)
+ * when psi^2 < 0 and beta != 0.                                            */
+int or_init_balanced(const or_params* P, const double* rho0, const double* T0,
+                     double* f, double* g)
+{
+    int err = check_params(P);
+    if (err) return err;
+    const int nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* psi2 = (double*)malloc(sizeof(double) * N);
+    if (!psi || !psi2) {
+        free(psi); free(psi2);
+        return OR_ERR_ARG;
+    }
+    for (int64_t s = 0; s < N; ++s) {
+        psi2[s] = or_psi_sq(P, rho0[s], T0[s]);
+        psi[s] = 0.0;
+        if (P->beta != 0.0) {
+            if (psi2[s] < 0.0) {
+                if (err < OR_ERR_PSI_DOMAIN) err = OR_ERR_PSI_DOMAIN;
+                psi[s] = NAN;
+            } else {
+                psi[s] = sqrt(psi2[s]);
+            }
+        }
+    }
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int64_t s = (int64_t)y * nx + x;
+            double Fx, Fy, feq[9];
+            force_at(P, psi, psi2, x, y, &Fx, &Fy);
+            double vx = -Fx / (2.0 * rho0[s]);
+            double vy = -Fy / (2.0 * rho0[s]);
+            or_feq(rho0[s], vx, vy, feq);
+            for (int i = 0; i < 9; ++i) {
+                f[i * N + s] = feq[i];
+                g[i * N + s] = P->cv * T0[s] * feq[i];
+            }
+        }
+    }
+    free(psi); free(psi2);
+    return err;
+}
+
 /* The state at t+1 at a list of sites only, from the full state at t.
  * Site x at t+1 receives f*_i(x - e_i), so the collisions of the nine source
  * sites are computed, each with the force from the psi values around it.

@@ -148,3 +148,42 @@ def test_planted_wall_fd_mistake_is_caught(name, old, new):
                 caught = exc
                 break
     assert caught is not None, f"no pin catches the planted mistake {name}"
+
+
+# ------------------------------------------------------- start at rest
+import test_oracle_init as ini  # noqa: E402
+
+INIT_MUTATIONS = [
+    ("init_velocity_sign", "double vx = -Fx / (2.0 * rho0[s]);", "double vx = Fx / (2.0 * rho0[s]);"),
+    ("init_velocity_half_missing", "double vy = -Fy / (2.0 * rho0[s]);", "double vy = -Fy / rho0[s];"),
+    ("init_psi_from_T_psi", "psi2[s] = or_psi_sq(P, rho0[s], T0[s]);",
+     "psi2[s] = or_psi_sq(P, rho0[s], P->T_psi);"),
+    ("init_g_without_T",
+     "or_feq(rho0[s], vx, vy, feq);\n            for (int i = 0; i < 9; ++i) {\n"
+     "                f[i * N + s] = feq[i];\n                g[i * N + s] = P->cv * T0[s] * feq[i];",
+     "or_feq(rho0[s], vx, vy, feq);\n            for (int i = 0; i < 9; ++i) {\n"
+     "                f[i * N + s] = feq[i];\n                g[i * N + s] = P->cv * feq[i];"),
+    ("init_g_east_scaled", "g[i * N + s] = P->cv * T0[s] * feq[i];\n            }\n        }\n    }\n    free(psi); free(psi2);",
+     "g[i * N + s] = P->cv * T0[s] * feq[i] * (i == 1 ? 1.001 : 1.0);\n            }\n        }\n    }\n"
+     "    free(psi); free(psi2);"),
+]
+
+INIT_PINS = [ini.test_balanced_start_of_uniform_state_is_plain_equilibrium] + [
+    (lambda c=c: ini.test_balanced_start_is_at_rest(*c)) for c in ini.CASES] + [
+    (lambda c=c: ini.test_balanced_start_keeps_rho_and_T(*c)) for c in ini.CASES]
+
+
+@pytest.mark.parametrize("name,old,new", INIT_MUTATIONS, ids=[m[0] for m in INIT_MUTATIONS])
+def test_planted_init_mistake_is_caught(name, old, new):
+    src = O.source_text()
+    assert src.count(old) == 1, f"mutation anchor not unique/present: {old}"
+    lib = O.build_variant(src.replace(old, new), name)
+    caught = None
+    with O.using(lib):
+        for pin in INIT_PINS:
+            try:
+                pin()
+            except (AssertionError, FloatingPointError, ValueError) as exc:
+                caught = exc
+                break
+    assert caught is not None, f"no pin catches the planted mistake {name}"
