@@ -147,6 +147,7 @@ typedef struct lb_params {
     double T_hot, T_cold;  /* cavity: left (x = -1/2) and right (x = nx - 1/2) walls   */
     double g_grav;         /* cavity: gravity along -y, buoyancy (0, -rho g) added to F */
     double T_in, T_w, U_in; /* channel: inlet temperature and velocity, plate temperature */
+    int32_t init_balanced; /* initial state: 0 at u = 0 in f^eq; 1 at rest under the force (lb_init) */
 } lb_params;
 
 typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
@@ -155,11 +156,21 @@ typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
  * tau_f=1, tau_g=0.8, c_v=1, Eq. (24), FP32, psi from the local T,
  * rho0 = 0.12, T0 = 0.075, periodic (cavity fields T_hot = 1.03,
  * T_cold = 0.97, g_grav = 0; channel fields T_in = 1.03, T_w = 0.97,
- * U_in = 0.05, Case A). */
+ * U_in = 0.05, Case A), init_balanced = 0. */
 void lb_params_default(lb_params* p);
 
 /* Create a context whose initial state is f = f^eq(rho0, u = 0) and
  * g = c_v T0 f^eq(rho0, 0) (Eq. (1) and Eq. (7) equilibria at rest).
+ * With p->init_balanced = 1 the state is instead at rest under the force:
+ * with the forcing of Eq. (1) the velocity is u = (sum e_i f_i + F/2)/rho,
+ * so f = f^eq(rho0, v) and g = c_v T0 f^eq(rho0, v) with v = -F/(2 rho0),
+ * F the Eq. (2)/(4) force of psi(rho0, T0) (T_psi when psi does not follow
+ * the local T); evaluated in FP64, rounded once to the storage precision.
+ * The plain start moves every interface with F/(2 rho) on its first step;
+ * this one does not (fields near a steady state restart without that
+ * impulse).  Periodic lattice Boltzmann contexts only: walls or the
+ * finite-difference treatment give LB_ERR_UNSUPPORTED; psi^2 < 0 with
+ * beta != 0 is reported as LB_ERR_PSI_DOMAIN by the next lb_synchronize.
  * rho0, T0: host float64 arrays [ny][nx], copied during the call.
  * stream: a cudaStream_t for all work of the context, or NULL for a stream
  * the library creates.  *out receives the context.  Returns LB_ERR_ARG for
@@ -257,7 +268,8 @@ typedef struct lb_batch lb_batch; /* opaque; owned by the library */
 
 /* Create a batch of n domains; params[d] describes domain d, rho0[d] and T0[d]
  * are its float64 fields [ny][nx], in host or device memory (copied; the
- * copy direction follows from unified addressing).  Initial state as lb_init. */
+ * copy direction follows from unified addressing).  Initial state as lb_init
+ * (params[d].init_balanced chooses it per domain). */
 lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const* rho0,
                         const double* const* T0, void* stream, lb_batch** out);
 

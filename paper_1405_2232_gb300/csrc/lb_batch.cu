@@ -297,7 +297,7 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         if (p.walls != LB_WALLS_PERIODIC)
             return err(LB_ERR_UNSUPPORTED, "domain %d: the batched solver runs periodic domains", d);
         if (!(p.tau_f > 0.5) || !(p.tau_g > 0.5) || p.G == 0.0 || !(p.cv > 0.0) || p.eos < 0 || p.eos > 2 ||
-            p.thermal < 0 || p.thermal > 1)
+            p.thermal < 0 || p.thermal > 1 || p.init_balanced < 0 || p.init_balanced > 1)
             return err(LB_ERR_ARG, "domain %d: invalid parameters", d);
     }
     lb_batch* b = new (std::nothrow) lb_batch();
@@ -397,8 +397,9 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
     }
     for (int d = 0; d < n; ++d) b->doms[d].kp.err = b->d_err + d;
     e = cudaMemcpyAsync(b->d_doms, b->doms.data(), sizeof(BatchDomain) * n, cudaMemcpyHostToDevice, b->stream);
-    // initial state of each domain: f = f^eq(rho0, 0), g = c_v T0 f^eq(rho0, 0),
-    // built from the fields staged in the reference buffers
+    // initial state of each domain: f = f^eq(rho0, 0), g = c_v T0 f^eq(rho0, 0)
+    // (or at rest under the force, init_balanced), built from the fields staged
+    // in the reference buffers
     for (int d = 0; d < n && e == cudaSuccess; ++d) {
         const size_t nb = sizeof(double) * (size_t)params[d].nx * params[d].ny;
         double* r = b->d_ref_rho + b->doms[d].fld_off;
@@ -408,11 +409,17 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         if (e == cudaSuccess) e = cudaMemcpyAsync(tt, T0[d], nb, cudaMemcpyDefault, b->stream);
         if (e == cudaSuccess) {
             const KParams& k = b->doms[d].kp;
-            if (prec == LB_PREC_FP32)
-                k_init<LB_PREC_FP32><<<64, 256, 0, b->stream>>>(static_cast<float*>(b->buf[0]) + b->doms[d].off, k, r, tt);
-            else
-                k_init<LB_PREC_FP64><<<64, 256, 0, b->stream>>>(static_cast<double*>(b->buf[0]) + b->doms[d].off, k, r, tt);
-            e = cudaGetLastError();
+            if (params[d].init_balanced) {
+                void* dst = prec == LB_PREC_FP32 ? static_cast<void*>(static_cast<float*>(b->buf[0]) + b->doms[d].off)
+                                                 : static_cast<void*>(static_cast<double*>(b->buf[0]) + b->doms[d].off);
+                e = launch_init_balanced(prec, dst, k, r, tt, b->stream);
+            } else {
+                if (prec == LB_PREC_FP32)
+                    k_init<LB_PREC_FP32><<<64, 256, 0, b->stream>>>(static_cast<float*>(b->buf[0]) + b->doms[d].off, k, r, tt);
+                else
+                    k_init<LB_PREC_FP64><<<64, 256, 0, b->stream>>>(static_cast<double*>(b->buf[0]) + b->doms[d].off, k, r, tt);
+                e = cudaGetLastError();
+            }
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -66,6 +66,10 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "unknown precision %d", p->precision);
     if (p->walls != LB_WALLS_PERIODIC && p->walls != LB_WALLS_CAVITY && p->walls != LB_WALLS_CHANNEL)
         return fail(LB_ERR_ARG, "unknown boundary kind %d", p->walls);
+    if (p->init_balanced != 0 && p->init_balanced != 1)
+        return fail(LB_ERR_ARG, "init_balanced must be 0 or 1 (got %d)", p->init_balanced);
+    if (p->init_balanced && (p->walls != LB_WALLS_PERIODIC || p->thermal >= LB_THERMAL_FD26))
+        return fail(LB_ERR_UNSUPPORTED, "the start at rest under the force is for periodic lattice Boltzmann contexts");
     if (p->walls == LB_WALLS_CHANNEL) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the channel stores FP64 or FP32");
@@ -251,6 +255,7 @@ cudaError_t dispatch_moments(const lb_ctx* c, MomentsLaunch& L) {
 
 cudaError_t dispatch_init(const lb_ctx* c, const double* rho0, const double* T0) {
     void* d = c->buf[c->cur];
+    if (c->p.init_balanced) return launch_init_balanced(c->p.precision, d, c->kp, rho0, T0, c->stream);
     switch (c->p.precision) {
         case LB_PREC_FP64: return launch_init_fp64(d, c->kp, rho0, T0, c->stream);
         case LB_PREC_FP32: return launch_init_fp32(d, c->kp, rho0, T0, c->stream);
@@ -507,6 +512,7 @@ void lb_params_default(lb_params* p) {
     p->T_w = 0.97;
     p->U_in = 0.05;
     p->adiabatic_bottom = 0;
+    p->init_balanced = 0;
 }
 
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,

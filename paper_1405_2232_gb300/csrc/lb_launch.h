@@ -116,4 +116,10 @@ LBGB_DECLARE_PREC(fp32)
 LBGB_DECLARE_PREC(fp16)
 LBGB_DECLARE_PREC(bf16)
 
+// Start at rest under the force (lb_init_balanced.cu): f = f^eq(rho0, -F/(2 rho0)),
+// g = c_v T0 f^eq(rho0, -F/(2 rho0)), for storage precision prec (LB_PREC_*);
+// periodic lattices only (cudaErrorInvalidValue for walls).
+cudaError_t launch_init_balanced(int prec, void* dst, const KParams& kp, const double* rho0,
+                                 const double* T0, cudaStream_t st);
+
 }  // namespace lbgb

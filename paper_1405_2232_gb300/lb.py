@@ -58,6 +58,7 @@ class lb_params(ctypes.Structure):
         ("walls", ctypes.c_int32), ("adiabatic_bottom", ctypes.c_int32),
         ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("g_grav", ctypes.c_double),
         ("T_in", ctypes.c_double), ("T_w", ctypes.c_double), ("U_in", ctypes.c_double),
+        ("init_balanced", ctypes.c_int32),
     ]
 
 

@@ -10,8 +10,10 @@ Pipeline (every numerical step runs in the CUDA library):
    mask) to the steady (rho, T), with Adam on shuffled mini-batches.
 3. ``evaluate``: on unseen cases, solve once from the plain initial state and
    once from the network's prediction (handoff ``un_warm_fields``: density and
-   temperature rescaled to the initial mass and energy), both with the same
-   batched solver and residual test; report wall-clock seconds and steps.
+   temperature rescaled to the initial mass and energy, then the start at rest
+   under the force, lb_params.init_balanced), both with the same batched
+   solver and residual test; report wall-clock seconds and steps, and the two
+   mixed arms (plain fields at rest; prediction at u = 0 in f^eq).
 
 Run as ``python -m paper_1405_2232_gb300.warmstart [--train N] [--test N]``;
 it prints one JSON object.  The sweep recipe: psi from the domain's T0
@@ -35,10 +37,11 @@ TOL = 1e-8
 K = 100
 
 
-def sweep_params(doms, thermal=lb.LB_THERMAL_EQ24, precision="fp32"):
+def sweep_params(doms, thermal=lb.LB_THERMAL_EQ24, precision="fp32", init_balanced=0):
     return [lb.lb_params_default(nx=d.L, ny=d.L, tau_f=d.tau_f, tau_g=d.tau_g, G=d.G, beta=BETA,
                                  thermal=thermal, precision=precision, psi_uses_local_T=0,
-                                 T_psi=d.T_over_Tc * I.CS_TC) for d in doms]
+                                 T_psi=d.T_over_Tc * I.CS_TC, init_balanced=init_balanced)
+            for d in doms]
 
 
 def _sync():
@@ -136,11 +139,22 @@ def predict(net, X, batch):
     return out
 
 
+def _arm(steps, st, wall):
+    return dict(wall_s=wall, converged=int(np.sum(st == lb.LB_OK)),
+                failed=int(np.sum((st != lb.LB_OK) & (st != lb.LB_ERR_NOT_CONVERGED))),
+                capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)))
+
+
 def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
+    """Plain solve from the initial fields (f^eq at u = 0) against the warm
+    solve (network prediction, handoff, start at rest under the force), with
+    the two other combinations beside them: the plain fields started at rest
+    (no network) and the prediction started at u = 0 in f^eq."""
     import torch
     dev = torch.device("cuda")
     L = doms[0].L
     params = sweep_params(doms)
+    params_bal = sweep_params(doms, init_balanced=1)
     rho0 = np.stack([d.rho for d in doms])
     T0 = np.stack([d.T for d in doms])
     # plain
@@ -148,6 +162,9 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     ok_p = np.flatnonzero(st_p == lb.LB_OK)
     ref = {int(d): Bp.fields(int(d)) for d in ok_p}
     Bp.close()
+    # plain fields, started at rest under the force
+    steps_pb, _, st_pb, wall_pb, Bpb = solve(params_bal, list(rho0), list(T0), cap, chunk_rows=chunk_rows)
+    Bpb.close()
     # warm: inference + handoff + solve, all timed
     X = torch.from_numpy(case_inputs(doms, masks)).to(dev)
     d_rho0 = torch.from_numpy(rho0).to(dev)
@@ -163,8 +180,11 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     stride = L * L * 8
     rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
     tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
-    steps_w, _, st_w, wall_w, Bw = solve(params, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
+    steps_w, _, st_w, wall_w, Bw = solve(params_bal, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
     Bw.close()
+    # the prediction started at u = 0 in f^eq (no balance)
+    steps_wu, _, st_wu, wall_wu, Bwu = solve(params, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
+    Bwu.close()
     # prediction error against the plain steady state
     h_rho, h_T = d_rho.cpu().numpy(), d_T.cpu().numpy()
     e_rho = [np.abs(h_rho[d] - ref[d][0]).max() / np.abs(ref[d][0]).max() for d in ref]
@@ -173,13 +193,26 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     med_rho = [float(np.median(np.abs(h_rho[d] - ref[d][0]))) for d in ref]
     rms_rho0 = [float(np.sqrt(np.mean((rho0[d] - ref[d][0]) ** 2))) for d in ref]
     both = np.flatnonzero((st_p == lb.LB_OK) & (st_w == lb.LB_OK))
+    conv = [st == lb.LB_OK for st in (st_p, st_pb, st_w, st_wu)]
+    allc = np.flatnonzero(conv[0] & conv[1] & conv[2] & conv[3])
+
+    def med(steps):
+        return float(np.median(steps[allc])) if allc.size else None
+
+    warm = _arm(steps_w, st_w, wall_w + t_inf)
+    warm.update(solve_s=wall_w, inference_s=t_inf, start="at rest under the force")
+    warm_u = _arm(steps_wu, st_wu, wall_wu + t_inf)
+    warm_u.update(solve_s=wall_wu, inference_s=t_inf, start="f^eq at u = 0")
+    plain_b = _arm(steps_pb, st_pb, wall_pb)
+    plain_b.update(start="at rest under the force")
+    plain = _arm(steps_p, st_p, wall_p)
+    plain.update(start="f^eq at u = 0")
     return dict(
         cases=len(doms), L=L, cap=cap,
-        plain=dict(wall_s=wall_p, converged=int(ok_p.size), failed=int(np.sum((st_p != 0) & (st_p != 8))),
-                   capped=int(np.sum(st_p == 8))),
-        warm=dict(wall_s=wall_w + t_inf, solve_s=wall_w, inference_s=t_inf,
-                  converged=int(np.sum(st_w == 0)), failed=int(np.sum((st_w != 0) & (st_w != 8))),
-                  capped=int(np.sum(st_w == 8))),
+        plain=plain, warm=warm, plain_balanced=plain_b, warm_unbalanced=warm_u,
+        all_four_converged=int(allc.size),
+        median_steps_all_four=dict(plain=med(steps_p), plain_balanced=med(steps_pb), warm=med(steps_w),
+                                   warm_unbalanced=med(steps_wu)),
         both_converged=int(both.size),
         median_steps_plain=float(np.median(steps_p[both])) if both.size else None,
         median_steps_warm=float(np.median(steps_w[both])) if both.size else None,
@@ -193,6 +226,8 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
         per_case=dict(T_over_Tc=[d.T_over_Tc for d in doms], tau_f=[d.tau_f for d in doms],
                       kind=[d.kind for d in doms], steps_plain=steps_p.tolist(), status_plain=st_p.tolist(),
                       steps_warm=steps_w.tolist(), status_warm=st_w.tolist(),
+                      steps_plain_balanced=steps_pb.tolist(), status_plain_balanced=st_pb.tolist(),
+                      steps_warm_unbalanced=steps_wu.tolist(), status_warm_unbalanced=st_wu.tolist(),
                       e_rho={int(d): float(e) for d, e in zip(ref, e_rho)}),
     )
 

@@ -56,11 +56,12 @@ def test_params_default_layout(lib):
     assert p.eos == lb.LB_EOS_CS and p.thermal == lb.LB_THERMAL_EQ24
     assert p.precision == lb.LB_PREC_FP32 and p.psi_uses_local_T == 1
     assert (p.rho0, p.T0) == (0.12, 0.075)
+    assert p.init_balanced == 0 and p.walls == lb.LB_WALLS_PERIODIC
 
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 2), ("ny", 0), ("tau_f", 0.5), ("tau_g", 0.3), ("G", 0.0), ("cv", 0.0),
-    ("eos", 7), ("thermal", 4), ("precision", 9), ("tile_x", 17),
+    ("eos", 7), ("thermal", 4), ("precision", 9), ("tile_x", 17), ("init_balanced", 2),
 ])
 def test_invalid_params_rejected_on_host(lib, field, value):
     import numpy as np
@@ -74,6 +75,25 @@ def test_invalid_params_rejected_on_host(lib, field, value):
     assert st == lb.LB_ERR_ARG
     assert ctx.value is None
     assert lb.lb_last_error() != ""
+
+
+@pytest.mark.parametrize("field,value", [("walls", 1), ("walls", 2), ("thermal", 2)])
+def test_start_at_rest_is_periodic_lb_only(lib, field, value):
+    """The start at rest under the force is refused on the host for walled
+    lattices and the finite-difference treatment."""
+    import numpy as np
+    lb, so = lib
+    p = lb.lb_params_default(nx=32, ny=8, precision=lb.LB_PREC_FP64, init_balanced=1)
+    setattr(p, field, value)
+    if field == "walls":
+        p.tile_x, p.tile_y = 32, 8
+    rho = np.ones((8, 32))
+    dp = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ctx = ctypes.c_void_p()
+    st = so.lb_init(ctypes.byref(p), dp, dp, None, ctypes.byref(ctx))
+    assert st == lb.LB_ERR_UNSUPPORTED
+    assert ctx.value is None
+    assert "rest" in lb.lb_last_error()
 
 
 def test_null_arguments(lib):
