@@ -426,6 +426,7 @@ def run_variants(lb, torch, rho, T, stream, sites):
             pv = workload_params(lb, prec, thermal)
             d_rho = torch.from_numpy(rho).cuda()
             d_T = torch.from_numpy(T).cuda()
+            torch.cuda.synchronize()  # the copies ran on torch's stream, the start on the library's
             c = lb.lb_init_device(pv, d_rho, d_T, stream)
             nseg = 2 if prec == "fp64" else 5
             tv = time_device(lb, c, stream, nseg, 1, torch)

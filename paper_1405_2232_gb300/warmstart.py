@@ -87,9 +87,22 @@ def case_inputs(doms, masks):
 
 
 def train(X, Y, L, epochs=30, batch=16, lr=1e-3, seed=7, log=None, augment=True):
-    """Train a fresh network on device tensors X [n, L, L, 3], Y [n, L, L, 2]."""
+    """Train a fresh network on device tensors X [n, L, L, 3], Y [n, L, L, 2].
+
+    The network and the batch preparation share one CUDA stream: the training
+    step does not synchronise, so a batch built on another stream could be
+    freed and its memory handed to the next batch by torch's caching allocator
+    while the network's kernels still read it."""
     import torch
-    net = UN.UNet(L, L, batch)
+    s_train = torch.cuda.Stream()
+    s_train.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_train):
+        return _train_on_stream(X, Y, L, epochs, batch, lr, seed, log, augment, s_train)
+
+
+def _train_on_stream(X, Y, L, epochs, batch, lr, seed, log, augment, stream):
+    import torch
+    net = UN.UNet(L, L, batch, stream=stream)
     arch = [("", ci, co, k, (3 if i == 0 else ci)) for i, (ci, co, k, _) in enumerate(UN.layer_table(net.cfg))]
     net.set_params(I.unet_init_params(arch, seed=11))
     n = X.shape[0]
