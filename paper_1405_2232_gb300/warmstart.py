@@ -152,17 +152,13 @@ def predict(net, X, batch):
     return out
 
 
-def _arm(steps, st, wall):
-    return dict(wall_s=wall, converged=int(np.sum(st == lb.LB_OK)),
-                failed=int(np.sum((st != lb.LB_OK) & (st != lb.LB_ERR_NOT_CONVERGED))),
-                capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)))
-
-
 def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
-    """Plain solve from the initial fields (f^eq at u = 0) against the warm
-    solve (network prediction, handoff, start at rest under the force), with
-    the two other combinations beside them: the plain fields started at rest
-    (no network) and the prediction started at u = 0 in f^eq."""
+    """Plain solve from the initial fields (f^eq at u = 0) against warm solves
+    from the network's prediction after the handoff (mass and energy restored),
+    with the start at rest under the force.  Beside them: the plain fields
+    started at rest (no network), the predicted density with the initial
+    temperature (t_dev_scale = 0 in the handoff), and the prediction started
+    at u = 0 in f^eq."""
     import torch
     dev = torch.device("cuda")
     L = doms[0].L
@@ -170,79 +166,79 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     params_bal = sweep_params(doms, init_balanced=1)
     rho0 = np.stack([d.rho for d in doms])
     T0 = np.stack([d.T for d in doms])
-    # plain
-    steps_p, _, st_p, wall_p, Bp = solve(params, list(rho0), list(T0), cap, chunk_rows=chunk_rows)
-    ok_p = np.flatnonzero(st_p == lb.LB_OK)
-    ref = {int(d): Bp.fields(int(d)) for d in ok_p}
-    Bp.close()
-    # plain fields, started at rest under the force
-    steps_pb, _, st_pb, wall_pb, Bpb = solve(params_bal, list(rho0), list(T0), cap, chunk_rows=chunk_rows)
-    Bpb.close()
+    arms, per_case = {}, {}
+
+    def run(name, prm, rhos, Ts, device_inputs, start, extra_s=0.0):
+        steps, _, st, wall, B = solve(prm, rhos, Ts, cap, device_inputs=device_inputs, chunk_rows=chunk_rows)
+        B_fields = {int(d): B.fields(int(d)) for d in np.flatnonzero(st == lb.LB_OK)} if name == "plain" else None
+        B.close()
+        arms[name] = dict(wall_s=wall + extra_s, solve_s=wall, converged=int(np.sum(st == lb.LB_OK)),
+                          failed=int(np.sum((st != lb.LB_OK) & (st != lb.LB_ERR_NOT_CONVERGED))),
+                          capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)), start=start)
+        per_case[name] = (steps, st)
+        return B_fields
+
+    ref = run("plain", params, list(rho0), list(T0), False, "f^eq at u = 0")
+    run("plain_balanced", params_bal, list(rho0), list(T0), False, "at rest under the force")
     # warm: inference + handoff + solve, all timed
     X = torch.from_numpy(case_inputs(doms, masks)).to(dev)
     d_rho0 = torch.from_numpy(rho0).to(dev)
     d_T0 = torch.from_numpy(T0).to(dev)
-    _sync()
-    t0 = time.perf_counter()
-    pred = predict(net, X, batch)
-    d_rho = torch.empty_like(d_rho0)
-    d_T = torch.empty_like(d_T0)
-    UN.warm_fields(len(doms), L, L, pred, I.UNET_NORM, d_rho0, d_T0, d_rho, d_T)
-    _sync()
-    t_inf = time.perf_counter() - t0
     stride = L * L * 8
-    rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
-    tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
-    steps_w, _, st_w, wall_w, Bw = solve(params_bal, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
-    Bw.close()
-    # the prediction started at u = 0 in f^eq (no balance)
-    steps_wu, _, st_wu, wall_wu, Bwu = solve(params, rp, tp, cap, device_inputs=True, chunk_rows=chunk_rows)
-    Bwu.close()
+    fields = {}
+    for tag, norm in (("", I.UNET_NORM), ("_T0", dict(I.UNET_NORM, t_dev_scale=0.0))):
+        _sync()
+        t0 = time.perf_counter()
+        pred = predict(net, X, batch)
+        d_rho = torch.empty_like(d_rho0)
+        d_T = torch.empty_like(d_T0)
+        UN.warm_fields(len(doms), L, L, pred, norm, d_rho0, d_T0, d_rho, d_T)
+        _sync()
+        t_inf = time.perf_counter() - t0
+        fields[tag] = (d_rho, d_T, t_inf)
+        rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
+        tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
+        run("warm" + tag, params_bal, rp, tp, True, "at rest under the force", t_inf)
+        if not tag:
+            run("warm_unbalanced", params, rp, tp, True, "f^eq at u = 0", t_inf)
+    for name in ("warm", "warm_T0", "warm_unbalanced"):
+        arms[name]["inference_s"] = fields["_T0" if name == "warm_T0" else ""][2]
     # prediction error against the plain steady state
-    h_rho, h_T = d_rho.cpu().numpy(), d_T.cpu().numpy()
+    h_rho, h_T = fields[""][0].cpu().numpy(), fields[""][1].cpu().numpy()
     e_rho = [np.abs(h_rho[d] - ref[d][0]).max() / np.abs(ref[d][0]).max() for d in ref]
     e_T = [np.abs(h_T[d] - ref[d][1]).max() / np.abs(ref[d][1]).max() for d in ref]
+    e_T0 = [np.abs(T0[d] - ref[d][1]).max() / np.abs(ref[d][1]).max() for d in ref]
     rms_rho = [float(np.sqrt(np.mean((h_rho[d] - ref[d][0]) ** 2))) for d in ref]
     med_rho = [float(np.median(np.abs(h_rho[d] - ref[d][0]))) for d in ref]
     rms_rho0 = [float(np.sqrt(np.mean((rho0[d] - ref[d][0]) ** 2))) for d in ref]
+    st_p, st_w = per_case["plain"][1], per_case["warm"][1]
+    steps_p, steps_w = per_case["plain"][0], per_case["warm"][0]
     both = np.flatnonzero((st_p == lb.LB_OK) & (st_w == lb.LB_OK))
-    conv = [st == lb.LB_OK for st in (st_p, st_pb, st_w, st_wu)]
-    allc = np.flatnonzero(conv[0] & conv[1] & conv[2] & conv[3])
-
-    def med(steps):
-        return float(np.median(steps[allc])) if allc.size else None
-
-    warm = _arm(steps_w, st_w, wall_w + t_inf)
-    warm.update(solve_s=wall_w, inference_s=t_inf, start="at rest under the force")
-    warm_u = _arm(steps_wu, st_wu, wall_wu + t_inf)
-    warm_u.update(solve_s=wall_wu, inference_s=t_inf, start="f^eq at u = 0")
-    plain_b = _arm(steps_pb, st_pb, wall_pb)
-    plain_b.update(start="at rest under the force")
-    plain = _arm(steps_p, st_p, wall_p)
-    plain.update(start="f^eq at u = 0")
-    return dict(
-        cases=len(doms), L=L, cap=cap,
-        plain=plain, warm=warm, plain_balanced=plain_b, warm_unbalanced=warm_u,
-        all_four_converged=int(allc.size),
-        median_steps_all_four=dict(plain=med(steps_p), plain_balanced=med(steps_pb), warm=med(steps_w),
-                                   warm_unbalanced=med(steps_wu)),
+    allc = np.flatnonzero(np.all([v[1] == lb.LB_OK for v in per_case.values()], axis=0))
+    out = dict(
+        cases=len(doms), L=L, cap=cap, **arms,
+        all_arms_converged=int(allc.size),
+        median_steps_all_arms={k: (float(np.median(v[0][allc])) if allc.size else None)
+                               for k, v in per_case.items()},
         both_converged=int(both.size),
         median_steps_plain=float(np.median(steps_p[both])) if both.size else None,
         median_steps_warm=float(np.median(steps_w[both])) if both.size else None,
         steps_ratio=float(np.sum(steps_w[both]) / np.sum(steps_p[both])) if both.size else None,
         prediction_error=dict(e_rho_median=float(np.median(e_rho)) if e_rho else None,
                               e_T_median=float(np.median(e_T)) if e_T else None,
+                              e_T_initial_state_median=float(np.median(e_T0)) if e_T0 else None,
                               e_rho_max=float(np.max(e_rho)) if e_rho else None,
                               rms_rho_median=float(np.median(rms_rho)) if rms_rho else None,
                               abs_rho_median_of_medians=float(np.median(med_rho)) if med_rho else None,
                               rms_rho_initial_state_median=float(np.median(rms_rho0)) if rms_rho0 else None),
-        per_case=dict(T_over_Tc=[d.T_over_Tc for d in doms], tau_f=[d.tau_f for d in doms],
-                      kind=[d.kind for d in doms], steps_plain=steps_p.tolist(), status_plain=st_p.tolist(),
-                      steps_warm=steps_w.tolist(), status_warm=st_w.tolist(),
-                      steps_plain_balanced=steps_pb.tolist(), status_plain_balanced=st_pb.tolist(),
-                      steps_warm_unbalanced=steps_wu.tolist(), status_warm_unbalanced=st_wu.tolist(),
-                      e_rho={int(d): float(e) for d, e in zip(ref, e_rho)}),
     )
+    pc = dict(T_over_Tc=[d.T_over_Tc for d in doms], tau_f=[d.tau_f for d in doms],
+              kind=[d.kind for d in doms], e_rho={int(d): float(e) for d, e in zip(ref, e_rho)})
+    for k, (steps, st) in per_case.items():
+        pc["steps_" + k] = steps.tolist()
+        pc["status_" + k] = st.tolist()
+    out["per_case"] = pc
+    return out
 
 
 def train_step_bench(L=256, batch=16, steps=10, warmup=3):
