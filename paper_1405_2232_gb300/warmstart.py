@@ -12,8 +12,10 @@ Pipeline (every numerical step runs in the CUDA library):
    once from the network's prediction (handoff ``un_warm_fields``: density and
    temperature rescaled to the initial mass and energy, then the start at rest
    under the force, lb_params.init_balanced), both with the same batched
-   solver and residual test; report wall-clock seconds and steps, and the two
-   mixed arms (plain fields at rest; prediction at u = 0 in f^eq).
+   solver and residual test; report wall-clock seconds and steps, and three
+   more arms on the same cases: the plain fields at rest (no network), the
+   predicted density with the initial temperature, and the prediction at
+   u = 0 in f^eq.
 
 Run as ``python -m paper_1405_2232_gb300.warmstart [--train N] [--test N]``;
 it prints one JSON object.  The sweep recipe: psi from the domain's T0
