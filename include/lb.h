@@ -179,7 +179,9 @@ lb_status lb_init(const lb_params* p, const double* rho0, const double* T0,
                   void* stream, lb_ctx** out);
 
 /* As lb_init, but rho0 and T0 are DEVICE float64 arrays [ny][nx]; they are
- * read by kernels on the stream before the call returns. */
+ * read by kernels on the stream before the call returns.  They must be
+ * complete when the call is made: work that writes them on another stream
+ * is synchronised by the caller first. */
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,
                          void* stream, lb_ctx** out);
 
@@ -267,9 +269,10 @@ lb_status lb_autotune(const lb_params* p, int32_t steps, void* stream, lb_params
 typedef struct lb_batch lb_batch; /* opaque; owned by the library */
 
 /* Create a batch of n domains; params[d] describes domain d, rho0[d] and T0[d]
- * are its float64 fields [ny][nx], in host or device memory (copied; the
- * copy direction follows from unified addressing).  Initial state as lb_init
- * (params[d].init_balanced chooses it per domain). */
+ * are its float64 fields [ny][nx], in host or device memory (copied on the
+ * batch's stream before the call returns; the copy direction follows from
+ * unified addressing; device fields must be complete when the call is made).
+ * Initial state as lb_init (params[d].init_balanced chooses it per domain). */
 lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const* rho0,
                         const double* const* T0, void* stream, lb_batch** out);
 

@@ -60,9 +60,14 @@ lb_status un_layer_info(const un_config* cfg, int32_t k, int32_t* cin, int32_t* 
                         int32_t* ksize, int64_t* offset);
 
 /* Create a net on the device of `stream` (NULL: the current device and a
- * stream of its own).  Parameters start at zero; set them with
+ * stream of its own, non-blocking).  Parameters start at zero; set them with
  * un_set_params.  LB_ERR_ARG for H, W not multiples of 8, base not a
- * multiple of 32 or max_batch < 1; LB_ERR_OOM if the activations do not fit. */
+ * multiple of 32 or max_batch < 1; LB_ERR_OOM if the activations do not fit.
+ * Every asynchronous call below runs on that stream and reads its device
+ * inputs there: the caller orders their production before the call and keeps
+ * them alive and unchanged until the net's stream has passed it (an input
+ * written on another stream, or freed to an allocator that hands its memory
+ * to other streams' work, races with the net). */
 lb_status un_create(const un_config* cfg, void* stream, un_net** out);
 
 /* Copy all n = un_param_count parameters in (host or device float32; resets
