@@ -60,6 +60,7 @@ def run(torch, N):
         d_in = torch.from_numpy(x).to(dev)
         d_t = torch.from_numpy(t).to(dev)
         d_out = torch.empty((NB, H, W, 2), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()  # inputs copied on torch's stream, read on the net's
         net.forward(d_in, d_out, NB)
         net.synchronize()  # the net runs on a stream of its own
         y = d_out.cpu().numpy().astype(np.float64)
@@ -214,6 +215,7 @@ def test_adam_step_and_training(torch, N):
     with N.UNet(H, W, NB, BASE) as net:
         net.set_params(flat)
         d_in, d_t = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
+        torch.cuda.synchronize()  # inputs copied on torch's stream, read on the net's
         net.loss_grad(d_in, d_t, NB)
         g = net.grads().astype(np.float64)
         net.adam_step(1e-3)
