@@ -232,6 +232,21 @@ lb_status lb_load_state(lb_ctx* ctx, const void* host_blob);
 /* Number of steps taken since lb_init (or the loaded state's time). */
 int64_t lb_time(const lb_ctx* ctx);
 
+/* Failure detection (the paper has no counterpart).  The strip-marching step
+ * kernels (lattice Boltzmann and finite-difference) hand rows from a copy
+ * warp to the compute warps through mbarriers, and every such wait is
+ * bounded: after `cycles` SM clock cycles (0: the default, 2e9, about one
+ * second at GB300 clocks) the CTA stops, records LB_ERR_TIMEOUT in the
+ * context's error word and leaves once the copies it issued have landed (that
+ * last wait always takes the default limit).  The next synchronising call
+ * reports LB_ERR_TIMEOUT; the state of the step that timed out is undefined
+ * (restore it with lb_load_state or lb_set_populations), the context and the
+ * device stay usable.  A tiny limit makes the wait give up on purpose (tests
+ * of the error path).  Applies to steps launched after the call; the tile
+ * kernels and the batched solver do not wait and ignore it.  LB_ERR_ARG for
+ * cycles < 0. */
+lb_status lb_set_wait_limit(lb_ctx* ctx, int64_t cycles);
+
 /* Parameters the context runs with (tile sizes resolved). */
 lb_status lb_get_params(const lb_ctx* ctx, lb_params* out);
 
@@ -344,9 +359,12 @@ lb_status lb_batch_autotune(lb_batch* b, int32_t steps, int32_t* chunk_rows,
  *
  * Limits and errors: nx*ny <= 16,777,216 sites (4096^2), else LB_ERR_ARG with
  * a message.  The first call on a device looks up the scratch address (make it
- * before any stream capture).  Every call shares the scratch; each call writes
- * all entries it reads, so nothing needs clearing, but calls that overlap on the
- * GPU race on it. */
+ * before any stream capture) and caches it for the life of the process, which
+ * assumes the device is not reset (cudaDeviceReset) meanwhile.  Every call
+ * shares the scratch; each call writes all entries it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU race on it.  The work runs on the
+ * stream's device (the current device for a NULL stream); the calling thread's
+ * current device is left as it was. */
 lb_status lb_field_totals_noalloc(int32_t nx, int32_t ny, double cv, const double* d_rho,
                                   const double* d_ux, const double* d_uy, const double* d_T,
                                   const double* d_ref_rho, const double* d_ref_T, int64_t K,

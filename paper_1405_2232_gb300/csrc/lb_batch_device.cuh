@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             for (int j = 0; j < njobs; ++j, ++jg) {
                 const int s = (int)(jg % STAGES);
                 if (jg >= STAGES) {
-                    if (!mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1))) {
+                    // the warp takes one decision (its lanes poll the barrier independently)
+                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1)))) {
                         if (lane == 0) atomicOr(D.kp.err, 1 << LB_ERR_TIMEOUT);
                         return;  // consumers then time out on "full" and leave
                     }

@@ -214,6 +214,7 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
         k.base_g[i] = dev ? (float)(wd(i) * p.rho0 * p.cv * p.T0) : 0.0f;
     }
     k.err = err;
+    k.wait_cycles = WAIT_CYCLES_DEFAULT;
     return k;
 }
 
@@ -356,6 +357,8 @@ lb_status check_device_error(lb_ctx* c) {
             return fail(LB_ERR_PSI_DOMAIN,
                         "psi^2 = 2 (p_EOS - rho cs^2)/G became negative with beta != 0");
         if (h & (1 << LB_ERR_NONFINITE)) return fail(LB_ERR_NONFINITE, "rho or T became non-finite");
+        if (h & (1 << LB_ERR_TIMEOUT))
+            return fail(LB_ERR_TIMEOUT, "a bounded device wait of the step kernel gave up (the state is undefined)");
         return fail(LB_ERR_CUDA, "device error word 0x%x", h);
     }
     return LB_OK;
@@ -697,8 +700,8 @@ lb_status lb_state_size(const lb_ctx* c, size_t* bytes) {
 lb_status lb_save_state(lb_ctx* c, void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
     if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
-    CU(cudaMemcpyAsync(host_blob, c->alloc[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(cudaMemcpyAsync(host_blob, c->alloc[c->cur], c->buf_bytes, cudaMemcpyDeviceToHost, c->stream), "save state");
     CU(cudaStreamSynchronize(c->stream), "synchronize");
     std::memcpy(static_cast<char*>(host_blob) + c->buf_bytes, &c->t, sizeof(int64_t));
     return LB_OK;
@@ -707,8 +710,8 @@ lb_status lb_save_state(lb_ctx* c, void* host_blob) {
 lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
     if (!c || !host_blob) return fail(LB_ERR_ARG, "NULL argument");
     if (c->fd) return fail(LB_ERR_UNSUPPORTED, "the finite-difference treatment has no g populations");
-    CU(cudaMemcpyAsync(c->alloc[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(cudaMemcpyAsync(c->alloc[c->cur], host_blob, c->buf_bytes, cudaMemcpyHostToDevice, c->stream), "load state");
     CU(cudaStreamSynchronize(c->stream), "synchronize");
     std::memcpy(&c->t, static_cast<const char*>(host_blob) + c->buf_bytes, sizeof(int64_t));
     c->have_ref = false;
@@ -716,6 +719,13 @@ lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
 }
 
 int64_t lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+
+lb_status lb_set_wait_limit(lb_ctx* c, int64_t cycles) {
+    if (!c) return fail(LB_ERR_ARG, "ctx is NULL");
+    if (cycles < 0) return fail(LB_ERR_ARG, "cycles must be >= 0 (0 restores the default)");
+    c->kp.wait_cycles = cycles == 0 ? WAIT_CYCLES_DEFAULT : (long long)cycles;
+    return LB_OK;
+}
 
 lb_status lb_get_params(const lb_ctx* c, lb_params* out) {
     if (!c || !out) return fail(LB_ERR_ARG, "NULL argument");

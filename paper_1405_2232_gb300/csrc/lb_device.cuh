@@ -95,7 +95,12 @@ struct KParams {
     double T_psi;
     float base_f[9], base_g[9];  // deviation bases of the 16-bit modes
     int* err;                    // sticky device error word (bit per lb_status)
+    long long wait_cycles;       // limit of the strip kernels' pipeline waits (<= 0: default)
 };
+
+// Default limit of a bounded device wait, in clock cycles (about one second
+// at GB300 clocks).
+constexpr long long WAIT_CYCLES_DEFAULT = 2000000000LL;
 
 enum BetaMode { BETA_ZERO = 0, BETA_ONE = 1, BETA_MIXED = 2 };
 

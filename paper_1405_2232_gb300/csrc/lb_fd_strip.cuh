@@ -163,7 +163,9 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         for (int j = 0; j < njobs; ++j) {
             const int s = j % STAGES;
             if (j >= STAGES) {
-                if (!mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                // the warp takes one decision (its lanes poll the barrier independently)
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1),
+                                                               kp.wait_cycles))) {
                     if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
                     break;
                 }
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         // A(j)
         if (j < njobs) {
             const int s = j % STAGES;
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort = 1;
             if (colA != -99) {
                 const elem* st = stage + (size_t)s * NP * SEGW;
                 const int c = colA + HALO;

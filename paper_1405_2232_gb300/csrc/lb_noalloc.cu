@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(NA_THREADS)
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) and cached.
+// device current) and cached.  The cache assumes the device is not reset
+// (cudaDeviceReset) while the library is loaded.
 std::mutex g_na_mu;
 double* g_na_addr[64] = {};
 
@@ -162,19 +163,29 @@ extern "C" lb_status lb_field_totals_noalloc(int32_t nx, int32_t ny, double cv, 
     if (have_ref && K <= 0) return lbgb::record_error(LB_ERR_ARG, "K must be > 0 with reference fields");
     if (!(cv > 0.0)) return lbgb::record_error(LB_ERR_ARG, "c_v must be > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int dev = 0;
-    cudaError_t e = st ? cudaStreamGetDevice(st, &dev) : cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    // the work runs on the stream's device; the caller's current device is
+    // restored before returning
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return lbgb::record_error(LB_ERR_CUDA, cudaGetErrorString(e));
+    int dev = prev;
+    if (st) e = cudaStreamGetDevice(st, &dev);
+    if (e == cudaSuccess && dev != prev) e = cudaSetDevice(dev);
     if (e != cudaSuccess) return lbgb::record_error(LB_ERR_CUDA, cudaGetErrorString(e));
     double* part = nullptr;
     lb_status ls = na_scratch(dev, &part);
-    if (ls != LB_OK) return ls;
-    const int nblocks = (int)((n + NA_SITES_PER_BLOCK - 1) / NA_SITES_PER_BLOCK);
-    k_na_partials<<<nblocks, NA_THREADS, 0, st>>>(n, cv, d_rho, d_ux, d_uy, d_T,
-                                                  have_ref ? d_ref_rho : nullptr,
-                                                  have_ref ? d_ref_T : nullptr, part);
-    k_na_final<<<1, NA_THREADS, 0, st>>>(part, nblocks, (long long)K, have_ref ? 1 : 0, d_out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return lbgb::record_error(LB_ERR_CUDA, cudaGetErrorString(e));
-    return LB_OK;
+    if (ls == LB_OK) {
+        const int nblocks = (int)((n + NA_SITES_PER_BLOCK - 1) / NA_SITES_PER_BLOCK);
+        k_na_partials<<<nblocks, NA_THREADS, 0, st>>>(n, cv, d_rho, d_ux, d_uy, d_T,
+                                                      have_ref ? d_ref_rho : nullptr,
+                                                      have_ref ? d_ref_T : nullptr, part);
+        k_na_final<<<1, NA_THREADS, 0, st>>>(part, nblocks, (long long)K, have_ref ? 1 : 0, d_out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) ls = lbgb::record_error(LB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (dev != prev) {
+        e = cudaSetDevice(prev);
+        if (e != cudaSuccess && ls == LB_OK) ls = lbgb::record_error(LB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return ls;
 }

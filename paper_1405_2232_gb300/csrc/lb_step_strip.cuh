@@ -30,7 +30,9 @@
 // never stalls the consumers' per-row synchronisation.
 //
 // Every mbarrier wait is bounded: on timeout the CTA records LB_ERR_TIMEOUT,
-// the producer waits (again bounded) for the copies it issued, and returns.
+// the producer waits (again bounded, always with the default limit, so that no
+// copy is still in flight when the CTA exits) for the copies it issued, and
+// returns.  The limit of the pipeline waits is kp.wait_cycles.
 #pragma once
 
 #include "lb_device.cuh"
@@ -77,12 +79,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait (about one second at GB300 clocks); false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: false once `limit` clock cycles have passed (the default is
+// about one second at GB300 clocks; a limit <= 0 means the default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit = WAIT_CYCLES_DEFAULT) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (limit <= 0) limit = WAIT_CYCLES_DEFAULT;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -216,7 +221,9 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             if (j >= STAGES) {
                 // the stage's previous job (j - STAGES) must have been released;
                 // on timeout stop issuing (the consumers then time out on "full")
-                if (!mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                // the warp takes one decision (its lanes poll the barrier independently)
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1),
+                                                               kp.wait_cycles))) {
                     if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
                     break;
                 }
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     int flags = 0;
     for (int j = 0; j < njobs; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) s_abort = 1;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort = 1;
         // 1. rho, T, psi of pre-collision row j at ring column r_psi
         if (has_psi) {
             const elem* st = stage + (size_t)s * 18 * SEGW;

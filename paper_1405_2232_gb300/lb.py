@@ -70,6 +70,7 @@ EXPORTED = [
     "lb_moments", "lb_moments_device", "lb_get_populations", "lb_set_populations",
     "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
     "lb_get_params", "lb_free", "lb_last_error", "lb_version", "lb_field_totals_noalloc",
+    "lb_set_wait_limit",
     "lb_batch_init", "lb_batch_step", "lb_batch_check", "lb_batch_run", "lb_batch_fields",
     "lb_batch_time", "lb_batch_free", "lb_tune_candidate", "lb_autotune",
     "lb_batch_set_chunk_rows", "lb_batch_chunk_rows", "lb_batch_autotune",
@@ -109,6 +110,7 @@ def load(path: str | None = None):
         "lb_save_state": (st, [vp, vp]),
         "lb_load_state": (st, [vp, vp]),
         "lb_time": (ctypes.c_int64, [vp]),
+        "lb_set_wait_limit": (st, [vp, ctypes.c_int64]),
         "lb_get_params": (st, [vp, P]),
         "lb_free": (st, [vp]),
         "lb_last_error": (ctypes.c_char_p, []),
@@ -269,15 +271,54 @@ def lb_time(ctx) -> int:
     return int(load().lb_time(ctx))
 
 
+def lb_set_wait_limit(ctx, cycles: int):
+    """Limit (SM clock cycles, 0 = default) of the strip kernels' bounded waits."""
+    _check(load().lb_set_wait_limit(ctx, int(cycles)))
+
+
 def lb_free(ctx):
     if ctx is not None:
         _check(load().lb_free(ctx))
 
 
+def _check_noalloc_args(nx, ny, fields, d_out, stream):
+    """The C entry point takes raw device addresses and trusts their sizes, so
+    the binding checks every tensor first: float64, C-contiguous, large enough
+    for the nx*ny sites (d_out: LB_TOTALS_N values), on a CUDA device, all on
+    the stream's device.  Raises LbError(LB_ERR_ARG) otherwise."""
+    n = int(nx) * int(ny)
+
+    def bad(msg):
+        raise LbError(LB_ERR_ARG, msg)
+
+    named = [(k, v) for k, v in fields if v is not None] + [("d_out", d_out)]
+    for name, t in named:
+        if not hasattr(t, "data_ptr") or not hasattr(t, "dtype"):
+            bad(f"{name}: a torch tensor is required")
+        if str(t.dtype) != "torch.float64":
+            bad(f"{name}: float64 required, got {t.dtype}")
+        if not t.is_contiguous():
+            bad(f"{name}: must be contiguous")
+        need = LB_TOTALS_N if name == "d_out" else n
+        if t.numel() < need:
+            bad(f"{name}: {t.numel()} elements, at least {need} required")
+    for name, t in named:
+        if not t.is_cuda:
+            bad(f"{name}: must be a CUDA tensor")
+    devs = {t.device.index for _, t in named}
+    if stream is not None and hasattr(stream, "device"):
+        devs.add(stream.device.index)
+    if len(devs) > 1:
+        bad(f"tensors and stream on different devices: {sorted(devs)}")
+
+
 def lb_field_totals_noalloc(nx, ny, cv, d_rho, d_ux, d_uy, d_T, d_out, d_ref_rho=None,
                             d_ref_T=None, K=0, stream=None):
     """Totals of device fields without any device allocation (see include/lb.h);
-    d_out receives [mass, energy, px, py, residual] on the device."""
+    d_out receives [mass, energy, px, py, residual] on the device.  Every
+    tensor is checked (dtype, layout, size, device) before the call."""
+    _check_noalloc_args(nx, ny, [("d_rho", d_rho), ("d_ux", d_ux), ("d_uy", d_uy), ("d_T", d_T),
+                                 ("d_ref_rho", d_ref_rho), ("d_ref_T", d_ref_T)], d_out, stream)
     _check(load().lb_field_totals_noalloc(int(nx), int(ny), float(cv), _addr(d_rho), _addr(d_ux),
                                           _addr(d_uy), _addr(d_T), _addr(d_ref_rho),
                                           _addr(d_ref_T), int(K), _addr(d_out), _stream(stream)))

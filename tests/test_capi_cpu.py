@@ -117,3 +117,30 @@ def test_oracle_and_cuda_path_share_nothing():
         if fn.endswith(".py"):
             text = open(os.path.join(ROOT, "paper_1405_2232_gb300", fn)).read()
             assert "import oracle" not in text and "from oracle" not in text, fn
+
+
+def test_noalloc_binding_rejects_bad_tensors(lib):
+    """lb_field_totals_noalloc takes raw device addresses, so the binding checks
+    dtype, layout, size and device of every tensor before the call (no tensor
+    reaches the library here: each case is rejected on the host)."""
+    import torch
+    lb, _ = lib
+    nx, ny = 8, 4
+    ok = lambda n=nx * ny: torch.zeros(n, dtype=torch.float64)
+    out = torch.zeros(lb.LB_TOTALS_N, dtype=torch.float64)
+    cases = [
+        ((torch.zeros(nx * ny, dtype=torch.float32), ok(), ok(), ok(), out), "float64"),
+        ((torch.zeros(ny, 2 * nx, dtype=torch.float64)[:, ::2], ok(), ok(), ok(), out), "contiguous"),
+        ((ok(nx * ny - 1), ok(), ok(), ok(), out), "at least"),
+        ((ok(), ok(), ok(), ok(), torch.zeros(4, dtype=torch.float64)), "at least 5"),
+        ((ok(), ok(), ok(), ok(), out), "CUDA"),
+        ((12345, ok(), ok(), ok(), out), "torch tensor"),
+    ]
+    for args, word in cases:
+        with pytest.raises(lb.LbError) as ei:
+            lb.lb_field_totals_noalloc(nx, ny, 1.0, *args)
+        assert ei.value.status == lb.LB_ERR_ARG and word in str(ei.value), (word, str(ei.value))
+    with pytest.raises(lb.LbError) as ei:  # a too-small reference field
+        lb.lb_field_totals_noalloc(nx, ny, 1.0, ok(), ok(), ok(), ok(), out, d_ref_rho=ok(3),
+                                   d_ref_T=ok(), K=1)
+    assert "d_ref_rho" in str(ei.value)

@@ -9,10 +9,14 @@ Tolerances (max-norm errors e_phi = max|d phi| / max|phi_oracle| per field):
     their plane's maximum; moments within 1e-5 (the velocity is a difference
     of populations divided by rho, so one FP32 ulp of the populations of the
     vapour, rho ~ 0.02, is ~4e-6 of max|u|).
-  * FP32 storage after 1000 steps of the 64x64 slab: rho, u and T within 2e-5
-    (the oracle amplifies an FP32-sized perturbation of the start state only
-    about 10x over these steps, tests/test_sensitivity.py).  u is measured
-    against max|u| over both components.
+  * FP32 storage after 1000 steps of the 64x64 slab: rho and T within 2e-5,
+    u within 1e-4 (measured on the GPU: e_u about 4e-5).  The 2e-5 target on u
+    is not met: FP32 arithmetic cannot meet it on this workload.  A float32
+    model of the step (tests/test_fp32_tolerance_cpu.py) shows FP32 storage
+    alone gives e_u = 8e-6, the FP32 collision alone 3.8e-5 and FP32
+    throughout 7.7e-5 (u, max 0.014, is a small balance of force and pressure,
+    so 1e-7 roundings of psi or the collision appear ~100x larger in it).
+    u is measured against max|u| over both components.
   * 16-bit deviation storage, one step: each population within half an ulp of
     its stored deviation plus the FP32 step error (bound derived per element).
 """

@@ -63,3 +63,55 @@ def test_noalloc_totals_match_lb_totals_two_calls():
         assert ei.value.status == lb.LB_ERR_ARG and "limit" in str(ei.value)
     finally:
         L.close()
+
+
+def test_noalloc_totals_full_scratch_no_device_memory_change():
+    """A 4096 x 4096 lattice fills every slot of the static scratch (4096 CTAs of
+    4096 sites).  Its totals match lb_totals of the same state on two calls in a
+    row, the free device memory reported by the driver is the same before and
+    after those calls (nothing is allocated), and the caller's current device is
+    unchanged."""
+    import torch
+    from paper_1405_2232_gb300 import lb
+    torch.cuda.set_device(0)
+    lb.load()
+    n = 4096
+    rho, T = I.spinodal_fields(n, n)
+    stream = torch.cuda.Stream()
+    # FP64 storage: the moments lb_totals sums are then exactly the fields handed over
+    L = lb.Lattice(rho, T, stream=stream, nx=n, ny=n, precision="fp64", beta=1.3,
+                   thermal=lb.LB_THERMAL_EQ24)
+    try:
+        fields = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(6)]
+        torch.cuda.synchronize()
+        L.step(10)
+        lb.lb_moments_device(L.ctx, fields[4], None, None, fields[5])  # reference at t = 10
+        L.totals()
+        L.step(20)
+        lb.lb_moments_device(L.ctx, *fields[:4])
+        expect = L.totals()                # residual over K = 20 steps
+        L.synchronize()
+        outs = [torch.full((lb.LB_TOTALS_N,), float("nan"), dtype=torch.float64, device="cuda")
+                for _ in range(2)]
+        torch.cuda.synchronize()
+        # set-up call (the first call on a device may load the library's device code)
+        lb.lb_field_totals_noalloc(n, n, 1.0, *fields[:4], outs[0], d_ref_rho=fields[4],
+                                   d_ref_T=fields[5], K=20, stream=stream)
+        stream.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for out in outs:                   # two calls in a row on the same scratch
+            lb.lb_field_totals_noalloc(n, n, 1.0, *fields[:4], out, d_ref_rho=fields[4],
+                                       d_ref_T=fields[5], K=20, stream=stream)
+        stream.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0, (free0, free1)
+        assert torch.cuda.current_device() == 0
+        for out in outs:
+            got = out.cpu().numpy()
+            assert got[0] == pytest.approx(expect[0], rel=1e-12)
+            assert got[1] == pytest.approx(expect[1], rel=1e-12)
+            assert abs(got[2] - expect[2]) <= 1e-12 * expect[0]
+            assert abs(got[3] - expect[3]) <= 1e-12 * expect[0]
+            assert got[4] == pytest.approx(expect[4], rel=1e-9) and got[4] > 0
+    finally:
+        L.close()
