@@ -400,7 +400,7 @@ def run_sweep(lb, torch, dist, world, rank, args):
         dist, wall, int(np.sum(st == 0)), int(np.sum((st != 0) & (st != 8))), int(np.sum(st == 8)), sites,
         "cuda")
     ok = st == 0
-    return {"workload": f"{args.sweep_domains} periodic domains, L~U{{64..512}} (multiple of 4), T/Tc~U[0.6,0.95], "
+    return {"workload": f"{args.sweep_domains} periodic domains, L~U{{64..512}}, T/Tc~U[0.6,0.95], "
                         "G~U[-1.2,-0.8], tau_f~U[0.6,1.2], droplet/slab, seed 4; FP32, Eq.24, beta 1.3, "
                         "psi(rho, T0)",
             "sites": int(tot_sites), "chunk_rows": rows,

@@ -85,7 +85,14 @@ enum {
 
 /* Storage of the populations in device memory; collision arithmetic is FP64
  * for LB_PREC_FP64 and FP32 otherwise.  The 16-bit modes store the deviation
- * h = f - w_i rho0 (and g - w_i rho0 c_v T0), rounded to nearest even. */
+ * h = f - w_i rho0 (and g - w_i rho0 c_v T0) of the eight moving populations
+ * rounded to nearest even, and keep the rest populations f_0, g_0 as FP32
+ * deviations (two 16-bit halves, 40 bytes per site and distribution set):
+ * after each collision the rest population takes the deviation that keeps the
+ * site's stored mass (energy) equal to the mass (energy) it loaded, so the
+ * 16-bit modes conserve mass and energy to one FP32 rounding per site and
+ * step (Eq. (13); sum C_i = 0 after Eq. (25)), where rounding each moving
+ * population on its own changes them coherently. */
 enum {
     LB_PREC_FP64 = 0,
     LB_PREC_FP32 = 1,
@@ -256,7 +263,7 @@ lb_status lb_free(lb_ctx* ctx);
 /* ---------------------------------------------------------------- autotune
  * The fused step (Eqs. 1, 2/4, 7 or 24-25) runs as one of LB_TUNE_N shapes:
  * k = 0, 1: the strip-marching kernel, 256 or 128 columns wide (tile_y == 0;
- * nx a multiple of 16 bytes of elements; FP64: 128 only); k = 2..4: the tile
+ * any nx; FP64: 128 only); k = 2..4: the tile
  * kernel with tiles 32x8, 32x16, 64x4.  Results do not depend on the shape
  * (FP64 storage: bit for bit), only the time does.
  *
@@ -280,7 +287,7 @@ lb_status lb_autotune(const lb_params* p, int32_t steps, void* stream, lb_params
  * row chunk) items.  All domains share the storage precision (FP32 or FP64),
  * the temperature treatment and the force form (beta == 0, beta == 1 or
  * mixed); size, tau_f, tau_g, G, beta, EOS and its constants and c_v are per
- * domain.  nx must be a multiple of 4 (FP32) or 2 (FP64). */
+ * domain; any nx, ny >= 3. */
 typedef struct lb_batch lb_batch; /* opaque; owned by the library */
 
 /* Create a batch of n domains; params[d] describes domain d, rho0[d] and T0[d]

@@ -285,15 +285,14 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
     const int prec = params[0].precision;
     if (prec != LB_PREC_FP32 && prec != LB_PREC_FP64)
         return err(LB_ERR_UNSUPPORTED, "batched solver supports FP32 and FP64 storage");
-    const int halo = prec == LB_PREC_FP64 ? 2 : 4;
     for (int d = 0; d < n; ++d) {
         const lb_params& p = params[d];
         if (!rho0[d] || !T0[d]) return err(LB_ERR_ARG, "domain %d: NULL field", d);
         if (p.precision != prec || p.thermal != params[0].thermal ||
             bmode_of(p.beta) != bmode_of(params[0].beta))
             return err(LB_ERR_ARG, "domain %d: precision, thermal treatment and force form must match domain 0", d);
-        if (p.nx < 3 || p.ny < 3 || p.nx % halo != 0)
-            return err(LB_ERR_ARG, "domain %d: nx must be >= 3 and a multiple of %d, ny >= 3", d, halo);
+        if (p.nx < 3 || p.ny < 3)
+            return err(LB_ERR_ARG, "domain %d: nx and ny must be >= 3", d);
         if (p.walls != LB_WALLS_PERIODIC)
             return err(LB_ERR_UNSUPPORTED, "domain %d: the batched solver runs periodic domains", d);
         if (!(p.tau_f > 0.5) || !(p.tau_g > 0.5) || p.G == 0.0 || !(p.cv > 0.0) || p.eos < 0 || p.eos > 2 ||

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 }
                 int y = item.y0 - 1 + j;
                 y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)18 * strip_copy_bytes<ES, HALO>(W));
                 __syncwarp();
                 if (lane < 18) {
                     const int i = lane;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
                     // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
                     bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW, row + (x0 - HALO),
-                                  (uint32_t)((W + 2 * HALO) * ES), &full[s]);
+                                  strip_copy_bytes<ES, HALO>(W), &full[s]);
                 }
             }
         }

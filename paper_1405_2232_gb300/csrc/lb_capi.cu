@@ -1,6 +1,7 @@
 // lb_capi.cu -- host implementation of the C ABI declared in include/lb.h.
 //
-// A context owns two 18-plane population buffers (ping-pong), an error word,
+// A context owns two population buffers (ping-pong; 18 planes, 20 in the
+// 16-bit modes), an error word,
 // the FP64 reference fields of the steady-state residual and the partial-sum
 // buffer of the deterministic totals reduction.  Every kernel runs on the
 // context's stream.
@@ -99,9 +100,6 @@ lb_status validate(const lb_params* p) {
             return fail(LB_ERR_ARG, "unsupported tile %dx%d", p->tile_x, p->tile_y);
         if (p->tile_y == 0 && p->precision == LB_PREC_FP64 && p->tile_x != 128)
             return fail(LB_ERR_ARG, "the FP64 strip kernel is 128 columns wide");
-        if (p->tile_y == 0 && p->nx % strip_halo(p->precision) != 0)
-            return fail(LB_ERR_ARG, "strip kernel needs nx to be a multiple of %d",
-                        strip_halo(p->precision));
         if (p->tile_y == 0) {
             const PopLayout L = pop_layout(p->precision, p->nx, p->ny, true);
             if (!strip_eligible(p->precision, p->nx, L.plane, p->tile_x))
@@ -421,7 +419,7 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     const bool strip = c->p.tile_y == 0;
     const PopLayout lay = pop_layout(p->precision, p->nx, p->ny, strip);
     const long long pitch = lay.pitch, plane = lay.plane;
-    c->buf_bytes = (size_t)plane * 18 * es;
+    c->buf_bytes = (size_t)plane * pop_planes(p->precision) * es;
     const long long n = (long long)p->nx * p->ny;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&c->alloc[0], c->buf_bytes);

@@ -6,8 +6,9 @@
 //   psi: sqrt(2 (p_EOS - rho cs^2) / G), Sec. II A
 //   g: Eq. (7) (g^eq = c_v T f^eq) or Eq. (24) with C_i of Eq. (25)
 //
-// Storage: 18 structure-of-arrays planes (f_0..f_8, g_0..g_8), plane stride
-// `plane` elements, row pitch `pitch` elements.  The buffer holds the
+// Storage: structure-of-arrays planes (f_0..f_8, g_0..g_8; the 16-bit modes
+// add the low halves of f_0 and g_0, see Store), plane stride `plane`
+// elements, row pitch `pitch` elements.  The buffer holds the
 // post-collision populations of the previous step at their source site, so
 // the pre-collision value f_i(x, t) is read ("pulled") from x - e_i.
 #pragma once
@@ -33,17 +34,29 @@ __host__ __device__ constexpr double wd(int i) {
 }
 
 // ---------------------------------------------------------------- storage
+// Store<PREC>: element type, arithmetic type and encoding of one storage mode.
+// NPLANES planes per buffer.  FP64 / FP32: 18 planes, f_0..f_8 then g_0..g_8.
+// 16-bit deviation modes: the eight moving populations of f and of g are
+// stored as 16-bit deviations h = f - base (RN-even), while the rest
+// populations f_0 and g_0, which carry each site's mass and energy balance,
+// are kept as FP32 deviations split into two 16-bit halves: the high half in
+// plane 0 (f_0) / 9 (g_0), the low half in plane 18 (f_0) / 19 (g_0), so that
+// every plane row has the same element size and alignment.
 template <int PREC> struct Store;
 
 template <> struct Store<LB_PREC_FP64> {
     using elem = double;
     using real = double;
+    static constexpr int NPLANES = 18;
+    static constexpr bool SPLIT = false;
     static __device__ __forceinline__ real load(const elem* p, real) { return *p; }
     static __device__ __forceinline__ void put(elem* p, real v, real) { *p = v; }
 };
 template <> struct Store<LB_PREC_FP32> {
     using elem = float;
     using real = float;
+    static constexpr int NPLANES = 18;
+    static constexpr bool SPLIT = false;
     static __device__ __forceinline__ real load(const elem* p, real) { return *p; }
     static __device__ __forceinline__ void put(elem* p, real v, real) { *p = v; }
 };
@@ -51,23 +64,87 @@ template <> struct Store<LB_PREC_FP32> {
 template <> struct Store<LB_PREC_FP16_DEV> {
     using elem = __half;
     using real = float;
-    static __device__ __forceinline__ real load(const elem* p, real base) {
-        return base + __half2float(*p);
-    }
-    static __device__ __forceinline__ void put(elem* p, real v, real base) {
-        *p = __float2half_rn(v - base);
-    }
+    static constexpr int NPLANES = 20;
+    static constexpr bool SPLIT = true;
+    static __device__ __forceinline__ real dec(elem h) { return __half2float(h); }
+    static __device__ __forceinline__ elem enc(real d) { return __float2half_rn(d); }
+    static __device__ __forceinline__ unsigned short bits(elem h) { return __half_as_ushort(h); }
+    static __device__ __forceinline__ elem from_bits(unsigned short b) { return __ushort_as_half(b); }
+    static __device__ __forceinline__ real load(const elem* p, real base) { return base + dec(*p); }
+    static __device__ __forceinline__ void put(elem* p, real v, real base) { *p = enc(v - base); }
 };
 template <> struct Store<LB_PREC_BF16_DEV> {
     using elem = __nv_bfloat16;
     using real = float;
-    static __device__ __forceinline__ real load(const elem* p, real base) {
-        return base + __bfloat162float(*p);
-    }
-    static __device__ __forceinline__ void put(elem* p, real v, real base) {
-        *p = __float2bfloat16_rn(v - base);
-    }
+    static constexpr int NPLANES = 20;
+    static constexpr bool SPLIT = true;
+    static __device__ __forceinline__ real dec(elem h) { return __bfloat162float(h); }
+    static __device__ __forceinline__ elem enc(real d) { return __float2bfloat16_rn(d); }
+    static __device__ __forceinline__ unsigned short bits(elem h) { return __bfloat16_as_ushort(h); }
+    static __device__ __forceinline__ elem from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
+    static __device__ __forceinline__ real load(const elem* p, real base) { return base + dec(*p); }
+    static __device__ __forceinline__ void put(elem* p, real v, real base) { *p = enc(v - base); }
 };
+
+// Planes apart from the high half of a rest population (plane 0 or 9) to its
+// low half (plane 18 or 19) in the 16-bit modes.
+__host__ __device__ constexpr int rest_lo_offset(int p) { return p == 0 ? 18 : 10; }
+__host__ __device__ constexpr bool is_rest_plane(int p) { return p == 0 || p == 9; }
+
+// Deviation of a population: the 16-bit value, or for a rest population of
+// a 16-bit mode the FP32 value whose halves sit `lo_off` elements apart.
+template <class S>
+__device__ __forceinline__ typename S::real dev_of(const typename S::elem* p, int plane_idx, long long lo_off) {
+    if constexpr (S::SPLIT) {
+        if (is_rest_plane(plane_idx))
+            return __uint_as_float(((unsigned)S::bits(p[0]) << 16) | (unsigned)S::bits(p[lo_off]));
+        return S::dec(*p);
+    } else {
+        return *p;
+    }
+}
+
+// Population of plane plane_idx (0..17) at p; `stride` is the distance
+// between planes of the container (kp.plane in device memory, the row
+// segment width in a shared-memory stage).
+template <class S>
+__device__ __forceinline__ typename S::real load_pop(const typename S::elem* p, long long stride, int plane_idx,
+                                                     typename S::real base) {
+    if constexpr (S::SPLIT) {
+        if (is_rest_plane(plane_idx)) return base + dev_of<S>(p, plane_idx, rest_lo_offset(plane_idx) * stride);
+    }
+    return S::load(p, base);
+}
+
+// Same, also adding the stored deviation to H (16-bit modes: the exact
+// deviation sums of mass and energy that the collision closes on).
+template <class S>
+__device__ __forceinline__ typename S::real load_pop_acc(const typename S::elem* p, long long stride,
+                                                         int plane_idx, typename S::real base,
+                                                         typename S::real& H) {
+    if constexpr (S::SPLIT) {
+        const typename S::real d = dev_of<S>(p, plane_idx, rest_lo_offset(plane_idx) * stride);
+        H += d;
+        return base + d;
+    } else {
+        return S::load(p, base);
+    }
+}
+
+// Write one population value v (absolute) of plane plane_idx at p.
+template <class S>
+__device__ __forceinline__ void put_pop(typename S::elem* p, long long stride, int plane_idx,
+                                        typename S::real v, typename S::real base) {
+    if constexpr (S::SPLIT) {
+        if (is_rest_plane(plane_idx)) {
+            const unsigned b = __float_as_uint(v - base);
+            p[0] = S::from_bits((unsigned short)(b >> 16));
+            p[rest_lo_offset(plane_idx) * stride] = S::from_bits((unsigned short)(b & 0xffffu));
+            return;
+        }
+    }
+    S::put(p, v, base);
+}
 
 // ---------------------------------------------------------------- params
 // Kernel parameters, derived once on the host from lb_params.
@@ -146,6 +223,67 @@ __device__ __forceinline__ void put_ghost(typename S::elem* p, int x, const KPar
     if (x >= kp.nx - kp.ghost) S::put(p - kp.nx, v, base);
 }
 
+// put_pop at p and, in the strip layout, at the periodic ghost copies of column x.
+template <class S>
+__device__ __forceinline__ void put_pop_ghost(typename S::elem* p, long long stride, int plane_idx, int x,
+                                              const KParams& kp, typename S::real v, typename S::real base) {
+    put_pop<S>(p, stride, plane_idx, v, base);
+    if (x < kp.ghost) put_pop<S>(p + kp.nx, stride, plane_idx, v, base);
+    if (x >= kp.nx - kp.ghost) put_pop<S>(p - kp.nx, stride, plane_idx, v, base);
+}
+
+// The post-collision populations of one site into storage; d points at the
+// site in plane 0, `stride` is the plane stride, and with ghost_lo / ghost_hi
+// the values also go to the periodic ghost copies nx columns right / left.
+//   FP64, FP32: every value as computed (the FP32 collision has already
+//     closed mass and energy through f_0 and g_0).
+//   16-bit modes: the moving populations are rounded to their 16-bit
+//     deviations first; the rest populations then take the deviations that
+//     keep the site's stored deviation sums equal to the loaded ones, Hf and
+//     Hg: h_0 = H - sum_{i>=1} h_i, at FP32 precision.  The collision of
+//     Eq. (1) conserves mass and Eqs. (7)/(24) energy (the sums of f^eq, F_i,
+//     g^eq and C_i), so this is exact up to one FP32 rounding per site, where
+//     the rounding of each moving population on its own would change the
+//     stored mass coherently, step after step.
+template <class S, typename IT>
+__device__ __forceinline__ void store_site(typename S::elem* d, IT stride, const KParams& kp,
+                                           const typename S::real f[9], const typename S::real g[9],
+                                           typename S::real Hf, typename S::real Hg, bool ghost_lo,
+                                           bool ghost_hi) {
+    using real = typename S::real;
+    using elem = typename S::elem;
+    const int nx = kp.nx;
+    auto put_raw = [&](int plane_idx, elem v) {
+        elem* q = d + (IT)plane_idx * stride;
+        *q = v;
+        if (ghost_lo) q[nx] = v;
+        if (ghost_hi) q[-nx] = v;
+    };
+    if constexpr (S::SPLIT) {
+        real sf = (real)0, sg = (real)0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const elem qf = S::enc(f[i] - (real)kp.base_f[i]);
+            const elem qg = S::enc(g[i] - (real)kp.base_g[i]);
+            sf += S::dec(qf);
+            sg += S::dec(qg);
+            put_raw(i, qf);
+            put_raw(9 + i, qg);
+        }
+        const unsigned bf = __float_as_uint(Hf - sf), bg = __float_as_uint(Hg - sg);
+        put_raw(0, S::from_bits((unsigned short)(bf >> 16)));
+        put_raw(18, S::from_bits((unsigned short)(bf & 0xffffu)));
+        put_raw(9, S::from_bits((unsigned short)(bg >> 16)));
+        put_raw(19, S::from_bits((unsigned short)(bg & 0xffffu)));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            put_raw(i, (elem)f[i]);
+            put_raw(9 + i, (elem)g[i]);
+        }
+    }
+}
+
 // wrap a coordinate that may lie a few tiles outside [0, n)
 __device__ __forceinline__ int wrapc(int v, int n) {
     while (v < 0) v += n;
@@ -170,8 +308,9 @@ __device__ __forceinline__ void pull18(const typename S::elem* __restrict__ src,
         const long long off = (long long)y * kp.pitch + x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            f[i] = S::load(src + (long long)i * kp.plane + off, (typename S::real)kp.base_f[i]);
-            g[i] = S::load(src + (long long)(9 + i) * kp.plane + off, (typename S::real)kp.base_g[i]);
+            f[i] = load_pop<S>(src + (long long)i * kp.plane + off, kp.plane, i, (typename S::real)kp.base_f[i]);
+            g[i] = load_pop<S>(src + (long long)(9 + i) * kp.plane + off, kp.plane, 9 + i,
+                               (typename S::real)kp.base_g[i]);
         }
         return;
     }
@@ -185,8 +324,32 @@ __device__ __forceinline__ void pull18(const typename S::elem* __restrict__ src,
         const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
         const long long sr = ey(i) == 1 ? rm : (ey(i) == -1 ? rp : r0);
         const long long off = sr + sx;
-        f[i] = S::load(src + (long long)i * kp.plane + off, (typename S::real)kp.base_f[i]);
-        g[i] = S::load(src + (long long)(9 + i) * kp.plane + off, (typename S::real)kp.base_g[i]);
+        f[i] = load_pop<S>(src + (long long)i * kp.plane + off, kp.plane, i, (typename S::real)kp.base_f[i]);
+        g[i] = load_pop<S>(src + (long long)(9 + i) * kp.plane + off, kp.plane, 9 + i,
+                           (typename S::real)kp.base_g[i]);
+    }
+}
+
+// pull18 of a periodic site that also returns the sums of the stored
+// deviations (16-bit modes; zero otherwise), which store_site closes on.
+template <class S>
+__device__ __forceinline__ void pull18h(const typename S::elem* __restrict__ src, const KParams& kp, int x,
+                                        int y, typename S::real f[9], typename S::real g[9],
+                                        typename S::real& Hf, typename S::real& Hg) {
+    Hf = Hg = (typename S::real)0;
+    const int xm = x == 0 ? kp.nx - 1 : x - 1;
+    const int xp = x == kp.nx - 1 ? 0 : x + 1;
+    const long long r0 = (long long)y * kp.pitch;
+    const long long rm = (long long)(y == 0 ? kp.ny - 1 : y - 1) * kp.pitch;
+    const long long rp = (long long)(y == kp.ny - 1 ? 0 : y + 1) * kp.pitch;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
+        const long long sr = ey(i) == 1 ? rm : (ey(i) == -1 ? rp : r0);
+        const long long off = sr + sx;
+        f[i] = load_pop_acc<S>(src + (long long)i * kp.plane + off, kp.plane, i, (typename S::real)kp.base_f[i], Hf);
+        g[i] = load_pop_acc<S>(src + (long long)(9 + i) * kp.plane + off, kp.plane, 9 + i,
+                               (typename S::real)kp.base_g[i], Hg);
     }
 }
 
@@ -393,8 +556,8 @@ __global__ void __launch_bounds__(BX* BY)
 
     const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
     if (gx < kp.nx && gy < kp.ny) {
-        real f[9], g[9];
-        pull18<S>(src, kp, gx, gy, f, g);
+        real f[9], g[9], Hf, Hg;
+        pull18h<S>(src, kp, gx, gy, f, g, Hf, Hg);
         real rho = f[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) rho += f[i];
@@ -403,11 +566,7 @@ __global__ void __launch_bounds__(BX* BY)
                                        WX, Fx, Fy);
         collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
         const long long off = (long long)gy * kp.pitch + gx;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            S::put(dst + (long long)i * kp.plane + off, f[i], (real)kp.base_f[i]);
-            S::put(dst + (long long)(9 + i) * kp.plane + off, g[i], (real)kp.base_g[i]);
-        }
+        store_site<S>(dst + off, kp.plane, kp, f, g, Hf, Hg, false, false);
     } else {
         flags = 0;
     }
@@ -527,10 +686,8 @@ __global__ void k_init(typename Store<PREC>::elem* __restrict__ dst, const KPara
             const long long off = (long long)y * kp.pitch + x;
             typename S::elem* pf = dst + (long long)i * kp.plane + off;
             typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;
-            S::put(pf, (real)fe, (real)kp.base_f[i]);
-            S::put(pg, (real)ge, (real)kp.base_g[i]);
-            put_ghost<S>(pf, x, kp, (real)fe, (real)kp.base_f[i]);
-            put_ghost<S>(pg, x, kp, (real)ge, (real)kp.base_g[i]);
+            put_pop_ghost<S>(pf, kp.plane, i, x, kp, (real)fe, (real)kp.base_f[i]);
+            put_pop_ghost<S>(pg, kp.plane, 9 + i, x, kp, (real)ge, (real)kp.base_g[i]);
         }
     }
 }
@@ -573,10 +730,8 @@ __global__ void k_scatter(typename Store<PREC>::elem* __restrict__ dst, const KP
             typename S::elem* pf = dst + (long long)i * kp.plane + off;
             typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;
             const real vf = (real)in[(long long)i * n + s], vg = (real)in[(long long)(9 + i) * n + s];
-            S::put(pf, vf, (real)kp.base_f[i]);
-            S::put(pg, vg, (real)kp.base_g[i]);
-            put_ghost<S>(pf, sx, kp, vf, (real)kp.base_f[i]);
-            put_ghost<S>(pg, sx, kp, vg, (real)kp.base_g[i]);
+            put_pop_ghost<S>(pf, kp.plane, i, sx, kp, vf, (real)kp.base_f[i]);
+            put_pop_ghost<S>(pg, kp.plane, 9 + i, sx, kp, vg, (real)kp.base_g[i]);
         }
     }
 }

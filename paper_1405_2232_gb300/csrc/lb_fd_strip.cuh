@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             }
             int y = y_start - 2 + j;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(NP * (W + 2 * HALO) * ES));
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)NP * strip_copy_bytes<ES, HALO>(W));
             __syncwarp();
             if (lane < NP) {
                 const elem* row;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     row = reinterpret_cast<const elem*>(Tn) + (size_t)((uint32_t)y * pitch);
                 }
                 bulk_copy_g2s(stage + ((size_t)s * NP + lane) * SEGW, row + (x0 - HALO),
-                              (uint32_t)((W + 2 * HALO) * ES), &full[s]);
+                              strip_copy_bytes<ES, HALO>(W), &full[s]);
             }
             issued = j + 1;
         }

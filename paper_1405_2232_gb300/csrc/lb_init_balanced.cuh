@@ -73,10 +73,8 @@ __global__ void __launch_bounds__(256)
             const long long off = (long long)ys * kp.pitch + xs;
             typename S::elem* pf = dst + (long long)i * kp.plane + off;
             typename S::elem* pg = dst + (long long)(9 + i) * kp.plane + off;
-            S::put(pf, (real)fe, (real)kp.base_f[i]);
-            S::put(pg, (real)ge, (real)kp.base_g[i]);
-            put_ghost<S>(pf, xs, kp, (real)fe, (real)kp.base_f[i]);
-            put_ghost<S>(pg, xs, kp, (real)ge, (real)kp.base_g[i]);
+            put_pop_ghost<S>(pf, kp.plane, i, xs, kp, (real)fe, (real)kp.base_f[i]);
+            put_pop_ghost<S>(pg, kp.plane, 9 + i, xs, kp, (real)ge, (real)kp.base_g[i]);
         }
     }
     if (flags) atomicOr(kp.err, flags);

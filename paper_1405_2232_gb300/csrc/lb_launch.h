@@ -64,20 +64,26 @@ inline int moments_grid_blocks(int nx, int ny) {
 // (bx, 0) selects the strip-marching kernel of width bx.
 bool step_tile_supported(int bx, int by);
 
+// Planes of a population buffer: 18, plus the low halves of the two rest
+// populations in the 16-bit modes (see Store in lb_device.cuh).
+inline int pop_planes(int prec) { return (prec == LB_PREC_FP64 || prec == LB_PREC_FP32) ? 18 : 20; }
+
 // Column halo of the strip kernel (16 bytes of elements) and its eligibility:
-// nx a multiple of the halo, and 32-bit element offsets over the 18 planes.
+// a supported width and 32-bit element offsets over all planes (any nx: the
+// row copies are rounded up to whole 16-byte units).
 inline int strip_halo(int prec) { return prec == LB_PREC_FP64 ? 2 : (prec == LB_PREC_FP32 ? 4 : 8); }
 inline bool strip_eligible(int prec, int nx, long long plane, int bx) {
+    (void)nx;
     if (prec == LB_PREC_FP64 && bx != 128) return false;
     if (bx != 128 && bx != 256) return false;
-    return nx % strip_halo(prec) == 0 && 18LL * plane < (1LL << 32);
+    return (long long)pop_planes(prec) * plane < (1LL << 32);
 }
 
 // Smallest nx of a finite-difference strip context: the FD_GHOST ghost
 // columns on each side must be distinct columns of the row.
 constexpr int FD_STRIP_MIN_NX = 8;
 
-// Population buffer layout, in elements: 18 planes, rows padded to 128 bytes,
+// Population buffer layout, in elements: pop_planes planes, rows padded to 128 bytes,
 // planes to 256 bytes.  The strip layout also leaves 128 bytes on each side
 // of every row for the periodic ghost columns (STRIP_GHOST of them are kept,
 // FD_GHOST on finite-difference contexts; the rest is read as halo padding

@@ -48,7 +48,8 @@ cudaError_t step_tile(const StepLaunch& L) {
 // share an SM (228 KB of shared memory).
 template <int BX>
 constexpr int strip_stages() {
-    constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<LBGB_PREC>::HALO) * StripCfg<LBGB_PREC>::ES;
+    constexpr size_t stage = (size_t)Store<LBGB_PREC>::NPLANES * (BX + 2 * StripCfg<LBGB_PREC>::HALO) *
+                             StripCfg<LBGB_PREC>::ES;
     constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<LBGB_PREC>::real);
     constexpr size_t budget = 110 * 1024 - 32;
     constexpr size_t s = (budget - ring) / stage;

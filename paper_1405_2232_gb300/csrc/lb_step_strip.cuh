@@ -23,7 +23,7 @@
 // first and last strips fetch their halo with the same single copy as every
 // other strip.  (Fetching the far end of the row with two extra 16-byte
 // copies per plane row made the two edge strips the slowest CTAs of the
-// launch.)  The kernel needs nx to be a multiple of HALO (checked on the host).
+// launch.)  Any nx: each plane-row copy is rounded up to whole 16-byte units.
 //
 // A dedicated producer warp issues the copies; the column warps release a
 // stage through a second mbarrier when its last reader is done, so copy issue
@@ -79,15 +79,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+        "p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
 // Bounded wait: false once `limit` clock cycles have passed (the default is
-// about one second at GB300 clocks; a limit <= 0 means the default).
+// about one second at GB300 clocks; a limit <= 0 means the default).  With
+// the default the polls are try_wait, which may suspend the thread for a
+// hardware-chosen time before it returns; a shorter, caller-set limit polls
+// with the non-blocking test_wait, so that the limit alone decides.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   long long limit = WAIT_CYCLES_DEFAULT) {
+    if (limit > 0 && limit < WAIT_CYCLES_DEFAULT) {
+        const long long t0 = clock64();
+        while (!mbar_test_wait(bar, parity)) {
+            if (clock64() - t0 > limit) return false;
+        }
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
-    if (limit <= 0) limit = WAIT_CYCLES_DEFAULT;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > limit) return false;
+        if (clock64() - t0 > WAIT_CYCLES_DEFAULT) return false;
     }
     return true;
 }
@@ -133,10 +150,19 @@ struct StripCfg {
     static constexpr int HALO = 16 / ES;  // 16-byte halo: 2 (FP64), 4 (FP32), 8 (16-bit)
 };
 
+// Bytes of one plane-row copy of a strip W columns wide with its column halo,
+// rounded up to the 16 bytes a bulk copy moves at a time (for any nx: the
+// rounding reads at most HALO - 1 elements more, inside the row's right
+// padding, which is never used).
+template <int ES, int HALO>
+__host__ __device__ constexpr uint32_t strip_copy_bytes(int W) {
+    return ((uint32_t)((W + 2 * HALO) * ES) + 15u) & ~15u;
+}
+
 template <int PREC, int BX, int STAGES>
 constexpr size_t strip_smem_bytes() {
     using C = StripCfg<PREC>;
-    return (size_t)STAGES * 18 * (BX + 2 * C::HALO) * C::ES +
+    return (size_t)STAGES * Store<PREC>::NPLANES * (BX + 2 * C::HALO) * C::ES +
            (size_t)8 * (BX + 2) * sizeof(typename C::real) + (size_t)2 * STAGES * 8 + 16;
 }
 
@@ -161,7 +187,7 @@ __host__ __device__ constexpr int strip_threads() {
 // Block: BX column threads (BX/32 warps), one halo warp and one producer warp.
 //   producer: for every job (pre-collision row) waits until its stage is
 //     released, then lane 0 arms the stage's "full" mbarrier with the byte
-//     count and lanes 0..17 each issue the copy of one plane-row segment.
+//     count and lanes 0..NPLANES-1 each issue the copy of one plane-row segment.
 //   column threads: wait "full", compute psi of their column of the row into
 //     the psi ring, sync with the halo warp (named barrier), collide their
 //     column of the row behind, then each warp releases the stage of the row
@@ -183,10 +209,11 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     constexpr int RW = BX + 2;
     constexpr int ES = C::ES;
     constexpr int NCW = BX / 32;  // consumer warps
+    constexpr int NPL = S::NPLANES;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
-    real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * 18 * SEGW);  // [4][RW]
+    elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][NPL][SEGW]
+    real* ring_psi = reinterpret_cast<real*>(stage + (size_t)STAGES * NPL * SEGW);  // [4][RW]
     real* ring_psi2 = ring_psi + 4 * RW;                                            // [4][RW]
     uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
@@ -230,17 +257,18 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             }
             int y = y_start - 1 + j;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(18 * (W + 2 * HALO) * ES));
+            const uint32_t cb = strip_copy_bytes<ES, HALO>(W);
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)NPL * cb);
             __syncwarp();
-            if (lane < 18) {
+            if (lane < NPL) {
                 const int i = lane;
-                const int d = i < 9 ? i : i - 9;
+                // direction of the plane (planes 18, 19: low halves of the rest populations)
+                const int d = i < 9 ? i : (i < 18 ? i - 9 : 0);
                 int sy = y - ey(d);
                 sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
                 const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
                 // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
-                bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW, row + (x0 - HALO),
-                              (uint32_t)((W + 2 * HALO) * ES), &full[s]);
+                bulk_copy_g2s(stage + ((size_t)s * NPL + i) * SEGW, row + (x0 - HALO), cb, &full[s]);
             }
             issued = j + 1;
         }
@@ -263,7 +291,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort = 1;
         // 1. rho, T, psi of pre-collision row j at ring column r_psi
         if (has_psi) {
-            const elem* st = stage + (size_t)s * 18 * SEGW;
+            const elem* st = stage + (size_t)s * NPL * SEGW;
             real* rp = ring_psi + (j & 3) * RW;
             real* rq = ring_psi2 + (j & 3) * RW;
             {
@@ -272,8 +300,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 real f[9], g[9], rho, T, psi, psi2;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
-                    g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                    f[i] = load_pop<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i]);
+                    g[i] = load_pop<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i]);
                 }
                 site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
                 if (BMODE != BETA_ZERO) rp[r] = psi;
@@ -286,13 +314,13 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
         if (j >= 2 && t < W) {
             const int sp = (j - 1) % STAGES;
-            const elem* st = stage + (size_t)sp * 18 * SEGW;
+            const elem* st = stage + (size_t)sp * NPL * SEGW;
             const int c = t + HALO;
-            real f[9], g[9];
+            real f[9], g[9], Hf = (real)0, Hg = (real)0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = S::load(st + i * SEGW + c - ex(i), (real)kp.base_f[i]);
-                g[i] = S::load(st + (9 + i) * SEGW + c - ex(i), (real)kp.base_g[i]);
+                f[i] = load_pop_acc<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i], Hf);
+                g[i] = load_pop_acc<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i], Hg);
             }
             real rho = f[0];
 #pragma unroll
@@ -308,22 +336,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             y = y >= ny ? y - ny : y;
             const int xg = x0 + t;
             const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
-            const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                elem* pf = dst + ((uint32_t)i * plane + off);
-                elem* pg = dst + ((uint32_t)(9 + i) * plane + off);
-                S::put(pf, f[i], (real)kp.base_f[i]);
-                S::put(pg, g[i], (real)kp.base_g[i]);
-                if (ghost_lo) {
-                    S::put(pf + nx, f[i], (real)kp.base_f[i]);
-                    S::put(pg + nx, g[i], (real)kp.base_g[i]);
-                }
-                if (ghost_hi) {
-                    S::put(pf - nx, f[i], (real)kp.base_f[i]);
-                    S::put(pg - nx, g[i], (real)kp.base_g[i]);
-                }
-            }
+            store_site<S>(dst + off, plane, kp, f, g, Hf, Hg, xg < STRIP_GHOST, xg >= nx - STRIP_GHOST);
         }
         // 3. the stage of job j-1 has had its last reader (psi at j-1, collision at j)
         if (j >= 1) {

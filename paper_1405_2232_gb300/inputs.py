@@ -180,12 +180,12 @@ class Domain:
 
 
 def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_TC,
-                  fixed_L=None, L_multiple=4, densities="coexistence"):
+                  fixed_L=None, L_multiple=1, densities="coexistence"):
     """Parameter sweep of independent periodic square domains.
 
     Per domain d (stream index 16 d + k of the counter-based generator):
-    side L ~ U{L_min..L_max} rounded down to a multiple of L_multiple (4: a row
-    of FP32 populations is then a whole number of 16-byte units),
+    side L ~ U{L_min..L_max} (rounded down to a multiple of L_multiple; 1, the
+    default, keeps the drawn side),
     T/T_c ~ U[0.6, 0.95], G ~ U[-1.2, -0.8],
     tau_f ~ U[0.6, 1.2], tau_g fixed; droplet (radius U[L/8, L/4]) or slab
     (width U[L/4, L/2]) from a fair coin.  densities="coexistence" starts the

@@ -28,6 +28,10 @@ DOMAINS = [
     (260, 9, 1.0, -0.9, "cs", 0.85, "slab"),
     (132, 17, 0.9, -1.0, "vdw", 0.90, "droplet"),
     (516, 140, 1.0, -1.0, "cs", 0.85, "droplet"),
+    # sides that are not a multiple of the 16-byte row unit (rounded-up row copies)
+    (37, 21, 1.0, -1.0, "cs", 0.85, "droplet"),
+    (131, 19, 0.9, -1.0, "cs", 0.85, "slab"),
+    (257, 33, 1.1, -1.1, "cs", 0.80, "droplet"),
 ]
 VDW = dict(a=9.0 / 49.0, b=2.0 / 21.0, R=1.0)
 
@@ -152,13 +156,13 @@ def test_batch_failed_domain_is_retired(lb):
 
 
 def test_batch_init_validates_on_host(lb):
-    """Mismatched precision, unaligned nx and unsupported storage are rejected before
-    any device work (runs without a GPU)."""
+    """Mismatched precision, a too-small domain and unsupported storage are rejected
+    before any device work (runs without a GPU; any nx >= 3 is accepted)."""
     rho = np.ones((12, 16))
     dp = ctypes.POINTER(ctypes.c_double)
     for mutate, code in [
         (lambda p: setattr(p[1], "precision", lb.LB_PREC_FP64), lb.LB_ERR_ARG),
-        (lambda p: setattr(p[1], "nx", 18), lb.LB_ERR_ARG),
+        (lambda p: setattr(p[1], "nx", 2), lb.LB_ERR_ARG),
         (lambda p: [setattr(q, "precision", lb.LB_PREC_FP16_DEV) for q in p], lb.LB_ERR_UNSUPPORTED),
         (lambda p: setattr(p[1], "thermal", lb.LB_THERMAL_EQ7), lb.LB_ERR_ARG),
         (lambda p: setattr(p[0], "tau_f", 0.4), lb.LB_ERR_ARG),
