@@ -155,7 +155,23 @@ typedef struct lb_params {
     double g_grav;         /* cavity: gravity along -y, buoyancy (0, -rho g) added to F */
     double T_in, T_w, U_in; /* channel: inlet temperature and velocity, plate temperature */
     int32_t init_balanced; /* initial state: 0 at u = 0 in f^eq; 1 at rest under the force (lb_init) */
+    int32_t halo_rows;     /* 0: periodic lattice; LB_HALO_ROWS: one y-slab of a decomposed lattice */
 } lb_params;
+
+/* Ghost rows per side of a y-slab of a lattice decomposed across ranks.  One
+ * fused step at row y reads the post-collision populations of rows y - 2 ..
+ * y + 2 (the pull reaches one row, the psi of the force stencil one more), so
+ * a slab that owns rows [y0, y1) of the global lattice is a context of
+ * ny = (y1 - y0) + 2 LB_HALO_ROWS rows holding global rows
+ * [y0 - LB_HALO_ROWS, y1 + LB_HALO_ROWS) (periodic in the global lattice).
+ * Its steps update only the owned rows [LB_HALO_ROWS, ny - LB_HALO_ROWS);
+ * between steps the caller refreshes the ghost rows from the neighbouring
+ * slabs (lb_halo_pack / lb_halo_unpack), after which the owned rows evolve bit
+ * for bit as the same rows of the whole lattice.  Periodic in x; lattice
+ * Boltzmann treatments (Eq. 7, Eq. 24) only; lb_moments, lb_totals and
+ * lb_get_populations cover all ny rows, of which only the owned ones are
+ * meaningful. */
+enum { LB_HALO_ROWS = 2 };
 
 typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
 
@@ -163,7 +179,7 @@ typedef struct lb_ctx lb_ctx; /* opaque; owned by the library */
  * tau_f=1, tau_g=0.8, c_v=1, Eq. (24), FP32, psi from the local T,
  * rho0 = 0.12, T0 = 0.075, periodic (cavity fields T_hot = 1.03,
  * T_cold = 0.97, g_grav = 0; channel fields T_in = 1.03, T_w = 0.97,
- * U_in = 0.05, Case A), init_balanced = 0. */
+ * U_in = 0.05, Case A), init_balanced = 0, halo_rows = 0. */
 void lb_params_default(lb_params* p);
 
 /* Create a context whose initial state is f = f^eq(rho0, u = 0) and
@@ -238,6 +254,26 @@ lb_status lb_load_state(lb_ctx* ctx, const void* host_blob);
 
 /* Number of steps taken since lb_init (or the loaded state's time). */
 int64_t lb_time(const lb_ctx* ctx);
+
+/* Ghost-row exchange of a y-slab context (halo_rows == LB_HALO_ROWS).
+ * lb_halo_bytes: size of one face's exchange buffer: every population plane
+ * (18; 20 in the 16-bit modes) x LB_HALO_ROWS whole rows of the context's
+ * padded row pitch, in the storage type (ghost columns included).
+ * lb_halo_pack(face): copy the first (face 0) or last (face 1) LB_HALO_ROWS
+ * owned rows of the current state into the DEVICE buffer d_buf, dense
+ * [planes][LB_HALO_ROWS][pitch]; face 0 goes to the neighbour below (it
+ * becomes that slab's upper ghost rows), face 1 to the neighbour above.
+ * lb_halo_unpack(face): write such a buffer into the lower (face 0) or upper
+ * (face 1) ghost rows.  Both are asynchronous on the context's stream and
+ * allocate nothing; the buffers must not be touched by other streams until
+ * the copies are done.  The owned rows of a slab at time t are exact only if
+ * its ghost rows hold the neighbours' rows at time t: exchange after every
+ * step.  LB_ERR_ARG for a context without ghost rows, a NULL buffer or a face
+ * other than 0 or 1.  (Row decomposition of one lattice over GPUs; the paper
+ * has no counterpart.) */
+lb_status lb_halo_bytes(const lb_ctx* ctx, size_t* bytes);
+lb_status lb_halo_pack(lb_ctx* ctx, int32_t face, void* d_buf);
+lb_status lb_halo_unpack(lb_ctx* ctx, int32_t face, const void* d_buf);
 
 /* Failure detection (the paper has no counterpart).  The strip-marching step
  * kernels (lattice Boltzmann and finite-difference) hand rows from a copy

@@ -293,7 +293,7 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
             return err(LB_ERR_ARG, "domain %d: precision, thermal treatment and force form must match domain 0", d);
         if (p.nx < 3 || p.ny < 3)
             return err(LB_ERR_ARG, "domain %d: nx and ny must be >= 3", d);
-        if (p.walls != LB_WALLS_PERIODIC)
+        if (p.walls != LB_WALLS_PERIODIC || p.halo_rows != 0)
             return err(LB_ERR_UNSUPPORTED, "domain %d: the batched solver runs periodic domains", d);
         if (!(p.tau_f > 0.5) || !(p.tau_g > 0.5) || p.G == 0.0 || !(p.cv > 0.0) || p.eos < 0 || p.eos > 2 ||
             p.thermal < 0 || p.thermal > 1 || p.init_balanced < 0 || p.init_balanced > 1)

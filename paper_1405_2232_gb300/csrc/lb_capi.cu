@@ -71,6 +71,15 @@ lb_status validate(const lb_params* p) {
         return fail(LB_ERR_ARG, "init_balanced must be 0 or 1 (got %d)", p->init_balanced);
     if (p->init_balanced && (p->walls != LB_WALLS_PERIODIC || p->thermal >= LB_THERMAL_FD26))
         return fail(LB_ERR_UNSUPPORTED, "the start at rest under the force is for periodic lattice Boltzmann contexts");
+    if (p->halo_rows != 0 && p->halo_rows != LB_HALO_ROWS)
+        return fail(LB_ERR_ARG, "halo_rows must be 0 or %d (got %d)", LB_HALO_ROWS, p->halo_rows);
+    if (p->halo_rows) {
+        if (p->walls != LB_WALLS_PERIODIC || p->thermal >= LB_THERMAL_FD26)
+            return fail(LB_ERR_UNSUPPORTED, "ghost-row sub-lattices are periodic lattice Boltzmann contexts");
+        if (p->ny < 2 * p->halo_rows + 1)
+            return fail(LB_ERR_ARG, "a sub-lattice with %d ghost rows each side needs ny >= %d", p->halo_rows,
+                        2 * p->halo_rows + 1);
+    }
     if (p->walls == LB_WALLS_CHANNEL) {
         if (p->precision != LB_PREC_FP64 && p->precision != LB_PREC_FP32)
             return fail(LB_ERR_UNSUPPORTED, "the channel stores FP64 or FP32");
@@ -162,6 +171,7 @@ struct lb_ctx {
     int64_t ref_time = 0;
     int64_t t = 0;
     int nchunks = 1;            // strip kernel: row chunks per strip
+    long long pitch = 0, plane = 0;  // population layout (elements)
     // finite-difference temperature treatment (Eqs. 26-27)
     bool fd = false;
     void* Tf_alloc[2] = {nullptr, nullptr};  // T^n, T^{n+1}: one population plane each
@@ -213,6 +223,7 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
     }
     k.err = err;
     k.wait_cycles = WAIT_CYCLES_DEFAULT;
+    k.halo_rows = p.halo_rows;
     return k;
 }
 
@@ -463,6 +474,8 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
     }
     c->kp = make_kparams(c->p, pitch, plane, c->d_err);
     c->kp.ghost = strip ? (c->fd ? FD_GHOST : STRIP_GHOST) : 0;
+    c->pitch = pitch;
+    c->plane = plane;
     if (strip) {
         // one wave of two resident CTAs per SM: strips x chunks <= 2 x SMs
         // (chunks of at least 8 rows)
@@ -470,7 +483,8 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0)
             sms = 152;
         const int strips = (p->nx + c->p.tile_x - 1) / c->p.tile_x;
-        const int max_ch = p->ny / 8 > 0 ? p->ny / 8 : 1;
+        const int rows = p->ny - 2 * p->halo_rows;
+        const int max_ch = rows / 8 > 0 ? rows / 8 : 1;
         int nch = (2 * sms) / strips;
         nch = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
         c->nchunks = nch;
@@ -514,6 +528,7 @@ void lb_params_default(lb_params* p) {
     p->U_in = 0.05;
     p->adiabatic_bottom = 0;
     p->init_balanced = 0;
+    p->halo_rows = 0;
 }
 
 lb_status lb_init_device(const lb_params* p, const double* d_rho0, const double* d_T0,
@@ -717,6 +732,44 @@ lb_status lb_load_state(lb_ctx* c, const void* host_blob) {
 }
 
 int64_t lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+
+lb_status lb_halo_bytes(const lb_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(LB_ERR_ARG, "NULL argument");
+    if (!c->p.halo_rows) return fail(LB_ERR_ARG, "the context has no ghost rows (halo_rows == 0)");
+    *bytes = (size_t)pop_planes(c->p.precision) * c->p.halo_rows * c->pitch * elem_size(c->p.precision);
+    return LB_OK;
+}
+
+namespace {
+// Whole rows [r0, r0 + H) of every plane of the current buffer <-> a dense
+// [planes][H][pitch] device buffer (ghost columns included), one 2D copy.
+lb_status halo_copy(lb_ctx* c, int32_t face, void* d_buf, bool pack) {
+    if (!c || !d_buf) return fail(LB_ERR_ARG, "NULL argument");
+    if (!c->p.halo_rows) return fail(LB_ERR_ARG, "the context has no ghost rows (halo_rows == 0)");
+    if (face != 0 && face != 1) return fail(LB_ERR_ARG, "face must be 0 (lower) or 1 (upper)");
+    const int H = c->p.halo_rows, ny = c->p.ny;
+    // pack: the first (face 0) or last (face 1) H updated rows; unpack: the
+    // lower (face 0) or upper (face 1) ghost rows
+    const int r0 = pack ? (face == 0 ? H : ny - 2 * H) : (face == 0 ? 0 : ny - H);
+    const size_t es = elem_size(c->p.precision);
+    char* rows = static_cast<char*>(c->alloc[c->cur]) + (size_t)r0 * c->pitch * es;
+    const size_t width = (size_t)H * c->pitch * es, spitch = (size_t)c->plane * es;
+    const int planes = pop_planes(c->p.precision);
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaError_t e = pack ? cudaMemcpy2DAsync(d_buf, width, rows, spitch, width, planes, cudaMemcpyDeviceToDevice,
+                                             c->stream)
+                         : cudaMemcpy2DAsync(rows, spitch, d_buf, width, width, planes, cudaMemcpyDeviceToDevice,
+                                             c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, pack ? "lb_halo_pack" : "lb_halo_unpack");
+    return LB_OK;
+}
+}  // namespace
+
+lb_status lb_halo_pack(lb_ctx* c, int32_t face, void* d_buf) { return halo_copy(c, face, d_buf, true); }
+
+lb_status lb_halo_unpack(lb_ctx* c, int32_t face, const void* d_buf) {
+    return halo_copy(c, face, const_cast<void*>(d_buf), false);
+}
 
 lb_status lb_set_wait_limit(lb_ctx* c, int64_t cycles) {
     if (!c) return fail(LB_ERR_ARG, "ctx is NULL");

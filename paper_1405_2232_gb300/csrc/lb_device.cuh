@@ -173,6 +173,8 @@ struct KParams {
     float base_f[9], base_g[9];  // deviation bases of the 16-bit modes
     int* err;                    // sticky device error word (bit per lb_status)
     long long wait_cycles;       // limit of the strip kernels' pipeline waits (<= 0: default)
+    int halo_rows;               // 0: periodic in y; H > 0: rows [0, H) and [ny - H, ny) are ghost
+                                 // rows of a y-decomposed lattice, the step updates [H, ny - H)
 };
 
 // Default limit of a bounded device wait, in clock cycles (about one second
@@ -541,21 +543,26 @@ __global__ void __launch_bounds__(BX* BY)
     __shared__ real s_psi2[BMODE != BETA_ONE ? WX * WY : 1];
 
     const int tid = threadIdx.x + threadIdx.y * BX;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    // rows updated: [H, ny - H) (H = kp.halo_rows; 0 on a periodic lattice)
+    const int H = kp.halo_rows;
+    const int x0 = blockIdx.x * BX, y0 = H + blockIdx.y * BY;
     int flags = 0;
     for (int s = tid; s < WX * WY; s += NT) {
         const int ly = s / WX, lx = s - ly * WX;
         const int gx = wrapc(x0 + lx - 1, kp.nx), gy = wrapc(y0 + ly - 1, kp.ny);
         real f[9], g[9], rho, T, psi, psi2;
+        int fl = 0;
         pull18<S>(src, kp, gx, gy, f, g);
-        site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
+        site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, fl);
+        // ring rows beyond the updated range (ghost rows' own ring) do not report
+        if (y0 + ly - 1 <= kp.ny - H) flags |= fl;
         if (BMODE != BETA_ZERO) s_psi[s] = psi;
         if (BMODE != BETA_ONE) s_psi2[s] = psi2;
     }
     __syncthreads();
 
     const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-    if (gx < kp.nx && gy < kp.ny) {
+    if (gx < kp.nx && gy < kp.ny - H) {
         real f[9], g[9], Hf, Hg;
         pull18h<S>(src, kp, gx, gy, f, g, Hf, Hg);
         real rho = f[0];

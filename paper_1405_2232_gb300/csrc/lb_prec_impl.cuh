@@ -20,7 +20,7 @@ template <int BX, int BY>
 cudaError_t step_tile(const StepLaunch& L) {
     using E = typename Store<LBGB_PREC>::elem;
     const dim3 block(BX, BY);
-    const dim3 grid((L.kp.nx + BX - 1) / BX, (L.kp.ny + BY - 1) / BY);
+    const dim3 grid((L.kp.nx + BX - 1) / BX, (L.kp.ny - 2 * L.kp.halo_rows + BY - 1) / BY);
     const E* src = static_cast<const E*>(L.src);
     E* dst = static_cast<E*>(L.dst);
     if (L.eq24) {

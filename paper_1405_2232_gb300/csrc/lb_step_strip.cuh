@@ -224,8 +224,11 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     const int nx = kp.nx, ny = kp.ny;
     const int x0 = blockIdx.x * BX;
     const int W = min(BX, nx - x0);
-    const int y_start = (int)((long long)blockIdx.y * ny / nchunks);
-    const int y_end = (int)((long long)(blockIdx.y + 1) * ny / nchunks);
+    // rows updated: [H, ny - H) (H = kp.halo_rows: ghost rows of a y-decomposed
+    // lattice; 0 on a periodic lattice, whose rows wrap)
+    const int H = kp.halo_rows, nrows = ny - 2 * H;
+    const int y_start = H + (int)((long long)blockIdx.y * nrows / nchunks);
+    const int y_end = H + (int)((long long)(blockIdx.y + 1) * nrows / nchunks);
     const int njobs = (y_end - y_start) + 2;  // pre-collision rows y_start-1 .. y_end
     const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
 

@@ -29,6 +29,7 @@ LB_WALLS_PERIODIC, LB_WALLS_CAVITY, LB_WALLS_CHANNEL = 0, 1, 2
 LB_TOTALS_N = 5
 LB_TUNE_N = 5
 LB_BATCH_TUNE_N = 4
+LB_HALO_ROWS = 2
 
 PRECISIONS = {"fp64": LB_PREC_FP64, "fp32": LB_PREC_FP32, "fp16": LB_PREC_FP16_DEV,
               "bf16": LB_PREC_BF16_DEV}
@@ -59,6 +60,7 @@ class lb_params(ctypes.Structure):
         ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("g_grav", ctypes.c_double),
         ("T_in", ctypes.c_double), ("T_w", ctypes.c_double), ("U_in", ctypes.c_double),
         ("init_balanced", ctypes.c_int32),
+        ("halo_rows", ctypes.c_int32),
     ]
 
 
@@ -70,7 +72,7 @@ EXPORTED = [
     "lb_moments", "lb_moments_device", "lb_get_populations", "lb_set_populations",
     "lb_totals", "lb_state_size", "lb_save_state", "lb_load_state", "lb_time",
     "lb_get_params", "lb_free", "lb_last_error", "lb_version", "lb_field_totals_noalloc",
-    "lb_set_wait_limit",
+    "lb_set_wait_limit", "lb_halo_bytes", "lb_halo_pack", "lb_halo_unpack",
     "lb_batch_init", "lb_batch_step", "lb_batch_check", "lb_batch_run", "lb_batch_fields",
     "lb_batch_time", "lb_batch_free", "lb_tune_candidate", "lb_autotune",
     "lb_batch_set_chunk_rows", "lb_batch_chunk_rows", "lb_batch_autotune",
@@ -111,6 +113,9 @@ def load(path: str | None = None):
         "lb_load_state": (st, [vp, vp]),
         "lb_time": (ctypes.c_int64, [vp]),
         "lb_set_wait_limit": (st, [vp, ctypes.c_int64]),
+        "lb_halo_bytes": (st, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+        "lb_halo_pack": (st, [vp, ctypes.c_int32, vp]),
+        "lb_halo_unpack": (st, [vp, ctypes.c_int32, vp]),
         "lb_get_params": (st, [vp, P]),
         "lb_free": (st, [vp]),
         "lb_last_error": (ctypes.c_char_p, []),
@@ -274,6 +279,22 @@ def lb_time(ctx) -> int:
 def lb_set_wait_limit(ctx, cycles: int):
     """Limit (SM clock cycles, 0 = default) of the strip kernels' bounded waits."""
     _check(load().lb_set_wait_limit(ctx, int(cycles)))
+
+
+def lb_halo_bytes(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(load().lb_halo_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def lb_halo_pack(ctx, face: int, d_buf):
+    """Owned edge rows (face 0: first, 1: last) into the device buffer d_buf."""
+    _check(load().lb_halo_pack(ctx, int(face), _addr(d_buf)))
+
+
+def lb_halo_unpack(ctx, face: int, d_buf):
+    """Device buffer d_buf into the ghost rows (face 0: lower, 1: upper)."""
+    _check(load().lb_halo_unpack(ctx, int(face), _addr(d_buf)))
 
 
 def lb_free(ctx):

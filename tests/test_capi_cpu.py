@@ -144,3 +144,25 @@ def test_noalloc_binding_rejects_bad_tensors(lib):
         lb.lb_field_totals_noalloc(nx, ny, 1.0, ok(), ok(), ok(), ok(), out, d_ref_rho=ok(3),
                                    d_ref_T=ok(), K=1)
     assert "d_ref_rho" in str(ei.value)
+
+
+def test_halo_rows_validated_on_host(lib):
+    """Ghost-row (y-slab) contexts: only LB_HALO_ROWS ghost rows, periodic lattice
+    Boltzmann contexts only, enough rows; the exchange calls reject a NULL context
+    (all rejected before any device work)."""
+    lb, so = lib
+    import numpy as np
+    rho = np.full((12, 16), 0.2)
+    for kw, code in [(dict(halo_rows=3), lb.LB_ERR_ARG), (dict(halo_rows=2, ny=4), lb.LB_ERR_ARG),
+                     (dict(halo_rows=2, walls=lb.LB_WALLS_CAVITY), lb.LB_ERR_UNSUPPORTED),
+                     (dict(halo_rows=2, thermal=lb.LB_THERMAL_FD26), lb.LB_ERR_UNSUPPORTED)]:
+        p = lb.lb_params_default(nx=16, ny=kw.pop("ny", 12), **kw)
+        r = np.full((p.ny, p.nx), 0.2)
+        ctx = ctypes.c_void_p()
+        st = so.lb_init(ctypes.byref(p), lb._dptr(r), lb._dptr(r), None, ctypes.byref(ctx))
+        assert st == code and ctx.value is None, (kw, st)
+    n = ctypes.c_size_t()
+    assert so.lb_halo_bytes(None, ctypes.byref(n)) == lb.LB_ERR_ARG
+    assert so.lb_halo_pack(None, 0, None) == lb.LB_ERR_ARG
+    assert so.lb_halo_unpack(None, 1, None) == lb.LB_ERR_ARG
+    assert lb.lb_params_default().halo_rows == 0 and lb.LB_HALO_ROWS == 2

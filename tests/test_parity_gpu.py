@@ -418,9 +418,13 @@ def test_16bit_one_step_within_rounding_bound(lb, prec, u, shape, tile):
         bound = u * np.abs(ref - base) * 1.01 + sub + 2e-6 * np.abs(ref).max() + 1e-12
         assert np.all(np.abs(got[1:] - ref[1:]) <= bound[1:])
         # the rest population (an FP32 deviation) closes the site's mass or
-        # energy: it carries the other eight populations' errors with the
-        # opposite sign, plus its own FP32 step error
-        bound0 = bound[1:].sum(axis=0) + 2e-6 * np.abs(ref[0]).max()
+        # energy: it carries with the opposite sign the errors of the eight
+        # populations that left the site, which now sit at x + e_i, plus its
+        # own FP32 step error
+        ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+        ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+        bound0 = sum(np.roll(bound[i], (-ey[i], -ex[i]), (0, 1)) for i in range(1, 9))
+        bound0 = bound0 + 2e-6 * np.abs(ref[0]).max()
         assert np.all(np.abs(got[0] - ref[0]) <= bound0)
 
 
