@@ -2,7 +2,7 @@
 
 The FP32 path stores populations in FP32 and computes psi, the force and the
 collision in FP32.  After 1000 steps of the 64x64 slab the GPU meets 2e-5 on
-rho and T, but its velocity error is about 4e-5, so the parity test bounds u
+rho and T, but its velocity error is 4e-5 to 7e-5, so the parity test bounds u
 by 1e-4 instead.  This file shows, on the CPU and without the GPU path, that
 the 2e-5 target on u is below what FP32 arithmetic supports on this workload
 while FP32 storage alone stays within it:
@@ -150,8 +150,8 @@ def test_fp32_collision_alone_exceeds_2e5_on_u(slab):
 
 def test_fp32_throughout_within_parity_bounds(slab):
     """The bounds the GPU parity test applies to the FP32 path: rho and T within
-    2e-5, u within 1e-4 (the float32 model without fused multiply-adds is the
-    less accurate of the two: the GPU's own e_u is about half of it)."""
+    2e-5, u within 1e-4 (the float32 model has no fused multiply-adds; the
+    GPU's own e_u, 4e-5 to 7e-5, is of the same size)."""
     P, f, g, ref = slab
     e_rho, e_u, e_T = errors(P, f, g, ref, (F32, F32, F32, F32))
     print(f"FP32 throughout: e_rho={e_rho:.2e} e_u={e_u:.2e} e_T={e_T:.2e}")
