@@ -360,6 +360,20 @@ lb_status lb_batch_run(lb_batch* b, double tol, int64_t K, int64_t max_steps, in
  * active domain this runs a check (the new residual reference).  Synchronises. */
 lb_status lb_batch_fields(lb_batch* b, int32_t d, double* rho, double* T);
 
+/* Restart domain d from the float64 fields rho0, T0 [ny][nx] (host or device,
+ * copied on the batch's stream before the call returns): its state becomes the
+ * initial state of lb_batch_init (init_balanced 0: f^eq at u = 0; 1: at rest
+ * under the force), its error word and status are cleared and it is active
+ * again (taken back onto the work list if it had converged or failed).  Its
+ * step count keeps counting from where it was, so a later lb_batch_run's step
+ * cap bounds the domain's steps over both starts; its next residual compares
+ * with the fields it restarted from.  This is the fallback of a warm-started
+ * solve: a domain whose prediction does not relax restarts from the plain
+ * initial fields.  Synchronises.  LB_ERR_ARG for an invalid domain or NULL
+ * field. */
+lb_status lb_batch_restart(lb_batch* b, int32_t d, const double* rho0, const double* T0,
+                           int32_t init_balanced);
+
 /* Steps the batch has taken since lb_batch_init. */
 int64_t lb_batch_time(const lb_batch* b);
 

@@ -565,6 +565,42 @@ lb_status lb_batch_fields(lb_batch* b, int32_t d, double* rho, double* T) {
     return LB_OK;
 }
 
+lb_status lb_batch_restart(lb_batch* b, int32_t d, const double* rho0, const double* T0, int32_t init_balanced) {
+    if (!b || d < 0 || d >= b->n || !rho0 || !T0)
+        return err(LB_ERR_ARG, "lb_batch_restart: invalid domain or NULL field");
+    if (init_balanced != 0 && init_balanced != 1) return err(LB_ERR_ARG, "lb_batch_restart: init_balanced must be 0 or 1");
+    BCU(cudaSetDevice(b->device), "cudaSetDevice");
+    const BatchDomain& D = b->doms[d];
+    const size_t nb = sizeof(double) * (size_t)b->params[d].nx * b->params[d].ny;
+    double* r = b->d_ref_rho + D.fld_off;
+    double* tt = b->d_ref_T + D.fld_off;
+    // the fields are staged in the domain's residual reference (its next
+    // residual compares with them), then the state is built in the buffer the
+    // active domains currently hold
+    BCU(cudaMemcpyAsync(r, rho0, nb, cudaMemcpyDefault, b->stream), "restart fields");
+    BCU(cudaMemcpyAsync(tt, T0, nb, cudaMemcpyDefault, b->stream), "restart fields");
+    void* dst = b->prec == LB_PREC_FP32 ? static_cast<void*>(static_cast<float*>(b->buf[b->cur]) + D.off)
+                                       : static_cast<void*>(static_cast<double*>(b->buf[b->cur]) + D.off);
+    cudaError_t e;
+    if (init_balanced) {
+        e = launch_init_balanced(b->prec, dst, D.kp, r, tt, b->stream);
+    } else {
+        if (b->prec == LB_PREC_FP32)
+            k_init<LB_PREC_FP32><<<64, 256, 0, b->stream>>>(static_cast<float*>(dst), D.kp, r, tt);
+        else
+            k_init<LB_PREC_FP64><<<64, 256, 0, b->stream>>>(static_cast<double*>(dst), D.kp, r, tt);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuerr(e, "restart initial state");
+    BCU(cudaMemsetAsync(b->d_err + d, 0, sizeof(int), b->stream), "restart error word");
+    BCU(cudaStreamSynchronize(b->stream), "synchronize");
+    const bool was_frozen = b->frozen[d] >= 0;
+    b->frozen[d] = -1;
+    b->status[d] = LB_OK;
+    b->params[d].init_balanced = init_balanced;
+    return was_frozen ? rebuild_lists(b) : LB_OK;
+}
+
 int64_t lb_batch_time(const lb_batch* b) { return b ? b->t : -1; }
 
 lb_status lb_batch_set_chunk_rows(lb_batch* b, int32_t rows) {

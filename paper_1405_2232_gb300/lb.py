@@ -75,7 +75,7 @@ EXPORTED = [
     "lb_set_wait_limit", "lb_halo_bytes", "lb_halo_pack", "lb_halo_unpack",
     "lb_batch_init", "lb_batch_step", "lb_batch_check", "lb_batch_run", "lb_batch_fields",
     "lb_batch_time", "lb_batch_free", "lb_tune_candidate", "lb_autotune",
-    "lb_batch_set_chunk_rows", "lb_batch_chunk_rows", "lb_batch_autotune",
+    "lb_batch_set_chunk_rows", "lb_batch_chunk_rows", "lb_batch_autotune", "lb_batch_restart",
 ]
 
 
@@ -137,6 +137,7 @@ def load(path: str | None = None):
         "lb_batch_set_chunk_rows": (st, [vp, ctypes.c_int32]),
         "lb_batch_chunk_rows": (ctypes.c_int32, [vp]),
         "lb_batch_autotune": (st, [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), dp]),
+        "lb_batch_restart": (st, [vp, ctypes.c_int32, vp, vp, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -396,6 +397,17 @@ def lb_batch_run(b, n, tol, K=100, max_steps=10 ** 6):
     return steps, resid, stt
 
 
+def lb_batch_restart(b, d, rho, T, init_balanced=0, shape=None):
+    """Restart domain d from fields rho, T: host float64 arrays [ny, nx] (shape
+    checked when given), or device tensors / addresses."""
+    if isinstance(rho, np.ndarray):
+        rho, T = _host(rho, shape), _host(T, shape)
+        _check(load().lb_batch_restart(b, int(d), rho.ctypes.data_as(ctypes.c_void_p),
+                                       T.ctypes.data_as(ctypes.c_void_p), int(init_balanced)))
+    else:
+        _check(load().lb_batch_restart(b, int(d), _addr(rho), _addr(T), int(init_balanced)))
+
+
 def lb_batch_fields(b, d, nx, ny):
     rho = np.empty((ny, nx))
     T = np.empty((ny, nx))
@@ -465,6 +477,11 @@ class Batch:
     def fields(self, d):
         p = self.params[d]
         return lb_batch_fields(self.b, d, p.nx, p.ny)
+
+    def restart(self, d, rho, T, init_balanced=0):
+        """Restart domain d from the fields rho, T (see lb_batch_restart)."""
+        p = self.params[d]
+        lb_batch_restart(self.b, d, rho, T, init_balanced, shape=(p.ny, p.nx))
 
     @property
     def time(self):

@@ -175,3 +175,39 @@ def test_batch_init_validates_on_host(lb):
         b = ctypes.c_void_p()
         st = lb.load().lb_batch_init(arr, 2, ptrs, ptrs, None, ctypes.byref(b))
         assert st == code and b.value is None
+
+
+@pytest.mark.gpu
+def test_batch_restart_domain(lb):
+    """lb_batch_restart: a restarted domain evolves as a fresh start (FP64: bit for
+    bit, from host or device fields, either initial state), the others are
+    untouched, and a domain that had failed comes back onto the work list."""
+    import torch
+    setups = [domain_setup(s, O.THERMAL_EQ24) for s in DOMAINS[:3]]
+    params = [lb_params_from(lb, P, "fp64") for _, _, P, _ in setups]
+    with lb.Batch(params, [s[0] for s in setups], [s[1] for s in setups]) as B:
+        B.step(30)
+        B.restart(0, setups[0][0], setups[0][1], init_balanced=0)                # host fields
+        d_rho = torch.from_numpy(setups[2][0]).cuda()
+        d_T = torch.from_numpy(setups[2][1]).cuda()
+        torch.cuda.synchronize()
+        B.restart(2, d_rho, d_T, init_balanced=1)                                # device fields
+        B.step(25)
+        for d, n, bal in ((0, 25, 0), (1, 55, 0), (2, 25, 1)):
+            rho0, T0, P, _ = setups[d]
+            f, g = O.init_balanced(P, rho0, T0)[:2] if bal else O.init_equilibrium(P, rho0, T0)
+            f, g, _ = O.step(P, f, g, n=n, check=False)
+            m = O.moments(P, f, g)
+            rho, T = B.fields(d)
+            assert np.array_equal(rho, m[0]) and np.array_equal(T, m[3]), d
+    # a failed domain is reactivated by a restart
+    rho, T = I.slab_fields(64, 64)
+    pa = lb.lb_params_default(nx=64, ny=64, thermal=lb.LB_THERMAL_EQ7, precision="fp32")
+    with lb.Batch([pa], [rho], [T]) as B:
+        steps, _, st = B.run(1e-12, K=20, max_steps=400)
+        assert st[0] == lb.LB_ERR_PSI_DOMAIN
+        B.restart(0, rho, T)
+        steps2, _, st2 = B.run(1e-12, K=20, max_steps=20)
+        assert steps2[0] == steps[0] + 20 and st2[0] in (lb.LB_ERR_NOT_CONVERGED, lb.LB_ERR_PSI_DOMAIN)
+    with pytest.raises(lb.LbError):
+        lb.lb_batch_restart(None, 0, rho, T)
