@@ -25,6 +25,15 @@ work-list granularity, run to residual < 1e-8 with a step cap: batched MLUPS
 and the wall-clock time to steady state, with converged / failed / capped
 counts.
 
+``warm_start`` (after the timed region, rank 0): the second half of the
+metric, time to a steady-state residual of 1e-8, warm-started vs plain, on a
+reduced case that fits the benchmark's few minutes: the network is trained
+on 512 solves of 128 x 128 sweep cases (converged targets, 40 epochs) and 64
+unseen cases are solved plain (f^eq at u = 0), warm (the prediction at rest
+under the force) and warm with the plain solve as fallback after 2000 steps;
+wall seconds (inference included), converged / failed / capped counts and
+steps on the cases both arms converge.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs its own lattice: weak scaling, no
 data-path collective (independent problems).
@@ -302,6 +311,10 @@ def main():
     ap.add_argument("--thermal", default="eq24", choices=["eq24", "fd26"],
                     help="temperature treatment of the timed lattice: Eq. (24) (the headline) "
                          "or the finite-difference Eqs. (26)-(27) (profiling)")
+    ap.add_argument("--no-warm", action="store_true",
+                    help="skip the warm vs plain time-to-steady-state comparison")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"],
+                    help="storage of the timed lattice: FP32 (the headline) or another mode (profiling)")
     ap.add_argument("--sweep-domains", type=int, default=256,
                     help="domains of the batched sweep (profiling: a smaller case)")
     args = ap.parse_args()
@@ -325,7 +338,7 @@ def main():
     stream = torch.cuda.Stream()
     rho, T = I.spinodal_fields(NX, NY)
     fd = args.thermal == "fd26"
-    p = workload_params(lb, thermal=lb.LB_THERMAL_FD26 if fd else None)
+    p = workload_params(lb, precision=args.precision, thermal=lb.LB_THERMAL_FD26 if fd else None)
 
     # ---- device-resident timing
     d_rho = torch.from_numpy(rho).cuda()
@@ -346,7 +359,7 @@ def main():
     updates = sites * SEG * args.steps
     value = world * updates / t / 1e6
     launch_s = t / (SEG * args.steps)
-    alg_bytes = (BYTES_PER_SITE_FD if fd else BYTES_PER_SITE)["fp32"] * sites
+    alg_bytes = (BYTES_PER_SITE_FD if fd else BYTES_PER_SITE)[args.precision] * sites
     tot = lb.lb_totals(ctx)
     lb.lb_free(ctx)
     del d_rho, d_T
@@ -367,11 +380,17 @@ def main():
     if not args.no_sweep:
         sweep = run_sweep(lb, torch, dist, world, rank, args)
 
+    # ---- time to steady state, learned warm start vs plain (rank 0, reduced case)
+    warm = None
+    if not args.no_warm and rank == 0:
+        from paper_1405_2232_gb300 import warmstart as WS
+        warm = WS.compare()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    return report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep)
+    return report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep, warm)
 
 
 def run_sweep(lb, torch, dist, world, rank, args):
@@ -467,7 +486,7 @@ def run_variants(lb, torch, rho, T, stream, sites):
     return variants
 
 
-def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep=None):
+def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, sites, sweep=None, warm=None):
     peak, peak_kind = peaks()
     achieved = alg_bytes / launch_s / 1e9
     cpu = None
@@ -481,16 +500,17 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
                          f"spinodal recipe ({dt:.1f} s)"}
 
     fd = getattr(args, "thermal", "eq24") == "fd26"
-    traffic = None if fd else ncu_traffic()
+    prec = getattr(args, "precision", "fp32")
+    traffic = None if fd or prec != "fp32" else ncu_traffic()
     clocks = clk.summary()
     out = {
         "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"spinodal_{NX}x{NY}_CS_T0.75Tc_rho0.12pm0.01_{'fd26' if fd else 'eq24'}_fp32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": f"spinodal_{NX}x{NY}_CS_T0.75Tc_rho0.12pm0.01_{'fd26' if fd else 'eq24'}_{prec}",
                    "nx": NX, "ny": NY, "lb_steps_per_bench_step": SEG,
-                   "thermal": "Eqs.26-27" if fd else "Eq.24", "storage": "fp32", "tau_f": 1.0, "tau_g": 0.8,
+                   "thermal": "Eqs.26-27" if fd else "Eq.24", "storage": prec, "tau_f": 1.0, "tau_g": 0.8,
                    "G": -1.0,
                    "force": "Eq.4", "beta": BETA,
                    "l2": "state 2x1.23 GB > 129 MB L2, no flush needed",
@@ -510,6 +530,7 @@ def report(args, world, value, t, launch_s, alg_bytes, tot, e2e, variants, clk, 
         "totals_after": {"mass": tot[0], "energy": tot[1]},
         "variants": variants,
         "sweep": sweep,
+        "warm_start": warm,
     }
     print(json.dumps(out))
     if args.dist:

@@ -223,7 +223,7 @@ def batched_sweep(n_domains=256, L_min=64, L_max=512, seed=4, tau_g=0.8, Tc=CS_T
 #: output (deviations from the case's initial fields rho0, T0):
 #: rho = rho0 + rho_dev_scale y0, T = T0 (1 + t_dev_scale y1).
 UNET_NORM = dict(t_mid=0.775, t_scale=0.1, g_mid=-1.0, g_scale=0.2, rho_dev_scale=0.1,
-                 t_dev_scale=0.01)
+                 t_dev_scale=0.001)
 
 
 def normal01(seed: int, index: np.ndarray) -> np.ndarray:

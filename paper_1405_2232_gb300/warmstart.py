@@ -61,12 +61,11 @@ def solve(params, rhos, Ts, cap, device_inputs=False, chunk_rows=None):
     return steps, resid, st, time.perf_counter() - t0, B
 
 
-def generate(n, L=256, seed=5, cap=40000, chunk_rows=None, near_tol=1e-6):
+def generate(n, L=256, seed=5, cap=40000, chunk_rows=None, near_tol=0.0):
     """Steady states of n sweep cases: (domains, masks, index, rho, T, info).
 
-    The targets are the converged cases plus those stopped by the step cap
-    with a residual below near_tol (their geometry has settled; what is left
-    is the slow decay of sound waves in the periodic box)."""
+    The targets are the converged cases, plus (near_tol > 0) those stopped by
+    the step cap with a residual below near_tol."""
     doms, masks = I.warm_start_cases(n, L=L, seed=seed)
     params = sweep_params(doms)
     steps, resid, st, wall, B = solve(params, [d.rho for d in doms], [d.T for d in doms], cap,
@@ -154,15 +153,62 @@ def predict(net, X, batch):
     return out
 
 
-def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
+def handoff(net, doms, masks, batch, norm=None):
+    """Network prediction -> device fields (rho, T) of every case after the
+    handoff (un_warm_fields: mass and energy of the initial fields restored);
+    returns (d_rho, d_T, seconds), inference and handoff timed together."""
+    import torch
+    dev = torch.device("cuda")
+    L = doms[0].L
+    rho0 = torch.from_numpy(np.stack([d.rho for d in doms])).to(dev)
+    T0 = torch.from_numpy(np.stack([d.T for d in doms])).to(dev)
+    X = torch.from_numpy(case_inputs(doms, masks)).to(dev)
+    _sync()
+    t0 = time.perf_counter()
+    pred = predict(net, X, batch)
+    d_rho = torch.empty_like(rho0)
+    d_T = torch.empty_like(T0)
+    UN.warm_fields(len(doms), L, L, pred, I.UNET_NORM if norm is None else norm, rho0, T0, d_rho, d_T)
+    _sync()
+    return d_rho, d_T, time.perf_counter() - t0
+
+
+def solve_with_fallback(params_warm, warm_fields, params_plain, plain_fields, cap, probe, chunk_rows=None):
+    """Warm-started batched solve with the plain solve as fallback.
+
+    Every domain starts from its warm fields; after `probe` steps each domain
+    that has not converged (still relaxing, or failed) restarts from its plain
+    initial fields (lb_batch_restart) and runs on with the remaining budget,
+    so no domain takes more than `cap` steps over both starts.  warm_fields /
+    plain_fields: (rho list, T list) of device addresses or host arrays.
+    Returns steps, residual, status, wall seconds and the number of restarts."""
+    rw, tw = warm_fields
+    dev_in = not isinstance(rw[0], np.ndarray)
+    B = lb.Batch(params_warm, rw, tw, device_inputs=dev_in)
+    if chunk_rows:
+        B.chunk_rows = chunk_rows
+    t0 = time.perf_counter()
+    steps, resid, st = B.run(TOL, K=K, max_steps=probe)
+    restarts = 0
+    for d in np.flatnonzero(st != lb.LB_OK):
+        B.restart(int(d), plain_fields[0][d], plain_fields[1][d], init_balanced=params_plain[d].init_balanced)
+        restarts += 1
+    if restarts:
+        steps, resid, st = B.run(TOL, K=K, max_steps=max(0, cap - probe))
+    wall = time.perf_counter() - t0
+    B.close()
+    return steps, resid, st, wall, restarts
+
+
+def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None, probe=2000,
+             arms_wanted=("plain", "plain_balanced", "warm", "warm_T0", "warm_fallback")):
     """Plain solve from the initial fields (f^eq at u = 0) against warm solves
     from the network's prediction after the handoff (mass and energy restored),
     with the start at rest under the force.  Beside them: the plain fields
     started at rest (no network), the predicted density with the initial
-    temperature (t_dev_scale = 0 in the handoff), and the prediction started
-    at u = 0 in f^eq."""
-    import torch
-    dev = torch.device("cuda")
+    temperature (t_dev_scale = 0 in the handoff), and the warm start with the
+    plain solve as fallback (solve_with_fallback after `probe` steps).  The
+    warm arms' wall seconds include inference and handoff."""
     L = doms[0].L
     params = sweep_params(doms)
     params_bal = sweep_params(doms, init_balanced=1)
@@ -170,69 +216,72 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
     T0 = np.stack([d.T for d in doms])
     arms, per_case = {}, {}
 
-    def run(name, prm, rhos, Ts, device_inputs, start, extra_s=0.0):
-        steps, _, st, wall, B = solve(prm, rhos, Ts, cap, device_inputs=device_inputs, chunk_rows=chunk_rows)
-        B_fields = {int(d): B.fields(int(d)) for d in np.flatnonzero(st == lb.LB_OK)} if name == "plain" else None
-        B.close()
+    def record(name, steps, st, wall, extra_s, start, **kw):
         arms[name] = dict(wall_s=wall + extra_s, solve_s=wall, converged=int(np.sum(st == lb.LB_OK)),
                           failed=int(np.sum((st != lb.LB_OK) & (st != lb.LB_ERR_NOT_CONVERGED))),
-                          capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)), start=start)
+                          capped=int(np.sum(st == lb.LB_ERR_NOT_CONVERGED)), start=start, **kw)
         per_case[name] = (steps, st)
-        return B_fields
 
-    ref = run("plain", params, list(rho0), list(T0), False, "f^eq at u = 0")
-    run("plain_balanced", params_bal, list(rho0), list(T0), False, "at rest under the force")
-    # warm: inference + handoff + solve, all timed
-    X = torch.from_numpy(case_inputs(doms, masks)).to(dev)
-    d_rho0 = torch.from_numpy(rho0).to(dev)
-    d_T0 = torch.from_numpy(T0).to(dev)
+    def run(name, prm, rhos, Ts, device_inputs, start, extra_s=0.0, keep=False):
+        steps, _, st, wall, B = solve(prm, rhos, Ts, cap, device_inputs=device_inputs, chunk_rows=chunk_rows)
+        kept = {int(d): B.fields(int(d)) for d in np.flatnonzero(st == lb.LB_OK)} if keep else None
+        B.close()
+        record(name, steps, st, wall, extra_s, start)
+        return kept
+
+    ref = run("plain", params, list(rho0), list(T0), False, "f^eq at u = 0", keep=True)
+    if "plain_balanced" in arms_wanted:
+        run("plain_balanced", params_bal, list(rho0), list(T0), False, "at rest under the force")
     stride = L * L * 8
-    fields = {}
-    for tag, norm in (("", I.UNET_NORM), ("_T0", dict(I.UNET_NORM, t_dev_scale=0.0))):
-        _sync()
-        t0 = time.perf_counter()
-        pred = predict(net, X, batch)
-        d_rho = torch.empty_like(d_rho0)
-        d_T = torch.empty_like(d_T0)
-        UN.warm_fields(len(doms), L, L, pred, norm, d_rho0, d_T0, d_rho, d_T)
-        _sync()
-        t_inf = time.perf_counter() - t0
-        fields[tag] = (d_rho, d_T, t_inf)
-        rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
-        tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
-        run("warm" + tag, params_bal, rp, tp, True, "at rest under the force", t_inf)
-        if not tag:
-            run("warm_unbalanced", params, rp, tp, True, "f^eq at u = 0", t_inf)
-    for name in ("warm", "warm_T0", "warm_unbalanced"):
-        arms[name]["inference_s"] = fields["_T0" if name == "warm_T0" else ""][2]
+    d_rho, d_T, t_inf = handoff(net, doms, masks, batch)
+    rp = [d_rho.data_ptr() + i * stride for i in range(len(doms))]
+    tp = [d_T.data_ptr() + i * stride for i in range(len(doms))]
+    if "warm" in arms_wanted:
+        run("warm", params_bal, rp, tp, True, "at rest under the force", t_inf)
+        arms["warm"]["inference_s"] = t_inf
+    if "warm_fallback" in arms_wanted:
+        steps, _, st, wall, nr = solve_with_fallback(params_bal, (rp, tp), params, (list(rho0), list(T0)), cap,
+                                                     probe, chunk_rows=chunk_rows)
+        record("warm_fallback", steps, st, wall, t_inf, f"at rest under the force; plain restart after {probe} steps",
+               restarts=nr, inference_s=t_inf)
+    if "warm_T0" in arms_wanted:
+        d_rho0_, d_T0_, t_inf0 = handoff(net, doms, masks, batch, dict(I.UNET_NORM, t_dev_scale=0.0))
+        rp0 = [d_rho0_.data_ptr() + i * stride for i in range(len(doms))]
+        tp0 = [d_T0_.data_ptr() + i * stride for i in range(len(doms))]
+        run("warm_T0", params_bal, rp0, tp0, True, "at rest under the force", t_inf0)
+        arms["warm_T0"]["inference_s"] = t_inf0
     # prediction error against the plain steady state
-    h_rho, h_T = fields[""][0].cpu().numpy(), fields[""][1].cpu().numpy()
+    h_rho, h_T = d_rho.cpu().numpy(), d_T.cpu().numpy()
     e_rho = [np.abs(h_rho[d] - ref[d][0]).max() / np.abs(ref[d][0]).max() for d in ref]
     e_T = [np.abs(h_T[d] - ref[d][1]).max() / np.abs(ref[d][1]).max() for d in ref]
     e_T0 = [np.abs(T0[d] - ref[d][1]).max() / np.abs(ref[d][1]).max() for d in ref]
     rms_rho = [float(np.sqrt(np.mean((h_rho[d] - ref[d][0]) ** 2))) for d in ref]
-    med_rho = [float(np.median(np.abs(h_rho[d] - ref[d][0]))) for d in ref]
     rms_rho0 = [float(np.sqrt(np.mean((rho0[d] - ref[d][0]) ** 2))) for d in ref]
-    st_p, st_w = per_case["plain"][1], per_case["warm"][1]
-    steps_p, steps_w = per_case["plain"][0], per_case["warm"][0]
-    both = np.flatnonzero((st_p == lb.LB_OK) & (st_w == lb.LB_OK))
+    rms_T = [float(np.sqrt(np.mean((h_T[d] - ref[d][1]) ** 2)) / ref[d][1].mean()) for d in ref]
+    rms_T0 = [float(np.sqrt(np.mean((T0[d] - ref[d][1]) ** 2)) / ref[d][1].mean()) for d in ref]
+    st_p, steps_p = per_case["plain"][1], per_case["plain"][0]
     allc = np.flatnonzero(np.all([v[1] == lb.LB_OK for v in per_case.values()], axis=0))
+    vs_plain = {}
+    for k, (steps_k, st_k) in per_case.items():
+        if k == "plain":
+            continue
+        both = np.flatnonzero((st_p == lb.LB_OK) & (st_k == lb.LB_OK))
+        vs_plain[k] = dict(both_converged=int(both.size),
+                           median_steps_plain=float(np.median(steps_p[both])) if both.size else None,
+                           median_steps=float(np.median(steps_k[both])) if both.size else None,
+                           steps_ratio=float(np.sum(steps_k[both]) / np.sum(steps_p[both])) if both.size else None,
+                           total_steps_ratio=float(np.sum(steps_k) / np.sum(steps_p)))
+    med = lambda v: float(np.median(v)) if v else None
     out = dict(
-        cases=len(doms), L=L, cap=cap, **arms,
+        cases=len(doms), L=L, cap=cap, probe=probe, **arms,
         all_arms_converged=int(allc.size),
         median_steps_all_arms={k: (float(np.median(v[0][allc])) if allc.size else None)
                                for k, v in per_case.items()},
-        both_converged=int(both.size),
-        median_steps_plain=float(np.median(steps_p[both])) if both.size else None,
-        median_steps_warm=float(np.median(steps_w[both])) if both.size else None,
-        steps_ratio=float(np.sum(steps_w[both]) / np.sum(steps_p[both])) if both.size else None,
-        prediction_error=dict(e_rho_median=float(np.median(e_rho)) if e_rho else None,
-                              e_T_median=float(np.median(e_T)) if e_T else None,
-                              e_T_initial_state_median=float(np.median(e_T0)) if e_T0 else None,
-                              e_rho_max=float(np.max(e_rho)) if e_rho else None,
-                              rms_rho_median=float(np.median(rms_rho)) if rms_rho else None,
-                              abs_rho_median_of_medians=float(np.median(med_rho)) if med_rho else None,
-                              rms_rho_initial_state_median=float(np.median(rms_rho0)) if rms_rho0 else None),
+        vs_plain=vs_plain,
+        prediction_error=dict(e_rho_median=med(e_rho), e_T_median=med(e_T), e_T_initial_state_median=med(e_T0),
+                              e_rho_max=float(np.max(e_rho)) if e_rho else None, rms_rho_median=med(rms_rho),
+                              rms_rho_initial_state_median=med(rms_rho0), rms_T_rel_median=med(rms_T),
+                              rms_T_initial_state_rel_median=med(rms_T0)),
     )
     pc = dict(T_over_Tc=[d.T_over_Tc for d in doms], tau_f=[d.tau_f for d in doms],
               kind=[d.kind for d in doms], e_rho={int(d): float(e) for d, e in zip(ref, e_rho)})
@@ -241,6 +290,30 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None):
         pc["status_" + k] = st.tolist()
     out["per_case"] = pc
     return out
+
+
+def compare(L=128, n_train=512, n_test=64, train_cap=20000, test_cap=40000, epochs=40, batch=16, probe=2000):
+    """Warm vs plain on a reduced case (for the benchmark): train a network on
+    n_train solves at L x L, then solve n_test unseen cases plain, warm, and
+    warm with the plain fallback.  Returns the evaluation summary (no per-case
+    lists) with the training figures."""
+    import torch
+    dev = torch.device("cuda")
+    t0 = time.perf_counter()
+    doms, masks, ok, rho, T, gen = generate(n_train, L=L, seed=5, cap=train_cap, near_tol=0.0)
+    X = torch.from_numpy(case_inputs([doms[i] for i in ok], masks[ok])).to(dev)
+    Y = torch.from_numpy(I.unet_target_planes(rho, T, np.stack([doms[i].rho for i in ok]),
+                                              [doms[i].T_over_Tc * I.CS_TC for i in ok])).to(dev)
+    net, losses, t_train = train(X, Y, L, epochs=epochs, batch=batch)
+    tdoms, tmasks = I.warm_start_cases(n_test, L=L, seed=6)
+    ev = evaluate(net, tdoms, tmasks, test_cap, batch=batch, probe=probe,
+                  arms_wanted=("plain", "warm", "warm_fallback"))
+    net.close()
+    ev.pop("per_case")
+    ev["train"] = dict(cases=n_train, targets=int(ok.size), epochs=epochs, seconds=round(t_train, 2),
+                       train_cap=train_cap)
+    ev["seconds_total"] = round(time.perf_counter() - t0, 1)
+    return ev
 
 
 def train_step_bench(L=256, batch=16, steps=10, warmup=3):
