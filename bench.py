@@ -28,8 +28,8 @@ counts.
 ``warm_start`` (after the timed region, rank 0): the second half of the
 metric, time to a steady-state residual of 1e-8, warm-started vs plain, on a
 reduced case that fits the benchmark's few minutes: the network is trained
-on 512 solves of 128 x 128 sweep cases (converged targets, 40 epochs) and 64
-unseen cases are solved plain (f^eq at u = 0), warm (the prediction at rest
+on the converged ones of 1024 solves of 128 x 128 sweep cases (60 epochs) and
+128 unseen cases are solved plain (f^eq at u = 0), warm (the prediction at rest
 under the force) and warm with the plain solve as fallback after 2000 steps;
 wall seconds (inference included), converged / failed / capped counts and
 steps on the cases both arms converge.

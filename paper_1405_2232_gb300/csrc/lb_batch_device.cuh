@@ -190,22 +190,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 const int y = item.y0 + j - 2;
                 const int xg = x0 + t;
                 const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
-                const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    elem* pf = dst + ((uint32_t)i * plane + off);
-                    elem* pg = dst + ((uint32_t)(9 + i) * plane + off);
-                    S::put(pf, f[i], (real)kp.base_f[i]);
-                    S::put(pg, g[i], (real)kp.base_g[i]);
-                    if (ghost_lo) {
-                        S::put(pf + nx, f[i], (real)kp.base_f[i]);
-                        S::put(pg + nx, g[i], (real)kp.base_g[i]);
-                    }
-                    if (ghost_hi) {
-                        S::put(pf - nx, f[i], (real)kp.base_f[i]);
-                        S::put(pg - nx, g[i], (real)kp.base_g[i]);
-                    }
-                }
+                store_site<S>(dst + off, plane, kp, f, g, (real)0, (real)0, xg < STRIP_GHOST,
+                              xg >= nx - STRIP_GHOST);
             }
             // the job before this one has had its last reader in this warp
             if (j >= 1) {

@@ -221,6 +221,26 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
         k.base_f[i] = dev ? (float)(wd(i) * p.rho0) : 0.0f;
         k.base_g[i] = dev ? (float)(wd(i) * p.rho0 * p.cv * p.T0) : 0.0f;
     }
+    if (dev) {
+        // constants of the deviation-variable collision (collide_dev): sums of
+        // the stored bases (exact in double), their offsets from rho0 and
+        // rho0 c_v T0, and the rounding of each base
+        const double e0 = p.rho0 * p.cv * p.T0;
+        double sf = 0.0, sg = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            sf += (double)k.base_f[i];
+            sg += (double)k.base_g[i];
+        }
+        k.sum_bf = (float)sf;
+        k.sum_bg = (float)sg;
+        k.dsum_f = (float)(sf - p.rho0);
+        k.dsum_g = (float)(sg - e0);
+        const int rep[3] = {0, 1, 5};  // rest, axis, diagonal
+        for (int q = 0; q < 3; ++q) {
+            k.cw_f[q] = (float)(wd(rep[q]) * p.rho0 - (double)k.base_f[rep[q]]);
+            k.cw_g[q] = (float)(wd(rep[q]) * e0 - (double)k.base_g[rep[q]]);
+        }
+    }
     k.err = err;
     k.wait_cycles = WAIT_CYCLES_DEFAULT;
     k.halo_rows = p.halo_rows;

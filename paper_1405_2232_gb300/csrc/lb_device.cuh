@@ -175,6 +175,10 @@ struct KParams {
     long long wait_cycles;       // limit of the strip kernels' pipeline waits (<= 0: default)
     int halo_rows;               // 0: periodic in y; H > 0: rows [0, H) and [ny - H, ny) are ghost
                                  // rows of a y-decomposed lattice, the step updates [H, ny - H)
+    // 16-bit modes, collision in deviation variables (collide_dev):
+    float sum_bf, sum_bg;        // sum_i base_f[i], sum_i base_g[i]
+    float dsum_f, dsum_g;        // sum_i base_f[i] - rho0, sum_i base_g[i] - rho0 c_v T0
+    float cw_f[3], cw_g[3];      // w rho0 - base_f, w rho0 c_v T0 - base_g (rest, axis, diagonal)
 };
 
 // Default limit of a bounded device wait, in clock cycles (about one second
@@ -234,6 +238,33 @@ __device__ __forceinline__ void put_pop_ghost(typename S::elem* p, long long str
     if (x >= kp.nx - kp.ghost) put_pop<S>(p - kp.nx, stride, plane_idx, v, base);
 }
 
+// Store one value per plane at d (plane stride `stride`) and, for the few
+// threads whose column has a periodic ghost copy, once more nx columns right
+// (ghost_lo) or left (ghost_hi): one branch per site, not one per plane.
+template <class S, typename IT>
+__device__ __forceinline__ void put_planes(typename S::elem* d, IT stride, int nx, const typename S::elem* v,
+                                           bool ghost_lo, bool ghost_hi) {
+    // (the plane offset is formed in IT, the signed column shift by pointer
+    // arithmetic: an unsigned IT must never absorb a negative shift)
+#pragma unroll
+    for (int p = 0; p < S::NPLANES; ++p) d[(IT)p * stride] = v[p];
+    if (ghost_lo || ghost_hi) {
+        const int sh = ghost_lo ? nx : -nx;
+#pragma unroll
+        for (int p = 0; p < S::NPLANES; ++p) {
+            typename S::elem* q = d + (IT)p * stride;
+            q[sh] = v[p];
+        }
+        if (ghost_lo && ghost_hi) {  // lattices narrower than twice the ghost width
+#pragma unroll
+            for (int p = 0; p < S::NPLANES; ++p) {
+                typename S::elem* q = d + (IT)p * stride;
+                q[-nx] = v[p];
+            }
+        }
+    }
+}
+
 // The post-collision populations of one site into storage; d points at the
 // site in plane 0, `stride` is the plane stride, and with ghost_lo / ghost_hi
 // the values also go to the periodic ghost copies nx columns right / left.
@@ -254,36 +285,29 @@ __device__ __forceinline__ void store_site(typename S::elem* d, IT stride, const
                                            bool ghost_hi) {
     using real = typename S::real;
     using elem = typename S::elem;
-    const int nx = kp.nx;
-    auto put_raw = [&](int plane_idx, elem v) {
-        elem* q = d + (IT)plane_idx * stride;
-        *q = v;
-        if (ghost_lo) q[nx] = v;
-        if (ghost_hi) q[-nx] = v;
-    };
+    elem v[S::NPLANES];
     if constexpr (S::SPLIT) {
         real sf = (real)0, sg = (real)0;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const elem qf = S::enc(f[i] - (real)kp.base_f[i]);
-            const elem qg = S::enc(g[i] - (real)kp.base_g[i]);
-            sf += S::dec(qf);
-            sg += S::dec(qg);
-            put_raw(i, qf);
-            put_raw(9 + i, qg);
+            v[i] = S::enc(f[i] - (real)kp.base_f[i]);
+            v[9 + i] = S::enc(g[i] - (real)kp.base_g[i]);
+            sf += S::dec(v[i]);
+            sg += S::dec(v[9 + i]);
         }
         const unsigned bf = __float_as_uint(Hf - sf), bg = __float_as_uint(Hg - sg);
-        put_raw(0, S::from_bits((unsigned short)(bf >> 16)));
-        put_raw(18, S::from_bits((unsigned short)(bf & 0xffffu)));
-        put_raw(9, S::from_bits((unsigned short)(bg >> 16)));
-        put_raw(19, S::from_bits((unsigned short)(bg & 0xffffu)));
+        v[0] = S::from_bits((unsigned short)(bf >> 16));
+        v[18] = S::from_bits((unsigned short)(bf & 0xffffu));
+        v[9] = S::from_bits((unsigned short)(bg >> 16));
+        v[19] = S::from_bits((unsigned short)(bg & 0xffffu));
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            put_raw(i, (elem)f[i]);
-            put_raw(9 + i, (elem)g[i]);
+            v[i] = (elem)f[i];
+            v[9 + i] = (elem)g[i];
         }
     }
+    put_planes<S>(d, stride, kp.nx, v, ghost_lo, ghost_hi);
 }
 
 // wrap a coordinate that may lie a few tiles outside [0, n)
@@ -352,6 +376,29 @@ __device__ __forceinline__ void pull18h(const typename S::elem* __restrict__ src
         f[i] = load_pop_acc<S>(src + (long long)i * kp.plane + off, kp.plane, i, (typename S::real)kp.base_f[i], Hf);
         g[i] = load_pop_acc<S>(src + (long long)(9 + i) * kp.plane + off, kp.plane, 9 + i,
                                (typename S::real)kp.base_g[i], Hg);
+    }
+}
+
+// The stored deviations of the 18 pre-collision populations of a periodic
+// site (16-bit modes) and their sums Hf, Hg.
+template <class S>
+__device__ __forceinline__ void pull18_dev(const typename S::elem* __restrict__ src, const KParams& kp, int x,
+                                           int y, float h[9], float q[9], float& Hf, float& Hg) {
+    Hf = Hg = 0.0f;
+    const int xm = x == 0 ? kp.nx - 1 : x - 1;
+    const int xp = x == kp.nx - 1 ? 0 : x + 1;
+    const long long r0 = (long long)y * kp.pitch;
+    const long long rm = (long long)(y == 0 ? kp.ny - 1 : y - 1) * kp.pitch;
+    const long long rp = (long long)(y == kp.ny - 1 ? 0 : y + 1) * kp.pitch;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int sx = ex(i) == 1 ? xm : (ex(i) == -1 ? xp : x);
+        const long long sr = ey(i) == 1 ? rm : (ey(i) == -1 ? rp : r0);
+        const long long off = sr + sx;
+        h[i] = dev_of<S>(src + (long long)i * kp.plane + off, i, rest_lo_offset(i) * kp.plane);
+        q[i] = dev_of<S>(src + (long long)(9 + i) * kp.plane + off, 9 + i, rest_lo_offset(9 + i) * kp.plane);
+        Hf += h[i];
+        Hg += q[i];
     }
 }
 
@@ -527,6 +574,89 @@ __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9],
     }
 }
 
+// 16-bit modes: the collision of Eq. (1) with F_i and of Eq. (7) / (24) in the
+// deviation variables the storage holds, h_i = f_i - base_f[i] and
+// q_i = g_i - base_g[i] (base = w_i rho0 and w_i rho0 c_v T0), for the moving
+// populations i = 1..8 (the rest populations follow from the closure in
+// store_site_dev).  Hf, Hg: the sums of all nine loaded deviations, so that
+// rho = sum base_f + Hf and the energy density rho c_v T = sum base_g + Hg.
+// The same formulas as collide(): with f^eq_i = w_i rho (1 + 3 e.u + 4.5 (e.u)^2
+// - 1.5 u^2) and c_v T rho = e,
+//   f^eq_i - base_i = w_i (rho - rho0) + (w_i rho0 - base_i) + w_i rho (4.5 (e.u)^2 - 1.5 u^2) + 3 w_i rho e.u
+//   c_v T f^eq_i - base_g,i = w_i (e - e0) + (w_i e0 - base_g,i) + w_i e (4.5 (e.u)^2 - 1.5 u^2) + 3 w_i e e.u
+// so no base is added to or subtracted from a population (fewer operations,
+// and the small deviations keep their own FP32 precision).
+template <bool EQ24>
+__device__ __forceinline__ void collide_dev(const KParams& kp, float h[9], float q[9], float Hf, float Hg,
+                                            float Fx, float Fy) {
+    const float rho = kp.sum_bf + Hf, e = kp.sum_bg + Hg;
+    const float drho = kp.dsum_f + Hf, de = kp.dsum_g + Hg;
+    const float mx = (h[1] - h[3]) + ((h[5] - h[7]) + (h[8] - h[6]));
+    const float my = (h[2] - h[4]) + ((h[5] - h[7]) + (h[6] - h[8]));
+    const float inv_rho = 1.0f / rho;
+    const float ux = (mx + 0.5f * Fx) * inv_rho;
+    const float uy = (my + 0.5f * Fy) * inv_rho;
+    const float cvT = e * inv_rho;
+    const float om_f = (float)kp.omega_f, om_g = (float)kp.omega_g;
+    const float guo = (float)kp.guo_pre, corr = (float)kp.corr_pre;
+    const float m15u2 = -1.5f * (ux * ux + uy * uy);
+    const float uF3 = 3.0f * (ux * Fx + uy * Fy);
+    const float Aa = (float)(1.0 / 9.0) * drho + kp.cw_f[1], Ad = (float)(1.0 / 36.0) * drho + kp.cw_f[2];
+    const float Ba = (float)(1.0 / 9.0) * de + kp.cw_g[1], Bd = (float)(1.0 / 36.0) * de + kp.cw_g[2];
+    // pairs of opposite directions (1,3), (2,4), (5,7), (8,6) share the even parts
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
+        const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
+        const float w = (float)wd(i);
+        const float A = p < 2 ? Aa : Ad, B = p < 2 ? Ba : Bd;
+        const float eu = (float)ex(i) * ux + (float)ey(i) * uy;
+        const float eF = (float)ex(i) * Fx + (float)ey(i) * Fy;
+        const float sq = 4.5f * eu * eu + m15u2;
+        const float rw = rho * w, ew = e * w;
+        const float fe = A + rw * sq, fo = 3.0f * rw * eu;
+        const float ge = B + ew * sq, go = 3.0f * ew * eu;
+        const float Fe = guo * w * (9.0f * eu * eF - uF3), Fo = 3.0f * guo * w * eF;
+        h[i] = h[i] + om_f * ((fe + fo) - h[i]) + (Fe + Fo);
+        h[k] = h[k] + om_f * ((fe - fo) - h[k]) + (Fe - Fo);
+        float gi = q[i] + om_g * ((ge + go) - q[i]);
+        float gk = q[k] + om_g * ((ge - go) - q[k]);
+        if (EQ24) {
+            const float C = 3.0f * corr * w * cvT * eF;
+            gi += C;
+            gk -= C;
+        }
+        q[i] = gi;
+        q[k] = gk;
+    }
+}
+
+// store_site for deviations already computed by collide_dev (16-bit modes):
+// the moving populations are rounded to 16 bits, the rest populations close
+// the stored deviation sums (see store_site).
+template <class S, typename IT>
+__device__ __forceinline__ void store_site_dev(typename S::elem* d, IT stride, const KParams& kp,
+                                               const float h[9], const float q[9], float Hf, float Hg,
+                                               bool ghost_lo, bool ghost_hi) {
+    static_assert(S::SPLIT, "deviation storage only");
+    using elem = typename S::elem;
+    elem v[S::NPLANES];
+    float sf = 0.0f, sg = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        v[i] = S::enc(h[i]);
+        v[9 + i] = S::enc(q[i]);
+        sf += S::dec(v[i]);
+        sg += S::dec(v[9 + i]);
+    }
+    const unsigned bf = __float_as_uint(Hf - sf), bg = __float_as_uint(Hg - sg);
+    v[0] = S::from_bits((unsigned short)(bf >> 16));
+    v[18] = S::from_bits((unsigned short)(bf & 0xffffu));
+    v[9] = S::from_bits((unsigned short)(bg >> 16));
+    v[19] = S::from_bits((unsigned short)(bg & 0xffffu));
+    put_planes<S>(d, stride, kp.nx, v, ghost_lo, ghost_hi);
+}
+
 // ---------------------------------------------------------------- step
 // One fused time step.  CTA tile BX x BY; phase 1 computes psi for the tile
 // plus a one-site ring from pulled populations (ring pulls hit L2), phase 2
@@ -563,17 +693,24 @@ __global__ void __launch_bounds__(BX* BY)
 
     const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
     if (gx < kp.nx && gy < kp.ny - H) {
-        real f[9], g[9], Hf, Hg;
-        pull18h<S>(src, kp, gx, gy, f, g, Hf, Hg);
-        real rho = f[0];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) rho += f[i];
         real Fx, Fy, ux, uy, T;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1,
                                        WX, Fx, Fy);
-        collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
         const long long off = (long long)gy * kp.pitch + gx;
-        store_site<S>(dst + off, kp.plane, kp, f, g, Hf, Hg, false, false);
+        if constexpr (S::SPLIT) {
+            float h[9], q[9], Hf, Hg;
+            pull18_dev<S>(src, kp, gx, gy, h, q, Hf, Hg);
+            collide_dev<EQ24>(kp, h, q, Hf, Hg, Fx, Fy);
+            store_site_dev<S>(dst + off, kp.plane, kp, h, q, Hf, Hg, false, false);
+        } else {
+            real f[9], g[9], Hf, Hg;
+            pull18h<S>(src, kp, gx, gy, f, g, Hf, Hg);
+            real rho = f[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) rho += f[i];
+            collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+            store_site<S>(dst + off, kp.plane, kp, f, g, Hf, Hg, false, false);
+        }
     } else {
         flags = 0;
     }

@@ -260,11 +260,15 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
                     const bool ghost_lo = xg < ghost, ghost_hi = xg >= nx - ghost;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        elem* pf = dst + ((uint32_t)i * plane + off);
-                        S::put(pf, f[i], (real)kp.base_f[i]);
-                        if (ghost_lo) S::put(pf + nx, f[i], (real)kp.base_f[i]);
-                        if (ghost_hi) S::put(pf - nx, f[i], (real)kp.base_f[i]);
+                    for (int i = 0; i < 9; ++i) S::put(dst + ((uint32_t)i * plane + off), f[i], (real)kp.base_f[i]);
+                    // the periodic ghost copies: one branch per site, not per plane
+                    if (ghost_lo || ghost_hi) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            elem* pf = dst + ((uint32_t)i * plane + off);
+                            if (ghost_lo) S::put(pf + nx, f[i], (real)kp.base_f[i]);
+                            if (ghost_hi) S::put(pf - nx, f[i], (real)kp.base_f[i]);
+                        }
                     }
                 }
             }

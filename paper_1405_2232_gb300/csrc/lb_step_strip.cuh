@@ -36,6 +36,7 @@
 #pragma once
 
 #include "lb_device.cuh"
+#include "lb_fd.cuh"
 
 namespace lbgb {
 
@@ -300,13 +301,27 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             {
                 const int r = r_psi;
                 const int c = r - 1 + HALO;  // smem column of the site
-                real f[9], g[9], rho, T, psi, psi2;
+                real rho, T, psi, psi2;
+                if constexpr (S::SPLIT) {
+                    // rho and the energy density from the sums of the stored deviations
+                    float Hf = 0.0f, Hg = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    f[i] = load_pop<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i]);
-                    g[i] = load_pop<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i]);
+                    for (int i = 0; i < 9; ++i) {
+                        Hf += dev_of<S>(st + i * SEGW + c - ex(i), i, rest_lo_offset(i) * SEGW);
+                        Hg += dev_of<S>(st + (9 + i) * SEGW + c - ex(i), 9 + i, rest_lo_offset(9 + i) * SEGW);
+                    }
+                    rho = kp.sum_bf + Hf;
+                    T = (kp.sum_bg + Hg) / (rho * (real)kp.cv);
+                    site_psi_T<real, BMODE>(kp, rho, T, psi, psi2, flags);
+                } else {
+                    real f[9], g[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        f[i] = load_pop<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i]);
+                        g[i] = load_pop<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i]);
+                    }
+                    site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
                 }
-                site_psi<real, BMODE>(kp, f, g, rho, T, psi, psi2, flags);
                 if (BMODE != BETA_ZERO) rp[r] = psi;
                 if (BMODE != BETA_ONE) rq[r] = psi2;
             }
@@ -319,27 +334,41 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             const int sp = (j - 1) % STAGES;
             const elem* st = stage + (size_t)sp * NPL * SEGW;
             const int c = t + HALO;
-            real f[9], g[9], Hf = (real)0, Hg = (real)0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                f[i] = load_pop_acc<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i], Hf);
-                g[i] = load_pop_acc<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i], Hg);
-            }
-            real rho = f[0];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) rho += f[i];
             const int r = t + 1;
-            real Fx, Fy, ux, uy, T;
+            real Fx, Fy;
             force_from_rows<real, BMODE>(
                 kp, ring_psi + ((j - 2) & 3) * RW + r, ring_psi + ((j - 1) & 3) * RW + r,
                 ring_psi + (j & 3) * RW + r, ring_psi2 + ((j - 2) & 3) * RW + r,
                 ring_psi2 + ((j - 1) & 3) * RW + r, ring_psi2 + (j & 3) * RW + r, Fx, Fy);
-            collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
             int y = y_start + j - 2;
             y = y >= ny ? y - ny : y;
             const int xg = x0 + t;
             const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
-            store_site<S>(dst + off, plane, kp, f, g, Hf, Hg, xg < STRIP_GHOST, xg >= nx - STRIP_GHOST);
+            if constexpr (S::SPLIT) {
+                float h[9], q[9], Hf = 0.0f, Hg = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    h[i] = dev_of<S>(st + i * SEGW + c - ex(i), i, rest_lo_offset(i) * SEGW);
+                    q[i] = dev_of<S>(st + (9 + i) * SEGW + c - ex(i), 9 + i, rest_lo_offset(9 + i) * SEGW);
+                    Hf += h[i];
+                    Hg += q[i];
+                }
+                collide_dev<EQ24>(kp, h, q, Hf, Hg, Fx, Fy);
+                store_site_dev<S>(dst + off, plane, kp, h, q, Hf, Hg, xg < STRIP_GHOST, xg >= nx - STRIP_GHOST);
+            } else {
+                real f[9], g[9], Hf = (real)0, Hg = (real)0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    f[i] = load_pop_acc<S>(st + i * SEGW + c - ex(i), SEGW, i, (real)kp.base_f[i], Hf);
+                    g[i] = load_pop_acc<S>(st + (9 + i) * SEGW + c - ex(i), SEGW, 9 + i, (real)kp.base_g[i], Hg);
+                }
+                real rho = f[0];
+#pragma unroll
+                for (int i = 1; i < 9; ++i) rho += f[i];
+                real ux, uy, T;
+                collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
+                store_site<S>(dst + off, plane, kp, f, g, Hf, Hg, xg < STRIP_GHOST, xg >= nx - STRIP_GHOST);
+            }
         }
         // 3. the stage of job j-1 has had its last reader (psi at j-1, collision at j)
         if (j >= 1) {

@@ -292,7 +292,7 @@ def evaluate(net, doms, masks, cap, batch=16, chunk_rows=None, probe=2000,
     return out
 
 
-def compare(L=128, n_train=512, n_test=64, train_cap=20000, test_cap=40000, epochs=40, batch=16, probe=2000):
+def compare(L=128, n_train=1024, n_test=128, train_cap=20000, test_cap=40000, epochs=60, batch=16, probe=2000):
     """Warm vs plain on a reduced case (for the benchmark): train a network on
     n_train solves at L x L, then solve n_test unseen cases plain, warm, and
     warm with the plain fallback.  Returns the evaluation summary (no per-case
@@ -311,7 +311,7 @@ def compare(L=128, n_train=512, n_test=64, train_cap=20000, test_cap=40000, epoc
     net.close()
     ev.pop("per_case")
     ev["train"] = dict(cases=n_train, targets=int(ok.size), epochs=epochs, seconds=round(t_train, 2),
-                       train_cap=train_cap)
+                       train_cap=train_cap, generate_s=round(gen["wall_s"], 2), loss_last=float(losses[-1]))
     ev["seconds_total"] = round(time.perf_counter() - t0, 1)
     return ev
 
