@@ -24,6 +24,7 @@
 #include "lb.h"
 #include "unet.h"
 #include "unet_kernels.cuh"
+#include "unet_tc.cuh"
 
 namespace lbgb {
 lb_status record_error(lb_status st, const char* msg);
@@ -133,6 +134,7 @@ struct un_net {
     float* hpart = nullptr;   // [hblocks][2C + 2]
     double* lpart = nullptr;  // [hblocks]
     double* d_loss = nullptr;
+    int* d_err = nullptr;     // sticky error word of the tcgen05 convolution
     int hblocks = 0;
     std::vector<void*> allocs;
 };
@@ -204,7 +206,20 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
     a.W = Wl(n, l);
     a.relu = relu;
     a.up = up;
+    a.err = n->d_err;
     const long long M = (long long)N * a.H * a.W;
+    if (a.W % unk::TC_M == 0 && unk::tc_layer_ok(Cout, Cin)) {
+        // fifth-generation tensor cores: persistent CTAs, one per SM at most
+        const long long tiles = (long long)N * a.H * (a.W / unk::TC_M);
+        const int grid = (int)(tiles < n->sms ? tiles : n->sms);
+        const size_t smem = unk::tc_smem_bytes(Cout, Cin);
+        switch (Cout) {
+            case 32: unk::k_conv3_tc<32><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
+            case 64: unk::k_conv3_tc<64><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
+            default: unk::k_conv3_tc<96><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     if (a.W % unk::HT_W == 0 && a.H % unk::HT_H == 0 && Cout % unk::HT_NT == 0) {
         // halo-tile form: one staged input halo serves all nine taps
         const unsigned tiles = (unsigned)((long long)N * (a.H / unk::HT_H) * (a.W / unk::HT_W));
@@ -549,6 +564,12 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess) e = alloc(n, &n->hpart, (long long)n->hblocks * (2 * cfg->base + 2));
     if (e == cudaSuccess) e = alloc(n, &n->lpart, n->hblocks);
     if (e == cudaSuccess) e = alloc(n, &n->d_loss, 1);
+    if (e == cudaSuccess) e = alloc(n, &n->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream);
+    // the tcgen05 convolution: the largest dynamic shared memory any layer asks
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::halo_smem_bytes());
@@ -664,7 +685,14 @@ lb_status un_get_tensor(un_net* n, int32_t id, float* host, int64_t count) {
 lb_status un_synchronize(un_net* n) {
     if (!n) return uerr(LB_ERR_ARG, "un_synchronize: NULL net");
     UCU(cudaSetDevice(n->device), "cudaSetDevice");
+    int h = 0;
+    UCU(cudaMemcpyAsync(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream), "read error word");
     UCU(cudaStreamSynchronize(n->stream), "synchronize");
+    if (h) {
+        UCU(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream), "clear error word");
+        UCU(cudaStreamSynchronize(n->stream), "synchronize");
+        return uerr(LB_ERR_TIMEOUT, "a bounded wait of the tensor-core convolution gave up (error word 0x%x)", h);
+    }
     return LB_OK;
 }
 

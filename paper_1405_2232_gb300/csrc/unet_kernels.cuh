@@ -95,6 +95,7 @@ struct ConvArgs {
     int N, H, W;
     int relu;  // forward: ReLU after the bias
     int up;    // store each output pixel to the 2x2 block of a 2H x 2W image
+    int* err;  // sticky error word of the net (k_conv3_tc: bit 6 on a wait that gave up)
 };
 
 constexpr int CV_MT = 128;   // pixels per CTA

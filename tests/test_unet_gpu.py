@@ -16,6 +16,10 @@ from paper_1405_2232_gb300 import inputs as I
 H = W = 32
 NB = 2
 BASE = 32
+# (H, W, batch) of the layer-by-layer checks: 32 x 32 runs the mma.sync
+# kernels at every level; 128 x 256 also runs the tcgen05 convolution on the
+# two finest levels (image widths 256 and 128)
+SHAPES = [(32, 32, 2), (128, 256, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +35,8 @@ def N():
     return _n
 
 
-def problem(seed=21):
+def problem(seed=21, shape=(H, W, NB)):
+    h, w, nb = shape
     arch = U.architecture(base=BASE)
     flat = I.unet_init_params(arch).astype(np.float64)
     r = np.random.default_rng(seed)
@@ -39,7 +44,7 @@ def problem(seed=21):
     for name, (Wt, b) in P.items():
         b[:] = 0.05 * r.standard_normal(b.size)
     flat = flat.astype(np.float32)
-    x = r.standard_normal((NB, H, W, 3)).astype(np.float32)
+    x = r.standard_normal((nb, h, w, 3)).astype(np.float32)
     t = np.tanh(x[..., :2] + 0.5 * x[..., 2:3]).astype(np.float32)
     return arch, flat, x, t
 
@@ -50,10 +55,11 @@ def pad(x):
     return out
 
 
-@pytest.fixture(scope="module")
-def run(torch, N):
+@pytest.fixture(scope="module", params=SHAPES, ids=lambda s: f"{s[0]}x{s[1]}x{s[2]}")
+def run(torch, N, request):
     """One forward + backward on the GPU; every tensor fetched to the host."""
-    arch, flat, x, t = problem()
+    H, W, NB = request.param
+    arch, flat, x, t = problem(shape=request.param)
     dev = torch.device("cuda")
     with N.UNet(H, W, NB, BASE) as net:
         net.set_params(flat)
