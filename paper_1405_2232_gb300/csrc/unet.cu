@@ -12,6 +12,8 @@
 // and a gradient buffer for each, plus gup[l] (l = 1..3) and gs[l] (l = 0..2).
 // Weight gradients come from the split-pixel wgrad kernel and a fixed-order
 // sum, so the gradient is deterministic.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -185,6 +187,38 @@ void wgrad_shape(const un_net* n, const Layer& L, long long M, int* MT, int* NT,
     *splits = (int)((nchunks + c - 1) / c);
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link-time dependence on the driver library); host-only encoding
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a BF16 NHWC activation view for k_conv3_tc: dims (channels of
+// the buffer, W, H, N), box (8 channels, 128 pixels, 1, 1); the view's first
+// channel is applied in the copy coordinates.
+bool conv_tensor_map(const bf16* x, int xC, int W, int H, int N, CUtensorMap* map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)xC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)xC * 2, (cuuint64_t)W * xC * 2, (cuuint64_t)H * W * xC * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)unk::TC_M, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16* w, const float* bias, int Cout,
                  bf16* y, int yC, int yoff, const bf16* mask, int mC, int moff, int N, int l, int relu, int up) {
     unk::ConvArgs a;
@@ -208,15 +242,17 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
     a.up = up;
     a.err = n->d_err;
     const long long M = (long long)N * a.H * a.W;
-    if (a.W % unk::TC_M == 0 && unk::tc_layer_ok(Cout, Cin)) {
+    CUtensorMap xmap;
+    if (a.W % unk::TC_M == 0 && unk::tc_layer_ok(Cout, Cin) && conv_tensor_map(x, xC, a.W, a.H, N, &xmap)) {
         // fifth-generation tensor cores: persistent CTAs, one per SM at most
         const long long tiles = (long long)N * a.H * (a.W / unk::TC_M);
         const int grid = (int)(tiles < n->sms ? tiles : n->sms);
         const size_t smem = unk::tc_smem_bytes(Cout, Cin);
+        const int stages = unk::tc_stages(Cout, Cin);
         switch (Cout) {
-            case 32: unk::k_conv3_tc<32><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
-            case 64: unk::k_conv3_tc<64><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
-            default: unk::k_conv3_tc<96><<<grid, unk::TC_THREADS, smem, n->stream>>>(a); break;
+            case 32: unk::k_conv3_tc<32><<<grid, unk::TC_THREADS, smem, n->stream>>>(a, xmap, stages); break;
+            case 64: unk::k_conv3_tc<64><<<grid, unk::TC_THREADS, smem, n->stream>>>(a, xmap, stages); break;
+            default: unk::k_conv3_tc<96><<<grid, unk::TC_THREADS, smem, n->stream>>>(a, xmap, stages); break;
         }
         return cudaGetLastError();
     }

@@ -12,9 +12,12 @@
 // Reuse: the CTA stages, per 32-channel chunk, the 3-row x 130-pixel input
 // halo of its row segment once, in the no-swizzle K-major core-matrix layout
 // with the pixels of a halo row 16 bytes apart inside each 8-channel group:
-//   group g (8 channels), halo row r, halo column h -> g * TC_KG + (r * TC_HW + h) * 16
+//   group g (8 channels), halo row r, slot h -> g * TC_KG + (r * TC_HROW + h) * 16
+// where slots 8 .. 135 hold the segment's 128 pixels (written by one TMA
+// tensor copy per group and row, 128-byte aligned) and slots 7 and 136 the
+// wrapped neighbours left and right (plain 16-byte copies: circular padding).
 // The A operand of tap (dy, dx) is then the same bytes seen through a matrix
-// descriptor that starts at halo row dy + 1, column dx + 1 (core matrices of
+// descriptor that starts at halo row dy + 1, slot 7 + dx + 1 (core matrices of
 // 8 consecutive pixels 128 bytes apart along M, 8-channel groups TC_KG bytes
 // apart along K), so the nine taps are nine descriptors over one staged halo.
 // The weights of the layer (9 x Cout x Cin, at most TC_MAX_WBYTES) stay
@@ -22,14 +25,16 @@
 // core-matrix layout (8 output channels x 8 input channels per core matrix).
 //
 // Persistent, warp-specialised CTAs (one per SM, tiles dealt round-robin):
-//   warps 0-3  producers: cp.async the halo of every (tile, chunk) into a
-//              TC_STAGES-deep ring (wrapped coordinates: circular padding),
-//              then fence.proxy.async and arrive on the stage's "full"
-//              mbarrier once their copies have landed;
-//   warp 8     one thread issues the 9 x (32 / 16) MMAs of a stage into the
+//   warp 0     producer: lane 0 arms the stage's "full" mbarrier with the
+//              byte count and issues the 12 TMA tensor copies (4 channel
+//              groups x 3 rows, cp.async.bulk.tensor, completion by
+//              transaction count); lanes 0..23 copy the 24 wrapped edge
+//              pixels and arrive once their copies have landed (after
+//              fence.proxy.async); the ring is `stages` deep (up to 8);
+//   warp 5     one thread issues the 9 x (32 / 16) MMAs of a stage into the
 //              tile's accumulator and tcgen05.commit's the stage's "empty"
 //              mbarrier; after the tile's last chunk it commits "acc full";
-//   warps 4-7  epilogue: wait "acc full", tcgen05.ld the tile (TMEM lane =
+//   warps 1-4  epilogue: wait "acc full", tcgen05.ld the tile (TMEM lane =
 //              pixel, column = output channel), add the bias, apply ReLU and
 //              the gradient mask, round to BF16 and store (or store each
 //              pixel to its 2 x 2 block for the upsampling), then arrive on
@@ -39,9 +44,12 @@
 //
 // Every mbarrier wait is bounded (about one second); a wait that gives up
 // sets bit LB_ERR_TIMEOUT (6) of *a.err and the CTA winds down: no role
-// waits unboundedly on another, producers wait for their own copies before
-// leaving, and TMEM is released after a block-wide barrier.
+// waits unboundedly on another, the producer waits (with the default limit)
+// for every copy it issued before leaving, and TMEM is released after a
+// block-wide barrier once the MMAs issued have completed.
 #pragma once
+
+#include <cuda.h>
 
 #include "unet_kernels.cuh"
 
@@ -49,23 +57,51 @@ namespace unk {
 
 constexpr int TC_M = 128;                       // pixels per tile (UMMA M)
 constexpr int TC_KC = 32;                       // input channels per stage
-constexpr int TC_HW = TC_M + 2;                 // halo row width (pixels)
-constexpr int TC_KG = 3 * TC_HW * 16;           // bytes of one 8-channel group of a halo (6240)
-constexpr int TC_ABYTES = (TC_KC / 8) * TC_KG;  // bytes of one halo stage
-constexpr int TC_ASTRIDE = (TC_ABYTES + 127) / 128 * 128;
-constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 288;                 // 4 producer, 4 epilogue warps, 1 MMA warp
+constexpr int TC_HROW = 144;                    // halo row slots (16 bytes each): pixels at 7 .. 136
+constexpr int TC_BODY = 8;                      // slot of the segment's first pixel (128-byte aligned)
+constexpr int TC_KG = 3 * TC_HROW * 16;         // bytes of one 8-channel group of a halo (6912)
+constexpr int TC_ASTRIDE = (TC_KC / 8) * TC_KG; // bytes of one halo stage (27648, a multiple of 128)
+constexpr int TC_TMA_BYTES = (TC_KC / 8) * 3 * TC_M * 16;  // bytes the 12 tensor copies deliver
+constexpr int TC_EDGES = (TC_KC / 8) * 3 * 2;   // wrapped edge pixels per stage (24)
+constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_THREADS = 192;                 // producer warp, 4 epilogue warps, MMA warp
 constexpr int TC_MAX_WBYTES = 100 * 1024;       // resident weights per layer
+constexpr size_t TC_SMEM_LIMIT = 232448;        // dynamic shared memory per CTA
 constexpr long long TC_WAIT = 2000000000LL;     // bounded-wait limit (clock cycles)
 
 __host__ __device__ constexpr size_t tc_wbytes(int N, int Cin) { return (size_t)9 * N * Cin * 2; }
+__host__ __device__ constexpr size_t tc_fixed_bytes(int N, int Cin) {
+    // weights (rounded to 1 KB), barriers + TMEM slot + flag, alignment slack
+    return (tc_wbytes(N, Cin) + 1023) / 1024 * 1024 + 256 + 1024;
+}
+// ring depth that fits the shared memory next to the layer's weights
+__host__ __device__ constexpr int tc_stages(int N, int Cin) {
+    const size_t room = TC_SMEM_LIMIT - tc_fixed_bytes(N, Cin);
+    const size_t s = room / TC_ASTRIDE;
+    return s > TC_MAX_STAGES ? TC_MAX_STAGES : (int)s;
+}
 __host__ __device__ constexpr size_t tc_smem_bytes(int N, int Cin) {
-    // weights (rounded to 1 KB), halo stages, 13 mbarriers + TMEM slot + flag, alignment slack
-    return (tc_wbytes(N, Cin) + 1023) / 1024 * 1024 + (size_t)TC_STAGES * TC_ASTRIDE + 128 + 1024;
+    return tc_fixed_bytes(N, Cin) + (size_t)tc_stages(N, Cin) * TC_ASTRIDE;
 }
 // whether a layer runs on this kernel (the host checks the image width too)
 __host__ __device__ constexpr bool tc_layer_ok(int N, int Cin) {
-    return (N == 32 || N == 64 || N == 96) && Cin % TC_KC == 0 && tc_wbytes(N, Cin) <= (size_t)TC_MAX_WBYTES;
+    return (N == 32 || N == 64 || N == 96) && Cin % TC_KC == 0 && tc_wbytes(N, Cin) <= (size_t)TC_MAX_WBYTES &&
+           tc_stages(N, Cin) >= 3;
+}
+
+__device__ __forceinline__ void tc_bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// TMA tensor copy of one box of a 4-D tensor map into shared memory, completion
+// counted on an mbarrier in bytes
+__device__ __forceinline__ void tc_tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                             uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_bar_init(uint64_t* bar, uint32_t count) {
@@ -106,16 +142,17 @@ __host__ __device__ constexpr uint32_t tc_tmem_cols() {
 }
 
 template <int N>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv3_tc(ConvArgs a, const __grid_constant__ CUtensorMap xmap, int stages) {
     extern __shared__ __align__(1024) uint8_t tc_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
     const int Cin = a.Cin;
     const size_t wround = (tc_wbytes(N, Cin) + 1023) / 1024 * 1024;
     uint8_t* sW = base;                       // [9][N/8][Cin/8] core matrices
-    uint8_t* sA = base + wround;              // [TC_STAGES][TC_ASTRIDE]
-    uint64_t* full = reinterpret_cast<uint64_t*>(sA + (size_t)TC_STAGES * TC_ASTRIDE);
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* accf = empty + TC_STAGES;       // [2]
+    uint8_t* sA = base + wround;              // [stages][TC_ASTRIDE], 1024-byte aligned
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + (size_t)stages * TC_ASTRIDE);
+    uint64_t* empty = full + TC_MAX_STAGES;
+    uint64_t* accf = empty + TC_MAX_STAGES;   // [2]
     uint64_t* acce = accf + 2;                // [2]
     uint64_t* mdone = acce + 2;               // the MMA thread's last commit
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mdone + 1);
@@ -130,8 +167,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
     const uint32_t wplane = (uint32_t)N * (uint32_t)Cin * 2u;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            tc_bar_init(&full[s], 128);
+        for (int s = 0; s < stages; ++s) {
+            tc_bar_init(&full[s], 1 + TC_EDGES);     // the armed byte count + the edge copies
             tc_bar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -164,9 +201,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
 
-    if (warp < 4) {
-        // ------------------------------------------------ producers
-        constexpr int D = 2;  // jobs in flight per thread before its arrival
+    if (warp == 0) {
+        // ------------------------------------------------ producer warp
+        constexpr int D = 2;  // edge-copy groups in flight before their arrival
+        // this lane's edge pixel: channel group g, halo row hr, side (0 left, 1 right)
+        const int eg = lane / 6, ehr = (lane % 6) >> 1, eside = lane & 1;
+        const bool edge = lane < TC_EDGES;
         long long j = 0;
         for (long long tile = blockIdx.x; tile < ntiles && !*s_abort; tile += gridDim.x) {
             const int seg = (int)(tile % segs);
@@ -174,39 +214,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
             const int y = (int)(r % H);
             const int n = (int)(r / H);
             const int x0 = seg * TC_M;
+            bool stop = false;
             for (int c = 0; c < nchunks; ++c, ++j) {
-                const int s = (int)(j % TC_STAGES);
-                if (j >= TC_STAGES &&
-                    !tc_bar_wait(&empty[s], (uint32_t)(((j / TC_STAGES) - 1) & 1))) {
-                    *s_abort = 1;
-                    if (a.err) atomicOr(a.err, 1 << 6);
+                const int s = (int)(j % stages);
+                // one decision per warp (its lanes poll the barrier independently)
+                if (j >= stages &&
+                    !__all_sync(0xffffffffu, tc_bar_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1)))) {
+                    if (lane == 0) {
+                        *s_abort = 1;
+                        if (a.err) atomicOr(a.err, 1 << 6);
+                    }
+                    stop = true;
                     break;
                 }
                 uint8_t* st = sA + (size_t)s * TC_ASTRIDE;
-                // (8-channel group, halo row, halo column) -> 16-byte copy
-                for (int q = tid; q < (TC_KC / 8) * 3 * TC_HW; q += 128) {
-                    const int g = q / (3 * TC_HW);
-                    const int rem = q - g * (3 * TC_HW);
-                    const int hr = rem / TC_HW, hc = rem - hr * TC_HW;
-                    const int yy = wrap(y + hr - 1, H), xx = wrap(x0 + hc - 1, W);
+                const int cbase = a.xoff + c * TC_KC;
+                if (lane == 0) {
+                    tc_bar_arrive_tx(&full[s], (uint32_t)TC_TMA_BYTES);
+#pragma unroll
+                    for (int g = 0; g < TC_KC / 8; ++g)
+#pragma unroll
+                        for (int hr = 0; hr < 3; ++hr)
+                            tc_tma_load4(st + g * TC_KG + (hr * TC_HROW + TC_BODY) * 16, &xmap, cbase + g * 8, x0,
+                                         wrap(y + hr - 1, H), n, &full[s]);
+                }
+                if (edge) {
+                    const int yy = wrap(y + ehr - 1, H);
+                    const int xx = eside ? wrap(x0 + TC_M, W) : wrap(x0 - 1, W);
                     const long long pix = ((long long)n * H + yy) * W + xx;
-                    cp_async16(st + g * TC_KG + rem * 16, a.x + pix * a.xC + a.xoff + c * TC_KC + g * 8, true);
+                    cp_async16(st + eg * TC_KG + (ehr * TC_HROW + (eside ? TC_BODY + TC_M : TC_BODY - 1)) * 16,
+                               a.x + pix * a.xC + cbase + eg * 8, true);
                 }
                 cp_async_commit();
                 if (j >= D) {
                     cp_async_wait<D>();
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    tc_bar_arrive(&full[(int)((j - D) % TC_STAGES)]);
+                    if (edge) tc_bar_arrive(&full[(int)((j - D) % stages)]);
                 }
             }
-            if (*s_abort) break;
+            if (stop) break;
         }
-        // the last jobs: their copies, then their arrivals (also after an abort,
-        // so that no copy is in flight when the CTA leaves)
+        // the last jobs' edge copies, then their arrivals; then every tensor
+        // copy issued has landed (waits with the default limit) before leaving
         cp_async_wait<0>();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (long long k = (j > D ? j - D : 0); k < j; ++k) tc_bar_arrive(&full[(int)(k % TC_STAGES)]);
-    } else if (warp == 8) {
+        if (edge)
+            for (long long k = (j > D ? j - D : 0); k < j; ++k) tc_bar_arrive(&full[(int)(k % stages)]);
+        if (lane == 0)
+            for (long long k = (j > stages ? j - stages : 0); k < j; ++k)
+                (void)tc_bar_wait(&full[(int)(k % stages)], (uint32_t)((k / stages) & 1));
+        __syncwarp();
+    } else if (warp == 5) {
         // ------------------------------------------------ MMA issue (one thread)
         if (lane == 0) {
             constexpr uint32_t IDESC = tc_idesc_n<N>();
@@ -222,8 +280,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + (uint32_t)(b * N);
                 for (int c = 0; c < nchunks; ++c, ++j) {
-                    const int s = (int)(j % TC_STAGES);
-                    if (!tc_bar_wait(&full[s], (uint32_t)((j / TC_STAGES) & 1))) {
+                    const int s = (int)(j % stages);
+                    if (!tc_bar_wait(&full[s], (uint32_t)((j / stages) & 1))) {
                         ok = false;
                         break;
                     }
@@ -231,11 +289,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
                     const uint32_t aA = smem_addr(sA + (size_t)s * TC_ASTRIDE);
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;  // halo row / column of the view
+                        const int dy = tap / 3, dx = tap % 3;  // halo row and column offset of the view
 #pragma unroll
                         for (int kk = 0; kk < TC_KC / 16; ++kk) {
-                            const uint64_t da =
-                                tc_mdesc(aA + (uint32_t)(2 * kk * TC_KG + (dy * TC_HW + dx) * 16), TC_KG, 128);
+                            const uint64_t da = tc_mdesc(
+                                aA + (uint32_t)(2 * kk * TC_KG + (dy * TC_HROW + TC_BODY - 1 + dx) * 16), TC_KG, 128);
                             const uint64_t db = tc_mdesc(
                                 aW + (uint32_t)tap * wplane + (uint32_t)((c * (TC_KC / 8) + 2 * kk) * 128), 128,
                                 (uint32_t)SBO_W);
@@ -270,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue (warps 4-7)
+        // ------------------------------------------------ epilogue (warps 1-4)
         const int q = warp & 3;                  // TMEM lanes 32 q .. 32 q + 31
         const int px = q * 32 + lane;            // pixel of the tile
         long long t = 0;
@@ -309,9 +367,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvArgs a) {
                     float f8[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) f8[k] = __uint_as_float(v[j8 * 8 + k]);
-                    if (a.bias)
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) f8[k] += a.bias[co + k];
+                    if (a.bias) {
+                        const float4 b0 = *reinterpret_cast<const float4*>(a.bias + co);
+                        const float4 b1 = *reinterpret_cast<const float4*>(a.bias + co + 4);
+                        f8[0] += b0.x; f8[1] += b0.y; f8[2] += b0.z; f8[3] += b0.w;
+                        f8[4] += b1.x; f8[5] += b1.y; f8[6] += b1.z; f8[7] += b1.w;
+                    }
                     if (a.relu)
 #pragma unroll
                         for (int k = 0; k < 8; ++k) f8[k] = fmaxf(f8[k], 0.0f);
