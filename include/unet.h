@@ -13,7 +13,10 @@
  * of 32).  Encoder level l (width C 2^l): two 3x3 circular convolutions +
  * ReLU, 2x2 average pool between levels; decoder: nearest 2x upsampling,
  * concatenation [upsampled, skip] along channels, two 3x3 convolutions +
- * ReLU; head: 1x1 convolution C -> 2, no activation.  Tensors are NHWC.
+ * ReLU; head: 1x1 convolution C -> 2, no activation.  The input and output
+ * planes are pixel-major ([N][H][W][c]); the BF16 activations inside the net
+ * are stored row by row in blocks of 8 channels (un_get_tensor returns them
+ * as NHWC).
  * Arithmetic: BF16 weights and activations (round to nearest even), FP32
  * accumulation on the tensor cores, FP32 bias, head, loss, gradients of the
  * weights and Adam state (FP32 master weights).

@@ -1,7 +1,7 @@
 // unet.cu -- host side of the warm-start network (include/unet.h).
 //
-// Buffers (BF16, NHWC, sized for max_batch; level l has H>>l x W>>l pixels
-// and C_l = base << l channels):
+// Buffers (BF16 in the row-blocked channel-group layout of act_at, sized for
+// max_batch; level l has H>>l x W>>l pixels and C_l = base << l channels):
 //   x0            padded input, 32 channels
 //   a[l]          first encoder conv output, l = 0..3
 //   cat[l]        l = 0..2: channels [0, C_{l+1}) the upsampled output of the
@@ -204,15 +204,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// Tensor map of a BF16 NHWC activation view for k_conv3_tc: dims (channels of
-// the buffer, W, H, N), box (8 channels, 128 pixels, 1, 1); the view's first
-// channel is applied in the copy coordinates.
+// Tensor map of a BF16 activation tensor (layout of act_at) for k_conv3_tc:
+// dims (64 values = 8 pixels x 8 channels, W / 8 pixel blocks, xC / 8
+// channel groups, N H rows), box (64, 16, 1, 1): one box is 128 pixels of one
+// channel group of one row, a contiguous 2 KB block moved as 16 rows of 128
+// bytes.  The view's first channel group is applied in the coordinates.
 bool conv_tensor_map(const bf16* x, int xC, int W, int H, int N, CUtensorMap* map) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)xC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    const cuuint64_t strides[3] = {(cuuint64_t)xC * 2, (cuuint64_t)W * xC * 2, (cuuint64_t)H * W * xC * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)unk::TC_M, 1, 1};
+    const cuuint64_t dims[4] = {64, (cuuint64_t)(W / 8), (cuuint64_t)(xC / 8), (cuuint64_t)N * H};
+    const cuuint64_t strides[3] = {128, (cuuint64_t)W * 16, (cuuint64_t)xC * W * 2};
+    const cuuint32_t box[4] = {64, (cuuint32_t)unk::TC_M / 8, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -243,7 +245,8 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
     a.err = n->d_err;
     const long long M = (long long)N * a.H * a.W;
     CUtensorMap xmap;
-    if (a.W % unk::TC_M == 0 && unk::tc_layer_ok(Cout, Cin) && conv_tensor_map(x, xC, a.W, a.H, N, &xmap)) {
+    if (a.W % unk::TC_M == 0 && M / unk::TC_M < (1LL << 31) && unk::tc_layer_ok(Cout, Cin) &&
+        conv_tensor_map(x, xC, a.W, a.H, N, &xmap)) {
         // fifth-generation tensor cores: persistent CTAs, one per SM at most
         const long long tiles = (long long)N * a.H * (a.W / unk::TC_M);
         const int grid = (int)(tiles < n->sms ? tiles : n->sms);
@@ -349,7 +352,7 @@ cudaError_t refresh_weights(un_net* n) {
 
 cudaError_t forward(un_net* n, int N, const float* d_in) {
     const int LV = UN_LEVELS;
-    unk::k_input<<<grid_for(Pl(n, 0, N)), 256, 0, n->stream>>>(d_in, Pl(n, 0, N), n->x0);
+    unk::k_input<<<grid_for(Pl(n, 0, N) * 4), 256, 0, n->stream>>>(d_in, (long long)N * Hl(n, 0), Wl(n, 0), n->x0);
     for (int l = 0; l < LV; ++l) {
         const bf16* src = l == 0 ? n->x0 : n->pl[l - 1];
         const int sC = l == 0 ? UN_IN_PAD : Cl(n, l - 1);
@@ -388,8 +391,12 @@ cudaError_t head_fwd(un_net* n, int N, float* out) {
     const int C = n->cfg.base;
     const int g = grid_for(P);
     switch (C) {
-        case 32: unk::k_head_fwd<32><<<g, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, P, out); break;
-        case 64: unk::k_head_fwd<64><<<g, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, P, out); break;
+        case 32:
+            unk::k_head_fwd<32><<<g, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, P, Wl(n, 0), out);
+            break;
+        case 64:
+            unk::k_head_fwd<64><<<g, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, P, Wl(n, 0), out);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -405,12 +412,12 @@ cudaError_t backward(un_net* n, int N, const float* d_target) {
     const float inv2 = (float)(2.0 / ((double)P * UN_OUT));
     switch (C) {
         case 32:
-            unk::k_head_bwd<32><<<hb, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, d_target, P, rows, inv2,
-                                                           n->gd0, n->hpart, n->lpart);
+            unk::k_head_bwd<32><<<hb, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, d_target, P, Wl(n, 0),
+                                                           rows, inv2, n->gd0, n->hpart, n->lpart);
             break;
         case 64:
-            unk::k_head_bwd<64><<<hb, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, d_target, P, rows, inv2,
-                                                           n->gd0, n->hpart, n->lpart);
+            unk::k_head_bwd<64><<<hb, 256, 0, n->stream>>>(n->d0, n->p + H.woff, n->p + H.boff, d_target, P, Wl(n, 0),
+                                                           rows, inv2, n->gd0, n->hpart, n->lpart);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -448,8 +455,9 @@ cudaError_t backward(un_net* n, int N, const float* d_target) {
     return cudaGetLastError();
 }
 
-// tensor table for un_get_tensor: pointer and element count at N
-bool tensor_of(const un_net* n, int id, int N, const bf16** ptr, long long* count) {
+// tensor table for un_get_tensor: pointer, element count at N, channels and
+// image width of the tensor
+bool tensor_of(const un_net* n, int id, int N, const bf16** ptr, long long* count, int* chans, int* width) {
     const int LV = UN_LEVELS;
     const bool grad = id >= UN_T_GRAD;
     const int b = grad ? id - UN_T_GRAD : id;
@@ -501,6 +509,9 @@ bool tensor_of(const un_net* n, int id, int N, const bf16** ptr, long long* coun
     }
     *ptr = p;
     *count = cnt;
+    const int lev = kind == UN_T_P ? l + 1 : l;
+    *width = Wl(n, lev);
+    *chans = (int)(cnt / Pl(n, lev, N));
     return true;
 }
 
@@ -705,16 +716,21 @@ lb_status un_get_tensor(un_net* n, int32_t id, float* host, int64_t count) {
     if (!n || !host) return uerr(LB_ERR_ARG, "un_get_tensor: NULL argument");
     const bf16* p = nullptr;
     long long cnt = 0;
-    if (n->lastN < 1 || !tensor_of(n, id, n->lastN, &p, &cnt) || cnt != count)
+    int C = 0, W = 0;
+    if (n->lastN < 1 || !tensor_of(n, id, n->lastN, &p, &cnt, &C, &W) || cnt != count)
         return uerr(LB_ERR_ARG, "un_get_tensor: unknown id %d or wrong size", id);
     UCU(cudaSetDevice(n->device), "cudaSetDevice");
     std::vector<uint16_t> h((size_t)cnt);
     UCU(cudaMemcpyAsync(h.data(), p, sizeof(uint16_t) * cnt, cudaMemcpyDeviceToHost, n->stream), "tensor download");
     UCU(cudaStreamSynchronize(n->stream), "synchronize");
-    for (long long i = 0; i < cnt; ++i) {
-        const uint32_t bits = (uint32_t)h[(size_t)i] << 16;
-        std::memcpy(host + i, &bits, 4);
-    }
+    // row-blocked channel groups -> NHWC
+    const long long rows = cnt / ((long long)C * W);
+    for (long long r = 0; r < rows; ++r)
+        for (int x = 0; x < W; ++x)
+            for (int c = 0; c < C; ++c) {
+                const uint32_t bits = (uint32_t)h[(size_t)unk::act_at(r, x, c, C, W)] << 16;
+                std::memcpy(host + (r * W + x) * C + c, &bits, 4);
+            }
     return LB_OK;
 }
 

@@ -9,6 +9,13 @@
 //     split over pixel ranges, partials reduced in a fixed order.
 // Everything else (pool, upsampling gradients, head, loss, Adam, handoff) is
 // element-wise or a small reduction and bound by memory traffic.
+//
+// Activation layout (every BF16 tensor of the net): per image row
+// (row = n H + y), the C / 8 channel groups one after the other, each group
+// the row's W pixels x 8 channels (16 bytes per pixel); see act_at.  A
+// pixel's 8 channels stay one 16-byte vector, a warp's 32 consecutive pixels
+// of one group are 512 contiguous bytes, and a group of a row segment is one
+// contiguous block for the tensor copies of the tcgen05 convolution.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -63,6 +70,12 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// element (row, x, c) of an activation tensor with C channels and W pixels
+// per row (C a multiple of 8): ((row C + 8 floor(c / 8)) W + 8 x + c mod 8
+__host__ __device__ __forceinline__ long long act_at(long long row, int x, int c, int C, int W) {
+    return (row * C + (c & ~7)) * (long long)W + x * 8 + (c & 7);
+}
+
 __device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
@@ -83,7 +96,7 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 
 // ------------------------------------------------------------ convolution
 struct ConvArgs {
-    const bf16* x;  // input view: pixel stride xC, first channel xoff, Cin channels
+    const bf16* x;  // input view: channels xoff .. xoff + Cin - 1 of a tensor of xC channels
     int xC, xoff, Cin;
     const bf16* w;  // [Cout][9][Cin]
     const float* bias;  // [Cout] or nullptr
@@ -134,9 +147,9 @@ __global__ void __launch_bounds__(256) k_conv3(ConvArgs a) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int yy = wrap(ay[i] + dy, a.H), xx = wrap(ax[i] + dx, a.W);
-            const long long pix = ((long long)an[i] * a.H + yy) * a.W + xx;
+            const long long row = (long long)an[i] * a.H + yy;
             cp_async16(&sA[s][((tid >> 2) + i * 64) * CV_LD + part * 8],
-                       a.x + pix * a.xC + a.xoff + c0 + part * 8, av[i]);
+                       a.x + act_at(row, xx, a.xoff + c0 + part * 8, a.xC, a.W), av[i]);
         }
         for (int q = tid; q < NT * 4; q += 256) {
             const int r = q >> 2, pp = q & 3;
@@ -214,23 +227,22 @@ __global__ void __launch_bounds__(256) k_conv3(ConvArgs a) {
                     v0 = fmaxf(v0, 0.0f);
                     v1 = fmaxf(v1, 0.0f);
                 }
+                const long long row = (long long)n * a.H + yy;
                 if (a.mask) {
-                    const bf16* mp = a.mask + (long long)m * a.mC + a.moff + co;
+                    const bf16* mp = a.mask + act_at(row, xx, a.moff + co, a.mC, a.W);
                     v0 = __bfloat162float(mp[0]) > 0.0f ? v0 : 0.0f;
                     v1 = __bfloat162float(mp[1]) > 0.0f ? v1 : 0.0f;
                 }
                 const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
                 if (!a.up) {
-                    *reinterpret_cast<__nv_bfloat162*>(a.y + (long long)m * a.yC + a.yoff + co) = o;
+                    *reinterpret_cast<__nv_bfloat162*>(a.y + act_at(row, xx, a.yoff + co, a.yC, a.W)) = o;
                 } else {
-                    const int W2 = 2 * a.W;
 #pragma unroll
                     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            const long long pix = ((long long)n * 2 * a.H + 2 * yy + dy) * W2 + 2 * xx + dx;
-                            *reinterpret_cast<__nv_bfloat162*>(a.y + pix * a.yC + a.yoff + co) = o;
-                        }
+                        for (int dx = 0; dx < 2; ++dx)
+                            *reinterpret_cast<__nv_bfloat162*>(
+                                a.y + act_at(2 * row + dy, 2 * xx + dx, a.yoff + co, a.yC, 2 * a.W)) = o;
                 }
             }
         }
@@ -267,12 +279,13 @@ __global__ void __launch_bounds__(256) k_conv3_halo(ConvArgs a) {
     auto load_chunk = [&](int c, int s) {
         const int c0 = c * CV_KC;
         bf16* A = sA + s * HT_A;
+        // consecutive threads take consecutive halo pixels of one channel group
         for (int q = tid; q < HT_HH * HT_HW * 4; q += 256) {
-            const int hp = q >> 2, part = q & 3;
+            const int part = q / (HT_HH * HT_HW), hp = q - part * (HT_HH * HT_HW);
             const int hy = hp / HT_HW, hx = hp - (hp / HT_HW) * HT_HW;
             const int yy = wrap(ty0 + hy - 1, a.H), xx = wrap(tx0 + hx - 1, a.W);
-            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
-            cp_async16(A + hp * CV_LD + part * 8, a.x + pix * a.xC + a.xoff + c0 + part * 8, true);
+            cp_async16(A + hp * CV_LD + part * 8,
+                       a.x + act_at((long long)n * a.H + yy, xx, a.xoff + c0 + part * 8, a.xC, a.W), true);
         }
         bf16* B = sB + s * HT_B;
         for (int q = tid; q < 9 * HT_NT * 4; q += 256) {
@@ -343,7 +356,7 @@ __global__ void __launch_bounds__(256) k_conv3_halo(ConvArgs a) {
         for (int h = 0; h < 2; ++h) {
             const int r = wm * 32 + mi * 16 + g + h * 8;
             const int yy = ty0 + r / HT_W, xx = tx0 + r % HT_W;
-            const long long m = ((long long)n * a.H + yy) * a.W + xx;
+            const long long row = (long long)n * a.H + yy;
 #pragma unroll
             for (int ni = 0; ni < NI; ++ni) {
                 const int co = co0 + wn * WN + ni * 8 + 2 * t4;
@@ -357,21 +370,20 @@ __global__ void __launch_bounds__(256) k_conv3_halo(ConvArgs a) {
                     v1 = fmaxf(v1, 0.0f);
                 }
                 if (a.mask) {
-                    const bf16* mp = a.mask + m * a.mC + a.moff + co;
+                    const bf16* mp = a.mask + act_at(row, xx, a.moff + co, a.mC, a.W);
                     v0 = __bfloat162float(mp[0]) > 0.0f ? v0 : 0.0f;
                     v1 = __bfloat162float(mp[1]) > 0.0f ? v1 : 0.0f;
                 }
                 const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
                 if (!a.up) {
-                    *reinterpret_cast<__nv_bfloat162*>(a.y + m * a.yC + a.yoff + co) = o;
+                    *reinterpret_cast<__nv_bfloat162*>(a.y + act_at(row, xx, a.yoff + co, a.yC, a.W)) = o;
                 } else {
 #pragma unroll
                     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            const long long pix = ((long long)n * 2 * a.H + 2 * yy + dy) * (2 * a.W) + 2 * xx + dx;
-                            *reinterpret_cast<__nv_bfloat162*>(a.y + pix * a.yC + a.yoff + co) = o;
-                        }
+                        for (int dx = 0; dx < 2; ++dx)
+                            *reinterpret_cast<__nv_bfloat162*>(
+                                a.y + act_at(2 * row + dy, 2 * xx + dx, a.yoff + co, a.yC, 2 * a.W)) = o;
                 }
             }
         }
@@ -379,7 +391,7 @@ __global__ void __launch_bounds__(256) k_conv3_halo(ConvArgs a) {
 
 // -------------------------------------------------------- weight gradient
 struct WgradArgs {
-    const bf16* g;  // gradient at the conv output: pixel stride gC, first channel goff, Cout channels
+    const bf16* g;  // gradient at the conv output: channels goff .. goff + Cout - 1 of a tensor of gC
     int gC, goff;
     const bf16* x;  // conv input view, Cin channels
     int xC, xoff;
@@ -416,7 +428,9 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
             const int px = qq / (MT / 8), pp = qq % (MT / 8);
             const int m = c * 32 + px;
             const bool v = m < M;
-            cp_async16(&sG[s][px * LG + pp * 8], a.g + (long long)(v ? m : 0) * a.gC + a.goff + co0 + pp * 8, v);
+            const int mm = v ? m : 0;
+            cp_async16(&sG[s][px * LG + pp * 8], a.g + act_at(mm / a.W, mm % a.W, a.goff + co0 + pp * 8, a.gC, a.W),
+                       v);
         }
         for (int qq = tid; qq < 32 * NT / 8; qq += 256) {
             const int px = qq / (NT / 8), pp = qq % (NT / 8);
@@ -426,8 +440,8 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
             const int n = mm / HW;
             const int r = mm - n * HW;
             const int yy = wrap(r / a.W + dy, a.H), xx = wrap(r % a.W + dx, a.W);
-            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
-            cp_async16(&sX[s][px * LX + pp * 8], a.x + pix * a.xC + a.xoff + ci0 + pp * 8, v);
+            cp_async16(&sX[s][px * LX + pp * 8],
+                       a.x + act_at((long long)n * a.H + yy, xx, a.xoff + ci0 + pp * 8, a.xC, a.W), v);
         }
     };
 
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
 // whose B fragments come from the halo at the shifted pixel rows.  Warp w owns
 // co rows 16 (w & 1) .. +15 and ci columns 8 (w >> 1) .. +7 of every tap.
 struct WgradHaloArgs {
-    const bf16* g;  // gradient at the conv output (pixel stride gC, first channel goff)
+    const bf16* g;  // gradient at the conv output (channels goff .. of a tensor of gC)
     int gC, goff;
     const bf16* x;  // conv input view
     int xC, xoff;
@@ -529,17 +543,18 @@ __global__ void __launch_bounds__(256) k_wgrad_halo(WgradHaloArgs a) {
         const int n = b / tiles_y;
         bf16* G = sG + s * WH_G;
         for (int q = tid; q < HT_H * HT_W * 4; q += 256) {
-            const int r = q >> 2, part = q & 3;
-            const long long pix = ((long long)n * a.H + ty0 + r / HT_W) * a.W + tx0 + (r % HT_W);
-            cp_async16(G + r * CV_LD + part * 8, a.g + pix * a.gC + a.goff + co0 + part * 8, true);
+            const int part = q / (HT_H * HT_W), r = q - part * (HT_H * HT_W);
+            const long long row = (long long)n * a.H + ty0 + r / HT_W;
+            cp_async16(G + r * CV_LD + part * 8, a.g + act_at(row, tx0 + (r % HT_W), a.goff + co0 + part * 8, a.gC, a.W),
+                       true);
         }
         bf16* X = sX + s * WH_X;
         for (int q = tid; q < HT_HH * HT_HW * 4; q += 256) {
-            const int hp = q >> 2, part = q & 3;
+            const int part = q / (HT_HH * HT_HW), hp = q - part * (HT_HH * HT_HW);
             const int hy = hp / HT_HW, hx = hp - (hp / HT_HW) * HT_HW;
             const int yy = wrap(ty0 + hy - 1, a.H), xx = wrap(tx0 + hx - 1, a.W);
-            const long long pix = ((long long)n * a.H + yy) * a.W + xx;
-            cp_async16(X + hp * CV_LD + part * 8, a.x + pix * a.xC + a.xoff + ci0 + part * 8, true);
+            cp_async16(X + hp * CV_LD + part * 8,
+                       a.x + act_at((long long)n * a.H + yy, xx, a.xoff + ci0 + part * 8, a.xC, a.W), true);
         }
     };
 
@@ -631,121 +646,99 @@ __global__ void __launch_bounds__(256) k_sum_splits_wide(const float* __restrict
     if (threadIdx.x == 0) out[i] = red[0];
 }
 
-// bias gradient partials: part[block][co] = sum over the block's pixels of g[p][co]
-__global__ void __launch_bounds__(256) k_bias_partial(const bf16* __restrict__ g, int gC, int goff, int Cout,
-                                                       int M, int rows_per_block, float* __restrict__ part) {
-    __shared__ float red[256];
-    const int groups = 256 / Cout;
-    const int c = threadIdx.x % Cout, grp = threadIdx.x / Cout;
-    const int p0 = blockIdx.x * rows_per_block, p1 = min(p0 + rows_per_block, M);
-    float s = 0.0f;
-    if (grp < groups)
-        for (int p = p0 + grp; p < p1; p += groups) s += __bfloat162float(g[(long long)p * gC + goff + c]);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x < Cout) {
-        float t = 0.0f;
-        for (int k = 0; k < groups; ++k) t += red[k * Cout + threadIdx.x];
-        part[(long long)blockIdx.x * Cout + threadIdx.x] = t;
-    }
-}
-
 // ------------------------------------------------------ element-wise parts
-// network input: 3 float32 planes -> BF16 pixels of 32 channels (zero padded)
-__global__ void k_input(const float* __restrict__ in, long long P, bf16* __restrict__ x0) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        __align__(16) bf16 v[32];
+// network input: 3 float32 planes [P][3] (pixel-major) -> BF16, 32 channels
+// (zero padded); one thread per (row, channel group, x), x fastest
+__global__ void k_input(const float* __restrict__ in, long long rows, int W, bf16* __restrict__ x0) {
+    const long long total = rows * 4 * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W);
+        const long long t = i / W;
+        const int g = (int)(t % 4);
+        const long long p = (t / 4) * W + x;
+        float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (g == 0)
 #pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = __float2bfloat16_rn(c < 3 ? in[p * 3 + c] : 0.0f);
-        uint4* dst = reinterpret_cast<uint4*>(x0 + p * 32);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(v)[k];
+            for (int c = 0; c < 3; ++c) f[c] = in[p * 3 + c];
+        *reinterpret_cast<uint4*>(x0 + i * 8) = pack8(f);  // act_at(row, x, 8 g, 32, W) = 8 i
     }
 }
 
-// 2x2 average pool of a view (H, W: input size) into a dense [N][H/2][W/2][C]
+// 2x2 average pool of a view (H, W: input size) into a dense tensor of
+// N x H/2 x W/2 pixels and C channels; one thread per output (row, group, x)
 __global__ void k_pool(const bf16* __restrict__ s, int sC, int soff, int C, int N, int H, int W,
                        bf16* __restrict__ out) {
     const int C8 = C / 8, H2 = H / 2, W2 = W / 2;
-    const long long total = (long long)N * H2 * W2 * C8;
+    const long long total = (long long)N * H2 * C8 * W2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c8 = (int)(i % C8);
-        const long long op = i / C8;
-        const int x = (int)(op % W2);
-        const long long t = op / W2;
-        const int y = (int)(t % H2);
-        const int n = (int)(t / H2);
+        const int x = (int)(i % W2);
+        const long long t = i / W2;
+        const int c8 = (int)(t % C8);
+        const long long row = t / C8;  // n H2 + y
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const long long ip = ((long long)n * H + 2 * y + dy) * W + 2 * x + dx;
                 float f[8];
-                unpack8(*reinterpret_cast<const uint4*>(s + ip * sC + soff + c8 * 8), f);
+                unpack8(*reinterpret_cast<const uint4*>(s + act_at(2 * row + dy, 2 * x + dx, soff + c8 * 8, sC, W)), f);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) acc[k] += f[k];
             }
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] *= 0.25f;
-        *reinterpret_cast<uint4*>(out + op * C + c8 * 8) = pack8(acc);
+        *reinterpret_cast<uint4*>(out + i * 8) = pack8(acc);  // act_at(row, x, 8 c8, C, W2) = 8 i
     }
 }
 
-// gradient through nearest upsampling: out[n][y][x][c] (coarse, dense) =
-// (sum of the 2x2 fine block of g) * (mask at fine (2y, 2x) > 0)
+// gradient through nearest upsampling: out (coarse, dense, C channels) at
+// (y, x) = (sum of the 2x2 fine block of g) * (mask at fine (2y, 2x) > 0)
 __global__ void k_up_bwd(const bf16* __restrict__ g, int gC, int goff, const bf16* __restrict__ mask, int mC,
                          int moff, int C, int N, int H, int W, bf16* __restrict__ out) {
     const int C8 = C / 8, H2 = H / 2, W2 = W / 2;
-    const long long total = (long long)N * H2 * W2 * C8;
+    const long long total = (long long)N * H2 * C8 * W2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c8 = (int)(i % C8);
-        const long long op = i / C8;
-        const int x = (int)(op % W2);
-        const long long t = op / W2;
-        const int y = (int)(t % H2);
-        const int n = (int)(t / H2);
+        const int x = (int)(i % W2);
+        const long long t = i / W2;
+        const int c8 = (int)(t % C8);
+        const long long row = t / C8;  // n H2 + y
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const long long ip = ((long long)n * H + 2 * y + dy) * W + 2 * x + dx;
                 float f[8];
-                unpack8(*reinterpret_cast<const uint4*>(g + ip * gC + goff + c8 * 8), f);
+                unpack8(*reinterpret_cast<const uint4*>(g + act_at(2 * row + dy, 2 * x + dx, goff + c8 * 8, gC, W)), f);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) acc[k] += f[k];
             }
-        const long long mp = ((long long)n * H + 2 * y) * W + 2 * x;
         float mk[8];
-        unpack8(*reinterpret_cast<const uint4*>(mask + mp * mC + moff + c8 * 8), mk);
+        unpack8(*reinterpret_cast<const uint4*>(mask + act_at(2 * row, 2 * x, moff + c8 * 8, mC, W)), mk);
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = mk[k] > 0.0f ? acc[k] : 0.0f;
-        *reinterpret_cast<uint4*>(out + op * C + c8 * 8) = pack8(acc);
+        *reinterpret_cast<uint4*>(out + i * 8) = pack8(acc);
     }
 }
 
-// skip gradient: out[p][c] (fine, dense) = (gp[parent(p)][c] / 4 + gcat[p][c]) * (s[p][c] > 0)
+// skip gradient: out (fine, dense, C channels) at p =
+// (gp[parent(p)] / 4 + gcat[p]) * (s[p] > 0), gp coarse dense with C channels
 __global__ void k_skip_bwd(const bf16* __restrict__ gp, const bf16* __restrict__ gcat, int gC, int goff,
                            const bf16* __restrict__ s, int sC, int soff, int C, int N, int H, int W,
                            bf16* __restrict__ out) {
     const int C8 = C / 8;
-    const long long total = (long long)N * H * W * C8;
+    const long long total = (long long)N * H * C8 * W;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c8 = (int)(i % C8);
-        const long long p = i / C8;
-        const int x = (int)(p % W);
-        const long long t = p / W;
-        const int y = (int)(t % H);
-        const int n = (int)(t / H);
-        const long long pp = ((long long)n * (H / 2) + y / 2) * (W / 2) + x / 2;
+        const int x = (int)(i % W);
+        const long long t = i / W;
+        const int c8 = (int)(t % C8);
+        const long long row = t / C8;  // n H + y; its parent row is row / 2 (H even)
         float a[8], b[8], m[8];
-        unpack8(*reinterpret_cast<const uint4*>(gp + pp * C + c8 * 8), a);
-        unpack8(*reinterpret_cast<const uint4*>(gcat + p * gC + goff + c8 * 8), b);
-        unpack8(*reinterpret_cast<const uint4*>(s + p * sC + soff + c8 * 8), m);
+        unpack8(*reinterpret_cast<const uint4*>(gp + act_at(row / 2, x / 2, c8 * 8, C, W / 2)), a);
+        unpack8(*reinterpret_cast<const uint4*>(gcat + act_at(row, x, goff + c8 * 8, gC, W)), b);
+        unpack8(*reinterpret_cast<const uint4*>(s + act_at(row, x, soff + c8 * 8, sC, W)), m);
 #pragma unroll
         for (int k = 0; k < 8; ++k) a[k] = m[k] > 0.0f ? 0.25f * a[k] + b[k] : 0.0f;
-        *reinterpret_cast<uint4*>(out + p * C + c8 * 8) = pack8(a);
+        *reinterpret_cast<uint4*>(out + i * 8) = pack8(a);
     }
 }
 
@@ -753,13 +746,15 @@ __global__ void k_skip_bwd(const bf16* __restrict__ gp, const bf16* __restrict__
 // y[p][j] = sum_c Wh[j][c] h[p][c] + bh[j], j = 0, 1 (FP32 weights)
 template <int C>
 __global__ void k_head_fwd(const bf16* __restrict__ h, const float* __restrict__ Wh, const float* __restrict__ bh,
-                           long long P, float* __restrict__ y) {
+                           long long P, int W, float* __restrict__ y) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         float y0 = bh[0], y1 = bh[1];
+        const long long row = p / W;
+        const int x = (int)(p - row * W);
 #pragma unroll
         for (int c8 = 0; c8 < C / 8; ++c8) {
             float f[8];
-            unpack8(*reinterpret_cast<const uint4*>(h + p * C + c8 * 8), f);
+            unpack8(*reinterpret_cast<const uint4*>(h + act_at(row, x, c8 * 8, C, W)), f);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 y0 += Wh[c8 * 8 + k] * f[k];
@@ -777,7 +772,7 @@ __global__ void k_head_fwd(const bf16* __restrict__ h, const float* __restrict__
 template <int C>
 __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ h, const float* __restrict__ Wh,
                                                    const float* __restrict__ bh, const float* __restrict__ tgt,
-                                                   long long P, int rows_per_block, float inv_count2,
+                                                   long long P, int W, int rows_per_block, float inv_count2,
                                                    bf16* __restrict__ gh, float* __restrict__ pw,
                                                    double* __restrict__ pl) {
     constexpr int NV = 2 * C + 2;
@@ -791,10 +786,12 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ h, co
     const long long p1 = min(p0 + rows_per_block, P);
     for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         float hv[C];
+        const long long row = p / W;
+        const int x = (int)(p - row * W);
 #pragma unroll
         for (int c8 = 0; c8 < C / 8; ++c8) {
             float f[8];
-            unpack8(*reinterpret_cast<const uint4*>(h + p * C + c8 * 8), f);
+            unpack8(*reinterpret_cast<const uint4*>(h + act_at(row, x, c8 * 8, C, W)), f);
 #pragma unroll
             for (int k = 0; k < 8; ++k) hv[c8 * 8 + k] = f[k];
         }
@@ -821,7 +818,7 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* __restrict__ h, co
             float f[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) f[k] = gv[c8 * 8 + k];
-            *reinterpret_cast<uint4*>(gh + p * C + c8 * 8) = pack8(f);
+            *reinterpret_cast<uint4*>(gh + act_at(row, x, c8 * 8, C, W)) = pack8(f);
         }
     }
     // warp then block reduction in a fixed order

@@ -14,7 +14,9 @@
 // with the pixels of a halo row 16 bytes apart inside each 8-channel group:
 //   group g (8 channels), halo row r, slot h -> g * TC_KG + (r * TC_HROW + h) * 16
 // where slots 8 .. 135 hold the segment's 128 pixels (written by one TMA
-// tensor copy per group and row, 128-byte aligned) and slots 7 and 136 the
+// tensor copy per group and row, 128-byte aligned; in the activation layout
+// of act_at the source is one contiguous 2 KB block, which the tensor map
+// moves as 16 rows of 128 bytes) and slots 7 and 136 the
 // wrapped neighbours left and right (plain 16-byte copies: circular padding).
 // The A operand of tap (dy, dx) is then the same bytes seen through a matrix
 // descriptor that starts at halo row dy + 1, slot 7 + dx + 1 (core matrices of
@@ -29,18 +31,23 @@
 //              byte count and issues the 12 TMA tensor copies (4 channel
 //              groups x 3 rows, cp.async.bulk.tensor, completion by
 //              transaction count); lanes 0..23 copy the 24 wrapped edge
-//              pixels and arrive once their copies have landed (after
-//              fence.proxy.async); the ring is `stages` deep (up to 8);
-//   warp 5     one thread issues the 9 x (32 / 16) MMAs of a stage into the
+//              pixels (cp.async), each arriving on the same barrier when it
+//              lands (cp.async.mbarrier.arrive; the MMA thread issues the
+//              proxy fence after its wait); the ring is `stages` deep (up
+//              to 8) and the producer never waits on its own copies;
+//   warp 9     runs the MMA loop warp-wide; one elected lane issues the
+//              9 x (32 / 16) MMAs of a stage into the
 //              tile's accumulator and tcgen05.commit's the stage's "empty"
 //              mbarrier; after the tile's last chunk it commits "acc full";
-//   warps 1-4  epilogue: wait "acc full", tcgen05.ld the tile (TMEM lane =
+//   warps 1-8  epilogue, two groups of four warps taking alternate tiles:
+//              wait "acc full", tcgen05.ld the tile (TMEM lane =
 //              pixel, column = output channel), add the bias, apply ReLU and
 //              the gradient mask, round to BF16 and store (or store each
 //              pixel to its 2 x 2 block for the upsampling), then arrive on
 //              "acc empty".
-// Two accumulator buffers (2 N TMEM columns, allocated once per CTA) let the
-// MMAs of tile t + 1 run while the epilogue drains tile t.
+// TC_NACC accumulator buffers (TC_NACC x N TMEM columns, allocated once per
+// CTA) let the MMAs of the next tiles run while the epilogue drains earlier
+// ones; the bias sits in shared memory.
 //
 // Every mbarrier wait is bounded (about one second); a wait that gives up
 // sets bit LB_ERR_TIMEOUT (6) of *a.err and the CTA winds down: no role
@@ -64,15 +71,17 @@ constexpr int TC_ASTRIDE = (TC_KC / 8) * TC_KG; // bytes of one halo stage (2764
 constexpr int TC_TMA_BYTES = (TC_KC / 8) * 3 * TC_M * 16;  // bytes the 12 tensor copies deliver
 constexpr int TC_EDGES = (TC_KC / 8) * 3 * 2;   // wrapped edge pixels per stage (24)
 constexpr int TC_MAX_STAGES = 8;
-constexpr int TC_THREADS = 192;                 // producer warp, 4 epilogue warps, MMA warp
+constexpr int TC_THREADS = 320;                 // producer warp, 2 x 4 epilogue warps, MMA warp
+constexpr int TC_NACC = 4;                      // accumulator buffers in TMEM
+constexpr int TC_MMA_WARP = 9;
 constexpr int TC_MAX_WBYTES = 100 * 1024;       // resident weights per layer
 constexpr size_t TC_SMEM_LIMIT = 232448;        // dynamic shared memory per CTA
 constexpr long long TC_WAIT = 2000000000LL;     // bounded-wait limit (clock cycles)
 
 __host__ __device__ constexpr size_t tc_wbytes(int N, int Cin) { return (size_t)9 * N * Cin * 2; }
 __host__ __device__ constexpr size_t tc_fixed_bytes(int N, int Cin) {
-    // weights (rounded to 1 KB), barriers + TMEM slot + flag, alignment slack
-    return (tc_wbytes(N, Cin) + 1023) / 1024 * 1024 + 256 + 1024;
+    // weights (rounded to 1 KB), bias, barriers + TMEM slot + flag, alignment slack
+    return (tc_wbytes(N, Cin) + 1023) / 1024 * 1024 + 1024 + 512 + 1024;
 }
 // ring depth that fits the shared memory next to the layer's weights
 __host__ __device__ constexpr int tc_stages(int N, int Cin) {
@@ -87,21 +96,6 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int N, int Cin) {
 __host__ __device__ constexpr bool tc_layer_ok(int N, int Cin) {
     return (N == 32 || N == 64 || N == 96) && Cin % TC_KC == 0 && tc_wbytes(N, Cin) <= (size_t)TC_MAX_WBYTES &&
            tc_stages(N, Cin) >= 3;
-}
-
-__device__ __forceinline__ void tc_bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// TMA tensor copy of one box of a 4-D tensor map into shared memory, completion
-// counted on an mbarrier in bytes
-__device__ __forceinline__ void tc_tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                             uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ void tc_bar_init(uint64_t* bar, uint32_t count) {
@@ -124,6 +118,99 @@ __device__ __forceinline__ bool tc_bar_wait(uint64_t* bar, uint32_t parity) {
         if (clock64() - t0 > TC_WAIT) return false;
     return true;
 }
+// One stage of the halo, issued by one elected lane of the (converged)
+// producer warp: arm the stage's barrier with TC_TMA_BYTES, then the 12 tensor
+// copies (channel group g = 0..3 of the chunk starting at group cg0, halo row
+// hr = 0..2 of image rows r0, r1, r2; 128 pixels from 8 xb) into the stage at
+// st: group g, row hr -> st + g TC_KG + (hr TC_HROW + TC_BODY) 16.
+static_assert(TC_KC == 32 && TC_KG == 6912 && TC_HROW == 144 && TC_BODY == 8, "offsets below");
+__device__ __forceinline__ void tc_produce_stage(const CUtensorMap* map, uint32_t st, uint32_t bar, int xb, int cg0,
+                                                 int r0, int r1, int r2) {
+    asm volatile(
+        "{\n"
+        ".reg .pred e;\n .reg .b32 el, d, c, z;\n"
+        "mov.u32 z, 0;\n"
+        "elect.sync el|e, 0xffffffff;\n"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n"
+        "add.u32 d, %1, 128;\n add.u32 c, %5, 0;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %6}], [%2];\n"
+        "add.u32 d, %1, 2432;\n add.u32 c, %5, 0;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %7}], [%2];\n"
+        "add.u32 d, %1, 4736;\n add.u32 c, %5, 0;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %8}], [%2];\n"
+        "add.u32 d, %1, 7040;\n add.u32 c, %5, 1;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %6}], [%2];\n"
+        "add.u32 d, %1, 9344;\n add.u32 c, %5, 1;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %7}], [%2];\n"
+        "add.u32 d, %1, 11648;\n add.u32 c, %5, 1;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %8}], [%2];\n"
+        "add.u32 d, %1, 13952;\n add.u32 c, %5, 2;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %6}], [%2];\n"
+        "add.u32 d, %1, 16256;\n add.u32 c, %5, 2;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %7}], [%2];\n"
+        "add.u32 d, %1, 18560;\n add.u32 c, %5, 2;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %8}], [%2];\n"
+        "add.u32 d, %1, 20864;\n add.u32 c, %5, 3;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %6}], [%2];\n"
+        "add.u32 d, %1, 23168;\n add.u32 c, %5, 3;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %7}], [%2];\n"
+        "add.u32 d, %1, 25472;\n add.u32 c, %5, 3;\n"
+        "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [d], [%0, {z, %4, c, %8}], [%2];\n"
+        "}\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(st), "r"(bar), "r"((uint32_t)TC_TMA_BYTES), "r"(xb), "r"(cg0), "r"(r0), "r"(r1), "r"(r2)
+        : "memory");
+}
+
+// arrive on an mbarrier once all of this thread's prior cp.async copies have
+// landed (the arrival counts towards the barrier's expected count)
+__device__ __forceinline__ void tc_cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// nine MMAs into accumulator d, issued by one elected lane of the (converged)
+// warp: view i has the descriptors {alo[i], ahi} and {blo[i], bhi}; the first
+// accumulates onto d iff acc0 != 0, the rest always
+__device__ __forceinline__ void tc_mma9(uint32_t d, uint32_t idesc, const uint32_t (&alo)[9], uint32_t ahi,
+                                        const uint32_t (&blo)[9], uint32_t bhi, uint32_t acc0) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p0, p1, e;\n"
+        ".reg .b32 el;\n"
+        ".reg .b64 a0, a1, a2, a3, a4, a5, a6, a7, a8, b0, b1, b2, b3, b4, b5, b6, b7, b8;\n"
+        "setp.ne.b32 p0, %22, 0;\n"
+        "setp.eq.b32 p1, %1, %1;\n"
+        "elect.sync el|e, 0xffffffff;\n"
+        "mov.b64 a0, {%2, %11};\n mov.b64 a1, {%3, %11};\n mov.b64 a2, {%4, %11};\n"
+        "mov.b64 a3, {%5, %11};\n mov.b64 a4, {%6, %11};\n mov.b64 a5, {%7, %11};\n"
+        "mov.b64 a6, {%8, %11};\n mov.b64 a7, {%9, %11};\n mov.b64 a8, {%10, %11};\n"
+        "mov.b64 b0, {%12, %21};\n mov.b64 b1, {%13, %21};\n mov.b64 b2, {%14, %21};\n"
+        "mov.b64 b3, {%15, %21};\n mov.b64 b4, {%16, %21};\n mov.b64 b5, {%17, %21};\n"
+        "mov.b64 b6, {%18, %21};\n mov.b64 b7, {%19, %21};\n mov.b64 b8, {%20, %21};\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, b0, %1, p0;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a4, b4, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a5, b5, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a6, b6, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a7, b7, %1, p1;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a8, b8, %1, p1;\n"
+        "}\n" ::"r"(d),
+        "r"(idesc), "r"(alo[0]), "r"(alo[1]), "r"(alo[2]), "r"(alo[3]), "r"(alo[4]), "r"(alo[5]), "r"(alo[6]),
+        "r"(alo[7]), "r"(alo[8]), "r"(ahi), "r"(blo[0]), "r"(blo[1]), "r"(blo[2]), "r"(blo[3]), "r"(blo[4]),
+        "r"(blo[5]), "r"(blo[6]), "r"(blo[7]), "r"(blo[8]), "r"(bhi), "r"(acc0)
+        : "memory");
+}
+
+// tcgen05.commit from one elected lane of the (converged) warp: the mbarrier
+// receives one arrival once every MMA issued before it has completed
+__device__ __forceinline__ void tc_commit_one(uint64_t* bar) {
+    asm volatile(
+        "{\n .reg .pred e;\n .reg .b32 el;\n elect.sync el|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
 // shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
 // byte offsets, each >> 4 in 14 bits; descriptor version 1 (bit 46); no swizzle
 __device__ __forceinline__ uint64_t tc_mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -138,7 +225,7 @@ __host__ __device__ constexpr uint32_t tc_idesc_n() {
 }
 template <int N>
 __host__ __device__ constexpr uint32_t tc_tmem_cols() {
-    return 2 * N <= 64 ? 64u : (2 * N <= 128 ? 128u : 256u);
+    return TC_NACC * N <= 64 ? 64u : (TC_NACC * N <= 128 ? 128u : (TC_NACC * N <= 256 ? 256u : 512u));
 }
 
 template <int N>
@@ -150,18 +237,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const size_t wround = (tc_wbytes(N, Cin) + 1023) / 1024 * 1024;
     uint8_t* sW = base;                       // [9][N/8][Cin/8] core matrices
     uint8_t* sA = base + wround;              // [stages][TC_ASTRIDE], 1024-byte aligned
-    uint64_t* full = reinterpret_cast<uint64_t*>(sA + (size_t)stages * TC_ASTRIDE);
+    float* sBias = reinterpret_cast<float*>(sA + (size_t)stages * TC_ASTRIDE);  // [N <= 96]
+    uint64_t* full = reinterpret_cast<uint64_t*>(sBias + 128);
     uint64_t* empty = full + TC_MAX_STAGES;
-    uint64_t* accf = empty + TC_MAX_STAGES;   // [2]
-    uint64_t* acce = accf + 2;                // [2]
-    uint64_t* mdone = acce + 2;               // the MMA thread's last commit
+    uint64_t* accf = empty + TC_MAX_STAGES;   // [TC_NACC]
+    uint64_t* acce = accf + TC_NACC;          // [TC_NACC]
+    uint64_t* mdone = acce + TC_NACC;         // the MMA thread's last commit
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mdone + 1);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = a.H, W = a.W;
     const int segs = W / TC_M;
-    const long long ntiles = (long long)a.N * H * segs;
+    const int ntiles = a.N * H * segs;  // the host keeps this below 2^31
     const int nchunks = Cin / TC_KC;
     const int SBO_W = (Cin / 8) * 128;                  // weights: 8-row (output channel) groups
     const uint32_t wplane = (uint32_t)N * (uint32_t)Cin * 2u;
@@ -171,9 +259,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_bar_init(&full[s], 1 + TC_EDGES);     // the armed byte count + the edge copies
             tc_bar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < TC_NACC; ++b) {
             tc_bar_init(&accf[b], 1);
-            tc_bar_init(&acce[b], 128);
+            tc_bar_init(&acce[b], 128);    // the four warps of the epilogue group of the tile
         }
         tc_bar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -193,6 +281,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* d = sW + (size_t)tap * wplane + (co >> 3) * SBO_W + k8 * 128 + (co & 7) * 16;
         cp_async16(d, a.w + ((long long)co * 9 + tap) * Cin + k8 * 8, true);
     }
+    for (int q = tid; q < N; q += TC_THREADS) sBias[q] = a.bias ? a.bias[q] : 0.0f;
     cp_async_commit();
     cp_async_wait<0>();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -203,23 +292,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         // ------------------------------------------------ producer warp
-        constexpr int D = 2;  // edge-copy groups in flight before their arrival
         // this lane's edge pixel: channel group g, halo row hr, side (0 left, 1 right)
         const int eg = lane / 6, ehr = (lane % 6) >> 1, eside = lane & 1;
         const bool edge = lane < TC_EDGES;
-        long long j = 0;
-        for (long long tile = blockIdx.x; tile < ntiles && !*s_abort; tile += gridDim.x) {
-            const int seg = (int)(tile % segs);
-            const long long r = tile / segs;
-            const int y = (int)(r % H);
-            const int n = (int)(r / H);
+        int j = 0, s = 0;                                // jobs issued, their stage
+        uint32_t ph = 0;                                 // (j / stages) & 1
+        // (the abort flag is read once per warp: every decision here is warp-uniform)
+        for (int tile = blockIdx.x; tile < ntiles && __shfl_sync(0xffffffffu, *s_abort, 0) == 0;
+             tile += gridDim.x) {
+            const int seg = tile % segs;
+            const int r = tile / segs;
+            const int y = r % H;
+            const int n = r / H;
             const int x0 = seg * TC_M;
+            const int rr0 = n * H + wrap(y - 1, H), rr1 = n * H + y, rr2 = n * H + wrap(y + 1, H);
             bool stop = false;
-            for (int c = 0; c < nchunks; ++c, ++j) {
-                const int s = (int)(j % stages);
+            for (int c = 0; c < nchunks; ++c) {
                 // one decision per warp (its lanes poll the barrier independently)
-                if (j >= stages &&
-                    !__all_sync(0xffffffffu, tc_bar_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1)))) {
+                if (j >= stages && !__all_sync(0xffffffffu, tc_bar_wait(&empty[s], ph ^ 1u))) {
                     if (lane == 0) {
                         *s_abort = 1;
                         if (a.err) atomicOr(a.err, 1 << 6);
@@ -229,124 +319,124 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 uint8_t* st = sA + (size_t)s * TC_ASTRIDE;
                 const int cbase = a.xoff + c * TC_KC;
-                if (lane == 0) {
-                    tc_bar_arrive_tx(&full[s], (uint32_t)TC_TMA_BYTES);
-#pragma unroll
-                    for (int g = 0; g < TC_KC / 8; ++g)
-#pragma unroll
-                        for (int hr = 0; hr < 3; ++hr)
-                            tc_tma_load4(st + g * TC_KG + (hr * TC_HROW + TC_BODY) * 16, &xmap, cbase + g * 8, x0,
-                                         wrap(y + hr - 1, H), n, &full[s]);
-                }
+                tc_produce_stage(&xmap, smem_addr(st), smem_addr(&full[s]), x0 / 8, cbase / 8, rr0, rr1, rr2);
                 if (edge) {
+                    // the copy arrives on the stage's barrier by itself once it has landed
                     const int yy = wrap(y + ehr - 1, H);
                     const int xx = eside ? wrap(x0 + TC_M, W) : wrap(x0 - 1, W);
-                    const long long pix = ((long long)n * H + yy) * W + xx;
                     cp_async16(st + eg * TC_KG + (ehr * TC_HROW + (eside ? TC_BODY + TC_M : TC_BODY - 1)) * 16,
-                               a.x + pix * a.xC + cbase + eg * 8, true);
+                               a.x + act_at((long long)n * H + yy, xx, cbase + eg * 8, a.xC, W), true);
+                    tc_cp_async_arrive(&full[s]);
                 }
-                cp_async_commit();
-                if (j >= D) {
-                    cp_async_wait<D>();
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (edge) tc_bar_arrive(&full[(int)((j - D) % stages)]);
+                ++j;
+                if (++s == stages) {
+                    s = 0;
+                    ph ^= 1u;
                 }
             }
             if (stop) break;
         }
-        // the last jobs' edge copies, then their arrivals; then every tensor
-        // copy issued has landed (waits with the default limit) before leaving
+        // every copy issued has landed before leaving (the full barriers of
+        // the last jobs complete only then; waits with the default limit)
         cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (edge)
-            for (long long k = (j > D ? j - D : 0); k < j; ++k) tc_bar_arrive(&full[(int)(k % stages)]);
         if (lane == 0)
-            for (long long k = (j > stages ? j - stages : 0); k < j; ++k)
-                (void)tc_bar_wait(&full[(int)(k % stages)], (uint32_t)((k / stages) & 1));
+            for (int k = (j > stages ? j - stages : 0); k < j; ++k)
+                (void)tc_bar_wait(&full[k % stages], (uint32_t)((k / stages) & 1));
         __syncwarp();
-    } else if (warp == 5) {
-        // ------------------------------------------------ MMA issue (one thread)
-        if (lane == 0) {
-            constexpr uint32_t IDESC = tc_idesc_n<N>();
-            const uint32_t aW = smem_addr(sW);
-            long long j = 0, t = 0;
-            bool ok = true;
-            for (long long tile = blockIdx.x; tile < ntiles && ok && !*s_abort; tile += gridDim.x, ++t) {
-                const int b = (int)(t & 1);
-                if (t >= 2 && !tc_bar_wait(&acce[b], (uint32_t)(((t / 2) - 1) & 1))) {
+    } else if (warp == TC_MMA_WARP) {
+        // ------------------------------------------------ MMA issue
+        // The whole warp runs this loop (warp-uniform control flow keeps the
+        // descriptors in the uniform datapath); one elected lane issues each
+        // MMA and commit.  The low word (start address >> 4) of every view
+        // of a stage is a constant offset from the stage's base; the high
+        // words (LBO, SBO, version) never change.
+        constexpr uint32_t IDESC = tc_idesc_n<N>();
+        const uint64_t da0 = tc_mdesc(smem_addr(sA) + (uint32_t)((TC_BODY - 1) * 16), TC_KG, 128);
+        const uint64_t db0 = tc_mdesc(smem_addr(sW), 128, (uint32_t)SBO_W);
+        const uint32_t ahi = (uint32_t)(da0 >> 32), bhi = (uint32_t)(db0 >> 32);
+        const uint32_t wp16 = wplane >> 4;
+        int s = 0, b = 0, t = 0;
+        uint32_t fph = 0, rnd = 0;  // (job / stages) & 1, (t / TC_NACC) & 1
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok && __shfl_sync(0xffffffffu, *s_abort, 0) == 0;
+             tile += gridDim.x, ++t) {
+            if (t >= TC_NACC && !__all_sync(0xffffffffu, tc_bar_wait(&acce[b], rnd ^ 1u))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)(b * N);
+            for (int c = 0; c < nchunks; ++c) {
+                // views of tap (dy, dx): halo row dy, slot TC_BODY - 1 + dx; kk = 1 is TC_KG * 2 bytes on
+                const uint32_t a_lo = (uint32_t)da0 + (uint32_t)s * (uint32_t)(TC_ASTRIDE >> 4);
+                const uint32_t b_lo = (uint32_t)db0 + (uint32_t)c * (uint32_t)((TC_KC / 8) * 128 >> 4);
+                uint32_t a0[9], a1[9], b0[9], b1[9];
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    a0[tap] = a_lo + (uint32_t)((tap / 3) * TC_HROW + tap % 3);
+                    a1[tap] = a0[tap] + (uint32_t)(2 * TC_KG >> 4);
+                    b0[tap] = b_lo + (uint32_t)tap * wp16;
+                    b1[tap] = b0[tap] + 16u;
+                }
+                if (!__all_sync(0xffffffffu, tc_bar_wait(&full[s], fph))) {
                     ok = false;
                     break;
                 }
+                // the edge pixels were written by cp.async (generic proxy), the
+                // MMAs read the stage through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t dacc = tmem + (uint32_t)(b * N);
-                for (int c = 0; c < nchunks; ++c, ++j) {
-                    const int s = (int)(j % stages);
-                    if (!tc_bar_wait(&full[s], (uint32_t)((j / stages) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t aA = smem_addr(sA + (size_t)s * TC_ASTRIDE);
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;  // halo row and column offset of the view
-#pragma unroll
-                        for (int kk = 0; kk < TC_KC / 16; ++kk) {
-                            const uint64_t da = tc_mdesc(
-                                aA + (uint32_t)(2 * kk * TC_KG + (dy * TC_HROW + TC_BODY - 1 + dx) * 16), TC_KG, 128);
-                            const uint64_t db = tc_mdesc(
-                                aW + (uint32_t)tap * wplane + (uint32_t)((c * (TC_KC / 8) + 2 * kk) * 128), 128,
-                                (uint32_t)SBO_W);
-                            const uint32_t accum = (c > 0 || tap > 0 || kk > 0) ? 1u : 0u;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                                "l"(da), "l"(db), "r"(IDESC), "r"(accum)
-                                : "memory");
-                        }
-                    }
-                    // the stage is free again once these MMAs have read it
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                            smem_addr(&empty[s]))
-                        : "memory");
+                tc_mma9(dacc, IDESC, a0, ahi, b0, bhi, c > 0 ? 1u : 0u);
+                tc_mma9(dacc, IDESC, a1, ahi, b1, bhi, 1u);
+                tc_commit_one(&empty[s]);  // the stage is free again once these MMAs have read it
+                if (++s == stages) {
+                    s = 0;
+                    fph ^= 1u;
                 }
-                if (!ok) break;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_addr(&accf[b]))
-                             : "memory");
             }
-            if (!ok) {
-                *s_abort = 1;
-                if (a.err) atomicOr(a.err, 1 << 6);
+            if (!ok) break;
+            tc_commit_one(&accf[b]);
+            if (++b == TC_NACC) {
+                b = 0;
+                rnd ^= 1u;
             }
-            // every MMA this thread issued has completed before TMEM is released
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(mdone))
-                         : "memory");
-            if (!tc_bar_wait(mdone, 0u) && a.err) atomicOr(a.err, 1 << 6);
         }
-        __syncwarp();
+        if (!ok && lane == 0) {
+            *s_abort = 1;
+            if (a.err) atomicOr(a.err, 1 << 6);
+        }
+        // every MMA issued has completed before TMEM is released
+        tc_commit_one(mdone);
+        if (!__all_sync(0xffffffffu, tc_bar_wait(mdone, 0u)) && lane == 0 && a.err) atomicOr(a.err, 1 << 6);
     } else {
-        // ------------------------------------------------ epilogue (warps 1-4)
+        // ------------------------------------------------ epilogue (warps 1-8)
+        // two groups of four warps take alternate tiles, so that one group's
+        // loads and stores overlap the other's; the k-th tile of group grp is
+        // the CTA's tile t = grp + 2 k: buffer t % 4 = grp + 2 (k % 2), phase
+        // (t / 4) % 2 = (k / 2) % 2
+        const int grp = (warp - 1) >> 2;         // 0: warps 1-4, 1: warps 5-8
         const int q = warp & 3;                  // TMEM lanes 32 q .. 32 q + 31
         const int px = q * 32 + lane;            // pixel of the tile
-        long long t = 0;
-        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
-            const int b = (int)(t & 1);
+        int k = 0;
+        for (int tile = blockIdx.x + grp * (int)gridDim.x; tile < ntiles; tile += 2 * (int)gridDim.x, ++k) {
+            const int b = grp + 2 * (k & 1);
+            const uint32_t rnd = (uint32_t)(k >> 1) & 1u;
+            const int seg = tile % segs;
+            const long long row = tile / segs;   // n H + y
+            const int x = seg * TC_M + px;
+            // the gradient mask of this pixel, loaded before the accumulator is ready
+            uint4 mraw[N / 8];
+            if (a.mask)
+#pragma unroll
+                for (int kk = 0; kk < N / 8; ++kk)
+                    mraw[kk] = __ldg(reinterpret_cast<const uint4*>(a.mask + act_at(row, x, a.moff + 8 * kk, a.mC, W)));
             // one decision per warp (the TMEM loads below are warp-wide)
-            if (!__all_sync(0xffffffffu, tc_bar_wait(&accf[b], (uint32_t)((t / 2) & 1)))) {
+            if (!__all_sync(0xffffffffu, tc_bar_wait(&accf[b], rnd))) {
                 *s_abort = 1;
                 if (a.err) atomicOr(a.err, 1 << 6);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int seg = (int)(tile % segs);
-            const long long r = tile / segs;
-            const int y = (int)(r % H);
-            const int n = (int)(r / H);
-            const int x = seg * TC_M + px;
-            const long long m = ((long long)n * H + y) * W + x;
 #pragma unroll
             for (int cc = 0; cc < N; cc += 32) {
                 uint32_t v[32];
@@ -366,33 +456,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int co = cc + j8 * 8;
                     float f8[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) f8[k] = __uint_as_float(v[j8 * 8 + k]);
-                    if (a.bias) {
-                        const float4 b0 = *reinterpret_cast<const float4*>(a.bias + co);
-                        const float4 b1 = *reinterpret_cast<const float4*>(a.bias + co + 4);
-                        f8[0] += b0.x; f8[1] += b0.y; f8[2] += b0.z; f8[3] += b0.w;
-                        f8[4] += b1.x; f8[5] += b1.y; f8[6] += b1.z; f8[7] += b1.w;
-                    }
+                    for (int e = 0; e < 8; ++e) f8[e] = __uint_as_float(v[j8 * 8 + e]) + sBias[co + e];
                     if (a.relu)
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) f8[k] = fmaxf(f8[k], 0.0f);
+                        for (int e = 0; e < 8; ++e) f8[e] = fmaxf(f8[e], 0.0f);
                     if (a.mask) {
                         float mk[8];
-                        unpack8(*reinterpret_cast<const uint4*>(a.mask + m * a.mC + a.moff + co), mk);
+                        unpack8(mraw[co / 8], mk);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) f8[k] = mk[k] > 0.0f ? f8[k] : 0.0f;
+                        for (int e = 0; e < 8; ++e) f8[e] = mk[e] > 0.0f ? f8[e] : 0.0f;
                     }
                     const uint4 u = pack8(f8);
                     if (!a.up) {
-                        *reinterpret_cast<uint4*>(a.y + m * a.yC + a.yoff + co) = u;
+                        *reinterpret_cast<uint4*>(a.y + act_at(row, x, a.yoff + co, a.yC, W)) = u;
                     } else {
 #pragma unroll
                         for (int uy = 0; uy < 2; ++uy)
 #pragma unroll
-                            for (int ux = 0; ux < 2; ++ux) {
-                                const long long pix = ((long long)n * 2 * H + 2 * y + uy) * (2 * W) + 2 * x + ux;
-                                *reinterpret_cast<uint4*>(a.y + pix * a.yC + a.yoff + co) = u;
-                            }
+                            for (int ux = 0; ux < 2; ++ux)
+                                *reinterpret_cast<uint4*>(a.y + act_at(2 * row + uy, 2 * x + ux, a.yoff + co, a.yC,
+                                                                       2 * W)) = u;
                     }
                 }
             }
