@@ -27,6 +27,7 @@
 #include "unet.h"
 #include "unet_kernels.cuh"
 #include "unet_tc.cuh"
+#include "unet_tcs.cuh"
 
 namespace lbgb {
 lb_status record_error(lb_status st, const char* msg);
@@ -111,6 +112,7 @@ struct un_net {
     long long nparam = 0, nq = 0;
     float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     bf16 *wb = nullptr, *wt = nullptr;
+    bf16 *wbk = nullptr, *wtk = nullptr;  // wb, wt blocked per stage of k_conv3_tcs (layers it takes)
     long long t = 0;
     int lastN = 0;
     // forward
@@ -209,16 +211,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // channel groups, N H rows), box (64, 16, 1, 1): one box is 128 pixels of one
 // channel group of one row, a contiguous 2 KB block moved as 16 rows of 128
 // bytes.  The view's first channel group is applied in the coordinates.
-bool conv_tensor_map(const bf16* x, int xC, int W, int H, int N, CUtensorMap* map) {
+bool conv_tensor_map(const bf16* x, int xC, int W, int H, int N, CUtensorMap* map, int boxw = unk::TC_M) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[4] = {64, (cuuint64_t)(W / 8), (cuuint64_t)(xC / 8), (cuuint64_t)N * H};
     const cuuint64_t strides[3] = {128, (cuuint64_t)W * 16, (cuuint64_t)xC * W * 2};
-    const cuuint32_t box[4] = {64, (cuuint32_t)unk::TC_M / 8, 1, 1};
+    const cuuint32_t box[4] = {64, (cuuint32_t)boxw / 8, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the stage images of k_conv3_tcs for weights w (a layer's copy in wb or wt)
+const bf16* blocked_of(const un_net* n, const bf16* w) {
+    if (w >= n->wb && w < n->wb + n->nq) return n->wbk + (w - n->wb);
+    if (w >= n->wt && w < n->wt + n->nq) return n->wtk + (w - n->wt);
+    return nullptr;
 }
 
 cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16* w, const float* bias, int Cout,
@@ -257,6 +266,21 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
             case 64: unk::k_conv3_tc<64><<<grid, unk::TC_THREADS, smem, n->stream>>>(a, xmap, stages); break;
             default: unk::k_conv3_tc<96><<<grid, unk::TC_THREADS, smem, n->stream>>>(a, xmap, stages); break;
         }
+        return cudaGetLastError();
+    }
+    const int NB = unk::ts_block(Cout);
+    const int segw = a.W < unk::TC_M ? a.W : unk::TC_M;
+    const bf16* wimg = blocked_of(n, w);
+    if (NB && wimg && Cin % 16 == 0 && Cout <= 384 && a.W % 16 == 0 && a.W % segw == 0 &&
+        a.H % unk::ts_rows(NB) == 0 && (M / segw) * (Cout / NB) < (1LL << 31) &&
+        conv_tensor_map(x, xC, a.W, a.H, N, &xmap, segw)) {
+        // fifth-generation tensor cores, weights streamed per 16-channel chunk
+        const long long tiles = (M / segw) / unk::ts_rows(NB) * (Cout / NB);
+        const int grid = (int)(tiles < n->sms ? tiles : n->sms);
+        if (NB == 128)
+            unk::k_conv3_tcs<128><<<grid, unk::TS_THREADS, unk::ts_smem_bytes(128), n->stream>>>(a, xmap, wimg);
+        else
+            unk::k_conv3_tcs<64><<<grid, unk::TS_THREADS, unk::ts_smem_bytes(64), n->stream>>>(a, xmap, wimg);
         return cudaGetLastError();
     }
     if (a.W % unk::HT_W == 0 && a.H % unk::HT_H == 0 && Cout % unk::HT_NT == 0) {
@@ -344,8 +368,17 @@ cudaError_t refresh_weights(un_net* n) {
     for (int k = 0; k < UN_LAYERS; ++k) {
         const Layer& L = n->L[k];
         if (L.k != 3) continue;
-        unk::k_refresh_w<<<grid_for((long long)L.cout * 9 * L.cin), 256, 0, n->stream>>>(
-            n->p + L.woff, L.cout, L.cin, n->wb + L.qoff, n->wt + L.qoff);
+        const long long nw = (long long)L.cout * 9 * L.cin;
+        unk::k_refresh_w<<<grid_for(nw), 256, 0, n->stream>>>(n->p + L.woff, L.cout, L.cin, n->wb + L.qoff,
+                                                              n->wt + L.qoff);
+        // stage images for the streamed tensor-core convolution (forward: Cout
+        // output channels; input gradient: Cin)
+        if (unk::ts_block(L.cout) && L.cin % 16 == 0)
+            unk::k_block_w<<<grid_for(nw), 256, 0, n->stream>>>(n->wb + L.qoff, L.cout, L.cin,
+                                                                unk::ts_block(L.cout), n->wbk + L.qoff);
+        if (unk::ts_block(L.cin) && L.cout % 16 == 0)
+            unk::k_block_w<<<grid_for(nw), 256, 0, n->stream>>>(n->wt + L.qoff, L.cin, L.cout,
+                                                                unk::ts_block(L.cin), n->wtk + L.qoff);
     }
     return cudaGetLastError();
 }
@@ -568,6 +601,8 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess) e = alloc(n, &n->grad, n->nparam);
     if (e == cudaSuccess) e = alloc(n, &n->wb, n->nq);
     if (e == cudaSuccess) e = alloc(n, &n->wt, n->nq);
+    if (e == cudaSuccess) e = alloc(n, &n->wbk, n->nq);
+    if (e == cudaSuccess) e = alloc(n, &n->wtk, n->nq);
     if (e == cudaSuccess) e = alloc(n, &n->x0, Pl(n, 0, N) * UN_IN_PAD);
     for (int l = 0; l < LV && e == cudaSuccess; ++l) {
         e = alloc(n, &n->a[l], Pl(n, l, N) * Cl(n, l));
@@ -617,6 +652,12 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_conv3_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_conv3_tcs<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unk::ts_smem_bytes(128));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_conv3_tcs<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unk::ts_smem_bytes(64));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::halo_smem_bytes());
