@@ -28,6 +28,7 @@
 #include "unet_kernels.cuh"
 #include "unet_tc.cuh"
 #include "unet_tcs.cuh"
+#include "unet_tcw.cuh"
 
 namespace lbgb {
 lb_status record_error(lb_status st, const char* msg);
@@ -173,6 +174,12 @@ int grid_for(long long work, int per_block = 256) {
     return (int)(b < 1 ? 1 : (b > 1 << 20 ? 1 << 20 : b));
 }
 
+// blocks of k_sum_splits for n outputs (32 per block, grid-stride beyond)
+int sum_grid(long long n) {
+    const long long b = (n + 31) / 32;
+    return (int)(b < 1 ? 1 : (b > 65536 ? 65536 : b));
+}
+
 // splits of the weight-gradient kernel for a layer at M pixels
 void wgrad_shape(const un_net* n, const Layer& L, long long M, int* MT, int* NT, int* tiles, int* splits,
                  int* cps) {
@@ -301,7 +308,57 @@ cudaError_t conv(un_net* n, const bf16* x, int xC, int xoff, int Cin, const bf16
 cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16* x, int xC, int xoff, int N, int l) {
     const Layer& L = n->L[k];
     const long long M = Pl(n, l, N);
-    if (Wl(n, l) % unk::HT_W == 0 && Hl(n, l) % unk::HT_H == 0) {
+    const long long nw = (long long)L.cout * 9 * L.cin;
+    const int NBW = unk::tw_block(L.cin);
+    const int W = Wl(n, l), H = Hl(n, l);
+    const int segw = unk::tw_segw(W);
+    CUtensorMap gmap, xmap;
+    if (L.cout % 64 == 0 && L.cout <= 384 && NBW && W % 16 == 0 && W % segw == 0 && M / segw < (1LL << 30) &&
+        conv_tensor_map(g, gC, W, H, N, &gmap, segw) && conv_tensor_map(x, xC, W, H, N, &xmap, segw)) {
+        // fifth-generation tensor cores: (output block, input block, kernel row, pixel split) per CTA
+        const int units = ((L.cout + unk::TW_MB - 1) / unk::TW_MB) * (L.cin / NBW) * 3;
+        const long long items = M / segw;
+        long long S = n->sms / units;
+        if (S < 1) S = 1;
+        if (S > items) S = items;
+        const long long cap = n->wpart_cap / nw;
+        if (S > cap) S = cap;
+        if (S > 1024LL * 256 / L.cout) S = 1024LL * 256 / L.cout;
+        if (S >= 1) {
+            const long long per = (items + S - 1) / S;
+            const int splits = (int)((items + per - 1) / per);
+            unk::WgradTcArgs a;
+            a.g = g;
+            a.gC = gC;
+            a.goff = goff;
+            a.x = x;
+            a.xC = xC;
+            a.xoff = xoff;
+            a.Cout = L.cout;
+            a.Cin = L.cin;
+            a.N = N;
+            a.H = H;
+            a.W = W;
+            a.splits = splits;
+            a.items_per_split = (int)per;
+            a.part = n->wpart;
+            a.bpart = n->bpart;
+            a.err = n->d_err;
+            const int stages = unk::tw_stages(NBW, segw);
+            const size_t smem = unk::tw_smem_bytes(NBW, segw);
+            const unsigned grid = (unsigned)(units * splits);
+            if (NBW == 128)
+                unk::k_wgrad_tc<128><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+            else if (NBW == 64)
+                unk::k_wgrad_tc<64><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+            else
+                unk::k_wgrad_tc<32><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+            unk::k_sum_splits<<<sum_grid(nw), dim3(32, 8), 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
+            unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
+            return cudaGetLastError();
+        }
+    }
+    if (W % unk::HT_W == 0 && H % unk::HT_H == 0) {
         // halo-tile form: one staged gradient tile and input halo per 128 pixels, all taps
         unk::WgradHaloArgs a;
         a.g = g;
@@ -326,8 +383,7 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
         a.part = n->wpart;
         a.bpart = n->bpart;
         unk::k_wgrad_halo<<<dim3(blocks, splits), 256, unk::wgrad_halo_smem_bytes(), n->stream>>>(a);
-        const long long nw = (long long)L.cout * 9 * L.cin;
-        unk::k_sum_splits<<<grid_for(nw), 256, 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
+        unk::k_sum_splits<<<sum_grid(nw), dim3(32, 8), 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
         unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
         return cudaGetLastError();
     }
@@ -353,8 +409,7 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
     else if (MT == 32) unk::k_wgrad<32, 64><<<grid, 256, 0, n->stream>>>(a);
     else if (NT == 32) unk::k_wgrad<64, 32><<<grid, 256, 0, n->stream>>>(a);
     else unk::k_wgrad<64, 64><<<grid, 256, 0, n->stream>>>(a);
-    const long long nw = (long long)L.cout * 9 * L.cin;
-    unk::k_sum_splits<<<grid_for(nw), 256, 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
+    unk::k_sum_splits<<<sum_grid(nw), dim3(32, 8), 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
     // bias: partials of the centre-tap CTAs, summed over the splits in order
     unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
     return cudaGetLastError();
@@ -364,24 +419,44 @@ const bf16* Wb(const un_net* n, int k) { return n->wb + n->L[k].qoff; }
 const bf16* Wt(const un_net* n, int k) { return n->wt + n->L[k].qoff; }
 const float* Bias(const un_net* n, int k) { return n->p + n->L[k].boff; }
 
-cudaError_t refresh_weights(un_net* n) {
-    for (int k = 0; k < UN_LAYERS; ++k) {
+// the Adam update (adam != 0) and every BF16 copy of the 3x3 weights, one launch
+cudaError_t adam_refresh(un_net* n, int adam, float lr, float b1, float b2, float eps, float c1, float c2) {
+    unk::AdamRefreshArgs a;
+    a.p = n->p;
+    a.m = n->m;
+    a.v = n->v;
+    a.g = n->grad;
+    a.n = n->nparam;
+    a.lr = lr;
+    a.b1 = b1;
+    a.b2 = b2;
+    a.eps = eps;
+    a.c1 = c1;
+    a.c2 = c2;
+    a.adam = adam;
+    a.wb = n->wb;
+    a.wt = n->wt;
+    a.wbk = n->wbk;
+    a.wtk = n->wtk;
+    a.nl = 0;
+    for (int k = 0; k < UN_LAYERS && a.nl < unk::AR_MAX_LAYERS; ++k) {
         const Layer& L = n->L[k];
         if (L.k != 3) continue;
-        const long long nw = (long long)L.cout * 9 * L.cin;
-        unk::k_refresh_w<<<grid_for(nw), 256, 0, n->stream>>>(n->p + L.woff, L.cout, L.cin, n->wb + L.qoff,
-                                                              n->wt + L.qoff);
+        a.woff[a.nl] = L.woff;
+        a.qoff[a.nl] = L.qoff;
+        a.cout[a.nl] = L.cout;
+        a.cin[a.nl] = L.cin;
         // stage images for the streamed tensor-core convolution (forward: Cout
         // output channels; input gradient: Cin)
-        if (unk::ts_block(L.cout) && L.cin % 16 == 0)
-            unk::k_block_w<<<grid_for(nw), 256, 0, n->stream>>>(n->wb + L.qoff, L.cout, L.cin,
-                                                                unk::ts_block(L.cout), n->wbk + L.qoff);
-        if (unk::ts_block(L.cin) && L.cout % 16 == 0)
-            unk::k_block_w<<<grid_for(nw), 256, 0, n->stream>>>(n->wt + L.qoff, L.cin, L.cout,
-                                                                unk::ts_block(L.cin), n->wtk + L.qoff);
+        a.nbf[a.nl] = L.cin % 16 == 0 ? unk::ts_block(L.cout) : 0;
+        a.nbt[a.nl] = L.cout % 16 == 0 ? unk::ts_block(L.cin) : 0;
+        ++a.nl;
     }
+    unk::k_adam_refresh<<<grid_for(n->nparam), 256, 0, n->stream>>>(a);
     return cudaGetLastError();
 }
+
+cudaError_t refresh_weights(un_net* n) { return adam_refresh(n, 0, 0.0f, 0.0f, 0.0f, 1.0f, 1.0f, 1.0f); }
 
 cudaError_t forward(un_net* n, int N, const float* d_in) {
     const int LV = UN_LEVELS;
@@ -658,6 +733,9 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_tcs<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::ts_smem_bytes(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::halo_smem_bytes());
@@ -740,10 +818,7 @@ lb_status un_adam_step(un_net* n, double lr, double beta1, double beta2, double 
     n->t += 1;
     const float c1 = (float)(1.0 / (1.0 - std::pow(beta1, (double)n->t)));
     const float c2 = (float)(1.0 / (1.0 - std::pow(beta2, (double)n->t)));
-    unk::k_adam<<<grid_for(n->nparam), 256, 0, n->stream>>>(n->p, n->m, n->v, n->grad, n->nparam, (float)lr,
-                                                             (float)beta1, (float)beta2, (float)eps, c1, c2);
-    UCU(cudaGetLastError(), "adam");
-    UCU(refresh_weights(n), "weight refresh");
+    UCU(adam_refresh(n, 1, (float)lr, (float)beta1, (float)beta2, (float)eps, c1, c2), "adam");
     return LB_OK;
 }
 

@@ -620,12 +620,27 @@ __global__ void __launch_bounds__(256) k_wgrad_halo(WgradHaloArgs a) {
         }
 }
 
-// out[i] = sum_s part[s * n + i], s = 0..splits-1 in order
-__global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+// out[i] = sum_s part[s * n + i] in a fixed order: blocks of 32 x 8 threads,
+// threadIdx.x the output within a chunk of 32, threadIdx.y a lane of splits
+// (s = y, y + 8, ...); the 8 lane sums are then added in order of y
+__global__ void __launch_bounds__(256) k_sum_splits(const float* __restrict__ part, int splits, long long n,
+                                                     float* __restrict__ out) {
+    __shared__ float red[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (long long i0 = blockIdx.x * 32LL; i0 < n; i0 += (long long)gridDim.x * 32) {
+        const long long i = i0 + tx;
         float s = 0.0f;
-        for (int k = 0; k < splits; ++k) s += part[(long long)k * n + i];
-        out[i] = s;
+        if (i < n)
+            for (int k = ty; k < splits; k += 8) s += part[(long long)k * n + i];
+        red[ty][tx] = s;
+        __syncthreads();
+        if (ty == 0 && i < n) {
+            float t = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += red[k][tx];
+            out[i] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -860,32 +875,64 @@ __global__ void __launch_bounds__(256) k_sum_doubles(const double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ Adam
-__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-    }
+// Element (co, tap, ci) of a layer's [Cout][9][Cin] weights in the per-stage
+// images of the streamed tensor-core convolution (output-channel block NB,
+// 16-channel chunks): block nb, chunk c16, tap, output group (of NB / 8),
+// input group (2), then the 8 x 8 core matrix (row = output channel).
+__host__ __device__ __forceinline__ long long blocked_at(int co, int tap, int ci, int Cin, int NB) {
+    const int nb = co / NB, cl = co % NB, c16 = ci / 16, kc = ci % 16;
+    const long long o = ((((long long)nb * (Cin / 16) + c16) * 9 + tap) * (NB / 8) + cl / 8) * 2 + kc / 8;
+    return o * 64 + (cl % 8) * 8 + kc % 8;
 }
 
-// BF16 copies of a 3x3 layer: Wb[co][tap][ci] and the input-gradient form
-// Wt[ci][8 - tap][co]
-__global__ void k_refresh_w(const float* __restrict__ Wm, int Cout, int Cin, bf16* __restrict__ Wb,
-                            bf16* __restrict__ Wt) {
-    const long long n = (long long)Cout * 9 * Cin;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int ci = (int)(i % Cin);
-        const long long r = i / Cin;
-        const int tap = (int)(r % 9);
-        const int co = (int)(r / 9);
-        const bf16 b = __float2bfloat16_rn(Wm[i]);
-        Wb[i] = b;
-        Wt[((long long)ci * 9 + (8 - tap)) * Cout + co] = b;
+constexpr int AR_MAX_LAYERS = 16;
+struct AdamRefreshArgs {
+    float* p;
+    float* m;
+    float* v;
+    const float* g;
+    long long n;                 // parameters
+    float lr, b1, b2, eps, c1, c2;
+    int adam;                    // 0: only the BF16 copies of the current p
+    bf16 *wb, *wt, *wbk, *wtk;   // [Cout][9][Cin], [Cin][9][Cout] (flipped taps), their stage images
+    int nl;
+    long long woff[AR_MAX_LAYERS], qoff[AR_MAX_LAYERS];
+    int cout[AR_MAX_LAYERS], cin[AR_MAX_LAYERS];
+    int nbf[AR_MAX_LAYERS], nbt[AR_MAX_LAYERS];  // stage-image blocks (0: none) of wb and wt
+};
+
+// One pass over the parameters: the Adam update (optional), then every BF16
+// copy of each 3x3 weight: wb[co][tap][ci], the input-gradient form
+// wt[ci][8 - tap][co] (shift_{8 - tap} = -shift_tap), and the stage images
+// of both for the streamed tensor-core convolution.
+__global__ void k_adam_refresh(AdamRefreshArgs a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
+        float pi = a.p[i];
+        if (a.adam) {
+            const float gi = a.g[i];
+            const float mi = a.b1 * a.m[i] + (1.0f - a.b1) * gi;
+            const float vi = a.b2 * a.v[i] + (1.0f - a.b2) * gi * gi;
+            a.m[i] = mi;
+            a.v[i] = vi;
+            pi = pi - a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
+            a.p[i] = pi;
+        }
+        for (int k = 0; k < a.nl; ++k) {
+            const long long j = i - a.woff[k];
+            const int Cout = a.cout[k], Cin = a.cin[k];
+            if (j < 0 || j >= (long long)Cout * 9 * Cin) continue;
+            const int ci = (int)(j % Cin);
+            const long long r = j / Cin;
+            const int tap = (int)(r % 9);
+            const int co = (int)(r / 9);
+            const bf16 b = __float2bfloat16_rn(pi);
+            const long long q = a.qoff[k];
+            a.wb[q + j] = b;
+            a.wt[q + ((long long)ci * 9 + (8 - tap)) * Cout + co] = b;
+            if (a.nbf[k]) a.wbk[q + blocked_at(co, tap, ci, Cin, a.nbf[k])] = b;
+            if (a.nbt[k]) a.wtk[q + blocked_at(ci, 8 - tap, co, Cout, a.nbt[k])] = b;
+            break;
+        }
     }
 }
 

@@ -17,7 +17,7 @@
 //      8 .. 8 + segw - 1 (one TMA box per group and row), the wrapped
 //      neighbours at slots 7 and 8 + segw (16-byte cp.async copies);
 //   B: the chunk's weights of the block for all 9 taps, one contiguous image
-//      (k_block_w) moved by one bulk copy: tap t, output-channel group j,
+//      (blocked_at) moved by one bulk copy: tap t, output-channel group j,
 //      input-channel group k -> t * NB * 32 + (2 j + k) * 128 bytes.
 // The MMA view of tap (dy, dx) for tile row r starts at halo row r + dy,
 // slot 7 + dx.
@@ -51,24 +51,6 @@ __host__ __device__ constexpr size_t ts_smem_bytes(int NB) {
 }
 // output-channel block of a layer (0: not for this kernel)
 __host__ __device__ constexpr int ts_block(int Cout) { return Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 0); }
-
-// weights [Cout][9][Cin] -> the per-stage images of k_conv3_tcs:
-// block nb, chunk c16, tap t, channel group j (of NB / 8), input group k (2),
-// row (output channel) r8, column (input channel) k8
-__global__ void k_block_w(const bf16* __restrict__ w, int Cout, int Cin, int NB, bf16* __restrict__ out) {
-    const long long n = (long long)Cout * 9 * Cin;
-    const int c16n = Cin / 16;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int ci = (int)(i % Cin);
-        const long long r = i / Cin;
-        const int tap = (int)(r % 9);
-        const int co = (int)(r / 9);
-        const int nb = co / NB, cl = co % NB;
-        const int c16 = ci / 16, kc = ci % 16;
-        const long long o = ((((long long)nb * c16n + c16) * 9 + tap) * (NB / 8) + cl / 8) * 2 + kc / 8;
-        out[o * 64 + (cl % 8) * 8 + kc % 8] = w[i];
-    }
-}
 
 // one MMA from the elected lane of the (converged) warp
 __device__ __forceinline__ void ts_mma1(uint32_t d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
