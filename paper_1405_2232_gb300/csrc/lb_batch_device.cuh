@@ -190,8 +190,26 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 const int y = item.y0 + j - 2;
                 const int xg = x0 + t;
                 const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
-                store_site<S>(dst + off, plane, kp, f, g, (real)0, (real)0, xg < STRIP_GHOST,
-                              xg >= nx - STRIP_GHOST);
+                // FP32 / FP64 storage, the values as computed; each plane's ghost
+                // copy right after its value (the one-branch-per-site form of
+                // store_site keeps all 18 values live past the main stores, which
+                // spills at this kernel's register budget of 2 CTAs per SM)
+                const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    elem* pf = dst + ((uint32_t)i * plane + off);
+                    elem* pg = dst + ((uint32_t)(9 + i) * plane + off);
+                    *pf = (elem)f[i];
+                    *pg = (elem)g[i];
+                    if (ghost_lo) {
+                        pf[nx] = (elem)f[i];
+                        pg[nx] = (elem)g[i];
+                    }
+                    if (ghost_hi) {
+                        pf[-nx] = (elem)f[i];
+                        pg[-nx] = (elem)g[i];
+                    }
+                }
             }
             // the job before this one has had its last reader in this warp
             if (j >= 1) {
