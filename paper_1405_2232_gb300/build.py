@@ -37,12 +37,14 @@ def nvcc() -> str:
 # contraction so its rounding is that of the printed expressions; the 16-bit
 # storage modes, whose step is bound by instruction issue, take the faster
 # FP32 division and square root (a few ulp, far below the 16-bit rounding of
-# the stored deviations; measured +5% on the 4096^2 step); the start at rest
-# under the force is FP64 arithmetic in printed order for every storage mode
+# the stored deviations; measured +5% on the 4096^2 step) and read the float
+# copies of the parameters (LB_KP_FLOAT: no double conversion on the narrow
+# FP64 pipe per site; +4-6%); the start at rest under the force is FP64
+# arithmetic in printed order for every storage mode
 EXTRA_FLAGS = {"lb_prec_fp64.cu": ["--fmad=false"], "lb_batch_fp64.cu": ["--fmad=false"],
                "lb_init_balanced.cu": ["--fmad=false"],
-               "lb_prec_fp16.cu": ["-prec-div=false", "-prec-sqrt=false"],
-               "lb_prec_bf16.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+               "lb_prec_fp16.cu": ["-prec-div=false", "-prec-sqrt=false", "-DLB_KP_FLOAT"],
+               "lb_prec_bf16.cu": ["-prec-div=false", "-prec-sqrt=false", "-DLB_KP_FLOAT"]}
 
 
 def _sources():

@@ -361,6 +361,7 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
         k.inv_cv = 1.0 / p.cv;
         k.T_psi = p.T_psi;
         k.ghost = STRIP_GHOST;
+        kp_fill_float(k);
         D.off = off + lay.origin;
         D.fld_off = fld;
         off += 18 * plane;

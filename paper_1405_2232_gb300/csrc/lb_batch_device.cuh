@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256)
             m += (double)f[i];
             en += (double)g[i];
         }
-        const double r = (double)rho, T = (double)(e / (rho * (real)kp.cv));
+        const double r = (double)rho, T = (double)(e / (rho * KPR(kp, cv)));
         const long long fo = D.fld_off + s;
         v[0] = m;
         v[1] = en;

@@ -244,6 +244,7 @@ KParams make_kparams(const lb_params& p, long long pitch, long long plane, int* 
     k.err = err;
     k.wait_cycles = WAIT_CYCLES_DEFAULT;
     k.halo_rows = p.halo_rows;
+    kp_fill_float(k);
     return k;
 }
 

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(CAV_BX* CAV_BY)
         real Fx, Fy, ux, uy, T;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1, WX, Fx,
                                        Fy);
-        Fy += -rho * (real)kp.g_grav;
+        Fy += -rho * KPR(kp, g_grav);
         collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(CAV_BX* CAV_BY)
                 S::put(dst + (long long)o * kp.plane + off, f[i], (real)kp.base_f[o]);
                 real gb;
                 if (out_x) {
-                    const real Tw = xd < 0 ? (real)kp.T_hot : (real)kp.T_cold;
-                    gb = -g[i] + (real)2.0 * (real)wd(i) * rho * (real)kp.cv * Tw;
+                    const real Tw = xd < 0 ? KPR(kp, T_hot) : KPR(kp, T_cold);
+                    gb = -g[i] + (real)2.0 * (real)wd(i) * rho * KPR(kp, cv) * Tw;
                 } else {
                     gb = g[i];
                 }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(CAV_BX* CAV_BY)
                                        Fy);
         collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
         const real cs2 = (real)(1.0 / 3.0);
-        const real uin = (real)kp.U_in;
+        const real uin = KPR(kp, U_in);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int xd = gx + ex(i), yd = gy + ey(i);
@@ -170,13 +170,13 @@ __global__ void __launch_bounds__(CAV_BX* CAV_BY)
                 if (yd < 0 && kp.adiabatic_bottom)
                     gb = g[i];
                 else
-                    gb = -g[i] + (real)2.0 * (real)wd(i) * rho * (real)kp.cv * (real)kp.T_w;
+                    gb = -g[i] + (real)2.0 * (real)wd(i) * rho * KPR(kp, cv) * KPR(kp, T_w);
                 S::put(pgo, gb, (real)kp.base_g[o]);
             } else if (xd < 0) {
                 // inlet
                 const real eu = (real)ex(i) * uin;
                 S::put(pfo, f[i] - (real)2.0 * (real)wd(i) * rho * eu / cs2, (real)kp.base_f[o]);
-                const real gb = -g[i] + (real)2.0 * (real)wd(i) * rho * (real)kp.cv * (real)kp.T_in *
+                const real gb = -g[i] + (real)2.0 * (real)wd(i) * rho * KPR(kp, cv) * KPR(kp, T_in) *
                                             ((real)1.0 + (real)0.5 * eu * eu / (cs2 * cs2) -
                                              (real)0.5 * uin * uin / cs2);
                 S::put(pgo, gb, (real)kp.base_g[o]);

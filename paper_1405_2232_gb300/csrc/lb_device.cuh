@@ -179,7 +179,56 @@ struct KParams {
     float sum_bf, sum_bg;        // sum_i base_f[i], sum_i base_g[i]
     float dsum_f, dsum_g;        // sum_i base_f[i] - rho0, sum_i base_g[i] - rho0 c_v T0
     float cw_f[3], cw_g[3];      // w rho0 - base_f, w rho0 c_v T0 - base_g (rest, axis, diagonal)
+    // the doubles above rounded to float once on the host (kp_fill_float):
+    // the 16-bit kernels read these (KPR, collide_dev), since converting a
+    // double at each use runs on the FP64 pipe, which is narrow on this GPU
+    struct {
+        float omega_f, omega_g, guo_pre, corr_pre, G, two_over_G, beta, half_1mbeta;
+        float T_hot, T_cold, g_grav, T_in, T_w, U_in, a, b, R, cv, inv_cv, T_psi;
+    } f;
 };
+
+// Set KParams::f from the double fields (call after they are final).
+inline void kp_fill_float(KParams& k) {
+    k.f.omega_f = (float)k.omega_f;
+    k.f.omega_g = (float)k.omega_g;
+    k.f.guo_pre = (float)k.guo_pre;
+    k.f.corr_pre = (float)k.corr_pre;
+    k.f.G = (float)k.G;
+    k.f.two_over_G = (float)k.two_over_G;
+    k.f.beta = (float)k.beta;
+    k.f.half_1mbeta = (float)k.half_1mbeta;
+    k.f.T_hot = (float)k.T_hot;
+    k.f.T_cold = (float)k.T_cold;
+    k.f.g_grav = (float)k.g_grav;
+    k.f.T_in = (float)k.T_in;
+    k.f.T_w = (float)k.T_w;
+    k.f.U_in = (float)k.U_in;
+    k.f.a = (float)k.a;
+    k.f.b = (float)k.b;
+    k.f.R = (float)k.R;
+    k.f.cv = (float)k.cv;
+    k.f.inv_cv = (float)k.inv_cv;
+    k.f.T_psi = (float)k.T_psi;
+}
+
+// a parameter in the arithmetic type `real`.  Translation units built with
+// LB_KP_FLOAT (the 16-bit storage modes, bound by instruction issue) read the
+// float copy when real is float; the others convert the double at the use
+// (the same rounding; on the HBM-bound FP32 step this measured faster,
+// 403 us against 438 us per 4096^2 launch, with the same registers).
+template <typename real>
+__device__ __forceinline__ real kpick(double d, float f) {
+    if constexpr (sizeof(real) == sizeof(float))
+        return f;
+    else
+        return (real)d;
+}
+#ifdef LB_KP_FLOAT
+#define KPR(kp, name) (::lbgb::kpick<real>((kp).name, (kp).f.name))
+#else
+#define KPR(kp, name) ((real)(kp).name)
+#endif
 
 // Default limit of a bounded device wait, in clock cycles (about one second
 // at GB300 clocks).
@@ -189,7 +238,7 @@ enum BetaMode { BETA_ZERO = 0, BETA_ONE = 1, BETA_MIXED = 2 };
 
 template <typename real>
 __device__ __forceinline__ real p_eos(const KParams& kp, real rho, real T) {
-    const real R = (real)kp.R, a = (real)kp.a, b = (real)kp.b;
+    const real R = KPR(kp, R), a = KPR(kp, a), b = KPR(kp, b);
     if (kp.eos == LB_EOS_IDEAL) return rho * R * T;
     if (kp.eos == LB_EOS_VDW) return rho * R * T / ((real)1 - b * rho) - a * rho * rho;
     // Carnahan-Starling, eta = b rho / 4
@@ -413,12 +462,12 @@ __device__ __forceinline__ void site_psi(const KParams& kp, const real f[9], con
         e += g[i];
     }
     rho = r;
-    T = e / (r * (real)kp.cv);
-    const real Te = kp.psi_local_T ? T : (real)kp.T_psi;
+    T = e / (r * KPR(kp, cv));
+    const real Te = kp.psi_local_T ? T : KPR(kp, T_psi);
     if constexpr (sizeof(real) == 8)
-        psi2 = (real)2 * (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) / (real)kp.G;
+        psi2 = (real)2 * (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) / KPR(kp, G);
     else
-        psi2 = (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) * (real)kp.two_over_G;
+        psi2 = (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) * KPR(kp, two_over_G);
     psi = (real)0;
     if (BMODE != BETA_ZERO) {
         if (psi2 < (real)0) flags |= 1 << LB_ERR_PSI_DOMAIN;
@@ -443,7 +492,7 @@ __device__ __forceinline__ void force_from_window(const KParams& kp, const real*
         const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
         const real s1x = w1 * (E - Wv) + w2 * (d1 + d2);
         const real s1y = w1 * (N - S) + w2 * (d1 + d3);
-        const real pc = (BMODE == BETA_ONE) ? p[c] : (real)kp.beta * p[c];
+        const real pc = (BMODE == BETA_ONE) ? p[c] : KPR(kp, beta) * p[c];
         fx += pc * s1x;
         fy += pc * s1y;
     }
@@ -454,12 +503,12 @@ __device__ __forceinline__ void force_from_window(const KParams& kp, const real*
         const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
         const real s2x = w1 * (E - Wv) + w2 * (d1 + d2);
         const real s2y = w1 * (N - S) + w2 * (d1 + d3);
-        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : (real)kp.half_1mbeta;
+        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : KPR(kp, half_1mbeta);
         fx += h * s2x;
         fy += h * s2y;
     }
-    Fx = -(real)kp.G * fx;
-    Fy = -(real)kp.G * fy;
+    Fx = -KPR(kp, G) * fx;
+    Fy = -KPR(kp, G) * fy;
 }
 
 // Collision of one site, Eq. (1) + F_i for f and Eq. (7) / (24) for g.
@@ -519,10 +568,10 @@ __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9],
         const real inv_rho = (real)1 / rho;
         const real ux = (mx + (real)0.5 * Fx) * inv_rho;
         const real uy = (my + (real)0.5 * Fy) * inv_rho;
-        const real T = e / (rho * (real)kp.cv);
-        const real cvT = (real)kp.cv * T;
-        const real om_f = (real)kp.omega_f, om_g = (real)kp.omega_g;
-        const real guo = (real)kp.guo_pre, corr = (real)kp.corr_pre;
+        const real T = e / (rho * KPR(kp, cv));
+        const real cvT = KPR(kp, cv) * T;
+        const real om_f = KPR(kp, omega_f), om_g = KPR(kp, omega_g);
+        const real guo = KPR(kp, guo_pre), corr = KPR(kp, corr_pre);
         const real base = (real)1 - (real)1.5 * (ux * ux + uy * uy);
         const real uF3 = (real)3 * (ux * Fx + uy * Fy);
         // Opposite directions i and i' = opposite(i) share the even parts of
@@ -597,8 +646,8 @@ __device__ __forceinline__ void collide_dev(const KParams& kp, float h[9], float
     const float ux = (mx + 0.5f * Fx) * inv_rho;
     const float uy = (my + 0.5f * Fy) * inv_rho;
     const float cvT = e * inv_rho;
-    const float om_f = (float)kp.omega_f, om_g = (float)kp.omega_g;
-    const float guo = (float)kp.guo_pre, corr = (float)kp.corr_pre;
+    const float om_f = kp.f.omega_f, om_g = kp.f.omega_g;
+    const float guo = kp.f.guo_pre, corr = kp.f.corr_pre;
     const float m15u2 = -1.5f * (ux * ux + uy * uy);
     const float uF3 = 3.0f * (ux * Fx + uy * Fy);
     const float Aa = (float)(1.0 / 9.0) * drho + kp.cw_f[1], Ad = (float)(1.0 / 36.0) * drho + kp.cw_f[2];
@@ -765,7 +814,7 @@ __global__ void __launch_bounds__(BX* BY)
         real Fx, Fy, ux, uy, T;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1,
                                        WX, Fx, Fy);
-        if (kp.walls) Fy += -rho * (real)kp.g_grav;  // cavity buoyancy
+        if (kp.walls) Fy += -rho * KPR(kp, g_grav);  // cavity buoyancy
         collide<real, false>(kp, f, g, rho, Fx, Fy, ux, uy, T);
         const long long idx = (long long)gy * kp.nx + gx;
         if (o_rho) o_rho[idx] = (double)rho;

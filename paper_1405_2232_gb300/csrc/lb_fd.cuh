@@ -57,11 +57,11 @@ __device__ __forceinline__ void pull9(const typename S::elem* __restrict__ src, 
 template <typename real, int BMODE>
 __device__ __forceinline__ void site_psi_T(const KParams& kp, real r, real T, real& psi, real& psi2,
                                            int& flags) {
-    const real Te = kp.psi_local_T ? T : (real)kp.T_psi;
+    const real Te = kp.psi_local_T ? T : KPR(kp, T_psi);
     if constexpr (sizeof(real) == 8)
-        psi2 = (real)2 * (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) / (real)kp.G;
+        psi2 = (real)2 * (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) / KPR(kp, G);
     else
-        psi2 = (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) * (real)kp.two_over_G;
+        psi2 = (p_eos<real>(kp, r, Te) - r * (real)(1.0 / 3.0)) * KPR(kp, two_over_G);
     psi = (real)0;
     if (BMODE != BETA_ZERO) {
         if (psi2 < (real)0) flags |= 1 << LB_ERR_PSI_DOMAIN;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
         for (int i = 1; i < 9; ++i) rho += f[i];
         real Fx, Fy, ux, uy, Tg;
         force_from_window<real, BMODE>(kp, s_psi, s_psi2, (threadIdx.y + 1) * WX + threadIdx.x + 1, WX, Fx, Fy);
-        if (kp.walls) Fy += -rho * (real)kp.g_grav;  // cavity buoyancy
+        if (kp.walls) Fy += -rho * KPR(kp, g_grav);  // cavity buoyancy
         // the f half of the collision; g (zero here) is not used
         collide<real, false>(kp, f, g, rho, Fx, Fy, ux, uy, Tg);
         const long long c = (long long)gy * kp.nx + gx;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(FD_BX* FD_BY)
                     } else if (kp.walls != 2 || yd < 0 || yd >= kp.ny) {
                         S::put(pfo, f[i], (real)kp.base_f[opp(i)]);
                     } else if (xd < 0) {
-                        const real eu = (real)ex(i) * (real)kp.U_in;
+                        const real eu = (real)ex(i) * KPR(kp, U_in);
                         S::put(pfo, f[i] - (real)2.0 * (real)wd(i) * rho * eu / cs2, (real)kp.base_f[opp(i)]);
                     } else {
                         const real eu = (real)ex(i) * ux + (real)ey(i) * uy;

@@ -373,15 +373,15 @@ template <typename real>
 __device__ __forceinline__ real fd_ghost(const KParams& kp, int rx, int ry, real Xm) {
     const int nx = kp.nx, ny = kp.ny;
     if (kp.walls == 1) {
-        if (rx < 0) return (real)2.0 * (real)kp.T_hot - Xm;
-        if (rx >= nx) return (real)2.0 * (real)kp.T_cold - Xm;
+        if (rx < 0) return (real)2.0 * KPR(kp, T_hot) - Xm;
+        if (rx >= nx) return (real)2.0 * KPR(kp, T_cold) - Xm;
         return Xm;
     }
     if (ry < 0 || ry >= ny) {
         if (ry < 0 && kp.adiabatic_bottom) return Xm;
-        return (real)2.0 * (real)kp.T_w - Xm;
+        return (real)2.0 * KPR(kp, T_w) - Xm;
     }
-    if (rx < 0) return (real)2.0 * (real)kp.T_in - Xm;
+    if (rx < 0) return (real)2.0 * KPR(kp, T_in) - Xm;
     return Xm;
 }
 

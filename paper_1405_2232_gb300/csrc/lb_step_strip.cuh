@@ -125,7 +125,7 @@ __device__ __forceinline__ void force_from_rows(const KParams& kp, const real* p
         const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
         const real s1x = w1 * (E - Wv) + w2 * (d1 + d2);
         const real s1y = w1 * (N - S) + w2 * (d1 + d3);
-        const real c = (BMODE == BETA_ONE) ? pc[0] : (real)kp.beta * pc[0];
+        const real c = (BMODE == BETA_ONE) ? pc[0] : KPR(kp, beta) * pc[0];
         fx += c * s1x;
         fy += c * s1y;
     }
@@ -135,12 +135,12 @@ __device__ __forceinline__ void force_from_rows(const KParams& kp, const real* p
         const real d1 = NE - SW, d2 = SE - NW, d3 = NW - SE;
         const real s2x = w1 * (E - Wv) + w2 * (d1 + d2);
         const real s2y = w1 * (N - S) + w2 * (d1 + d3);
-        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : (real)kp.half_1mbeta;
+        const real h = (BMODE == BETA_ZERO) ? (real)0.5 : KPR(kp, half_1mbeta);
         fx += h * s2x;
         fy += h * s2y;
     }
-    Fx = -(real)kp.G * fx;
-    Fy = -(real)kp.G * fy;
+    Fx = -KPR(kp, G) * fx;
+    Fy = -KPR(kp, G) * fy;
 }
 
 template <int PREC>
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                         Hg += dev_of<S>(st + (9 + i) * SEGW + c - ex(i), 9 + i, rest_lo_offset(9 + i) * SEGW);
                     }
                     rho = kp.sum_bf + Hf;
-                    T = (kp.sum_bg + Hg) / (rho * (real)kp.cv);
+                    T = (kp.sum_bg + Hg) / (rho * KPR(kp, cv));
                     site_psi_T<real, BMODE>(kp, rho, T, psi, psi2, flags);
                 } else {
                     real f[9], g[9];
