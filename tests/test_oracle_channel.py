@@ -65,3 +65,36 @@ def test_fd_table1_fully_developed_nusselt(case):
     nus = [O.channel_nusselt_wall(P, Ch, rho, ux, T, x) for x in range(60, 121, 15)]
     assert np.ptp(nus) < 0.01 * np.mean(nus)
     assert np.mean(nus) == pytest.approx(NU_ANALYTICAL[case], rel=0.02), nus
+
+
+def test_eq7_lateral_conduction_vanishes():
+    """Why Eq. (7) under-reads the plate channel (Sec. III A; the paper's
+    Fig. 1 has it high).  Eq. (23): Eq. (7) solves the temperature equation
+    with the flux lambda grad T + vartheta T F, vartheta = lambda / p,
+    p = rho c_s^2, so across the channel lambda_eff,y = lambda (1 + c) with
+    c = T F_y / (p dT/dy).  With the ideal EOS the pseudopotential force is
+    F = -grad(rho R T - rho c_s^2) (the text after Eq. 4), and a developed
+    channel flow is in lateral balance of the total pressure rho R T, so
+    F_y = c_s^2 d rho/dy = -c_s^2 rho (dT/dy) / T and c = -1: heat is not
+    conducted across the flow at all.  Checked on the developed state of both
+    treatments (the momentum balance does not depend on the thermal
+    equation), and the consequence for Eq. (7): a plate Nusselt number far
+    below Eq. (24)'s."""
+    import os
+    nx, ny = 120, 20
+    out = {}
+    for th in (O.THERMAL_EQ7, O.THERMAL_EQ24):
+        P, Ch = O.channel_setup(nx, ny, "A", thermal=th)
+        f, g = O.init_equilibrium(P, np.ones((ny, nx)), np.ones((ny, nx)))
+        f, g, _ = O.step_channel(P, Ch, f, g, n=20000, threads=os.cpu_count() or 1)
+        rho, ux, uy, T, Fx, Fy = O.moments(P, f, g)
+        dT = 0.5 * (T[2:, :] - T[:-2, :])  # d/dy at rows 1 .. ny - 2
+        c = T[1:-1, :] * Fy[1:-1, :] / (rho[1:-1, :] * (1.0 / 3.0) * dT)  # p = rho c_s^2, c_s^2 = 1/3
+        # interior rows with a clear gradient, away from the plates (the
+        # moment routine's force is periodic, the channel's clamped) and from
+        # the channel's centre line (dT/dy = 0), in the developed half
+        rows = [r - 1 for r in (2, 3, 4, 5, ny - 6, ny - 5, ny - 4, ny - 3)]
+        sel = c[rows][:, nx // 2: 3 * nx // 4]
+        assert np.abs(sel + 1.0).max() < 0.01, sel
+        out[th] = O.channel_nusselt_grad(P, Ch, rho, ux, T, nx // 2)
+    assert out[O.THERMAL_EQ7] < 0.2 * out[O.THERMAL_EQ24], out
