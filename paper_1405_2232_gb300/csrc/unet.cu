@@ -309,14 +309,18 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
     const Layer& L = n->L[k];
     const long long M = Pl(n, l, N);
     const long long nw = (long long)L.cout * 9 * L.cin;
-    const int NBW = unk::tw_block(L.cin);
+    // the swapped orientation (M = input channels) for 32 output channels
+    // and at least 64 input channels; otherwise M = output channels
+    const bool xm = L.cout == 32 && L.cin >= 64 && L.cin % 32 == 0;
+    const int NBW = xm ? unk::TW_MB : unk::tw_block(L.cin);
     const int W = Wl(n, l), H = Hl(n, l);
     const int segw = unk::tw_segw(W);
     CUtensorMap gmap, xmap;
-    if (L.cout % 64 == 0 && L.cout <= 384 && NBW && W % 16 == 0 && W % segw == 0 && M / segw < (1LL << 30) &&
-        conv_tensor_map(g, gC, W, H, N, &gmap, segw) && conv_tensor_map(x, xC, W, H, N, &xmap, segw)) {
+    if ((xm || (L.cout % 64 == 0 && L.cout <= 384 && NBW)) && W % 16 == 0 && W % segw == 0 &&
+        M / segw < (1LL << 30) && conv_tensor_map(g, gC, W, H, N, &gmap, segw) &&
+        conv_tensor_map(x, xC, W, H, N, &xmap, segw)) {
         // fifth-generation tensor cores: (output block, input block, kernel row, pixel split) per CTA
-        const int units = ((L.cout + unk::TW_MB - 1) / unk::TW_MB) * (L.cin / NBW) * 3;
+        const int units = (xm ? 1 : (L.cout + unk::TW_MB - 1) / unk::TW_MB) * ((L.cin + NBW - 1) / NBW) * 3;
         const long long items = M / segw;
         long long S = n->sms / units;
         if (S < 1) S = 1;
@@ -344,15 +348,18 @@ cudaError_t wgrad(un_net* n, int k, const bf16* g, int gC, int goff, const bf16*
             a.part = n->wpart;
             a.bpart = n->bpart;
             a.err = n->d_err;
-            const int stages = unk::tw_stages(NBW, segw);
-            const size_t smem = unk::tw_smem_bytes(NBW, segw);
+            const int na = xm ? 32 : NBW;
+            const int stages = unk::tw_stages(na, xm, segw);
+            const size_t smem = unk::tw_smem_bytes(na, xm, segw);
             const unsigned grid = (unsigned)(units * splits);
-            if (NBW == 128)
-                unk::k_wgrad_tc<128><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+            if (xm)
+                unk::k_wgrad_tc<32, true><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+            else if (NBW == 128)
+                unk::k_wgrad_tc<128, false><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
             else if (NBW == 64)
-                unk::k_wgrad_tc<64><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+                unk::k_wgrad_tc<64, false><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
             else
-                unk::k_wgrad_tc<32><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
+                unk::k_wgrad_tc<32, false><<<grid, unk::TW_THREADS, smem, n->stream>>>(a, gmap, xmap, stages);
             unk::k_sum_splits<<<sum_grid(nw), dim3(32, 8), 0, n->stream>>>(n->wpart, splits, nw, n->grad + L.woff);
             unk::k_sum_splits_wide<<<L.cout, 256, 0, n->stream>>>(n->bpart, splits, L.cout, n->grad + L.boff);
             return cudaGetLastError();
@@ -711,6 +718,15 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
         long long smax = (4LL * n->sms + tiles - 1) / tiles;
         const long long smax_h = (4LL * n->sms + hblocks - 1) / hblocks;
         if (smax_h > smax) smax = smax_h;
+        // the tcgen05 weight gradient: one split per SM's share of its units
+        const bool xm = n->L[k].cout == 32 && n->L[k].cin >= 64 && n->L[k].cin % 32 == 0;
+        const int nbw = xm ? unk::TW_MB : unk::tw_block(n->L[k].cin);
+        if (xm || (n->L[k].cout % 64 == 0 && nbw)) {
+            const long long units = (xm ? 1 : (n->L[k].cout + unk::TW_MB - 1) / unk::TW_MB) *
+                                    ((n->L[k].cin + nbw - 1) / nbw) * 3;
+            const long long s_tc = n->sms / units > 1 ? n->sms / units : 1;
+            if (s_tc > smax) smax = s_tc;
+        }
         const long long need = smax * n->L[k].cout * 9 * n->L[k].cin;
         if (need > cap) cap = need;
     }
@@ -733,9 +749,14 @@ lb_status un_create(const un_config* cfg, void* stream, un_net** out) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_tcs<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::ts_smem_bytes(64));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(unk::k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_wgrad_tc<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_wgrad_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_wgrad_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(unk::k_wgrad_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(unk::k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unk::halo_smem_bytes());

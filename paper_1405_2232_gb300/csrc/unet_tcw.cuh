@@ -21,6 +21,13 @@
 // at slot 7 + dx.  The three accumulators (dx = 0, 1, 2; NBW TMEM columns
 // each) stay in TMEM for the CTA's whole range.
 //
+// With XM (layers with 32 output channels and at least 64 input channels)
+// the roles of the operands swap: A = x with M = 128 input channels, B = g
+// with N = NA = Cout, so the 128 MMA rows are the wider side (with M = 32
+// output channels three quarters of every MMA would be empty); the
+// accumulators are D[ci][co] and the partial sums are written with TMEM lane
+// = input channel.
+//
 // Roles: warp 0 produces (elected lane: barrier byte count and the tensor
 // copies; lanes: the wrapped neighbours, arriving when they land), warp 5
 // issues the MMAs (warp-wide loop, elected lane), warps 1-4 sum g for the bias
@@ -51,37 +58,43 @@ struct WgradTcArgs {
 };
 
 __host__ __device__ constexpr int tw_segw(int W) { return W < TC_M ? W : TC_M; }
-__host__ __device__ constexpr int tw_gbytes(int segw) { return (TW_MB / 8) * segw * 16; }
-__host__ __device__ constexpr int tw_xbytes(int NBW) { return (NBW / 8) * TC_HROW * 16; }
-__host__ __device__ constexpr int tw_stage_bytes(int NBW, int segw) { return tw_gbytes(segw) + tw_xbytes(NBW); }
-__host__ __device__ constexpr int tw_stages(int NBW, int segw) {
-    return (int)((232448 - 1024 - 512) / tw_stage_bytes(NBW, segw)) > 6 ? 6
-                                                                         : (int)((232448 - 1024 - 512) /
-                                                                                 tw_stage_bytes(NBW, segw));
+// channel groups staged per stage: g (output channels) and x (input channels)
+__host__ __device__ constexpr int tw_gplanes(int NA, bool XM) { return XM ? NA / 8 : TW_MB / 8; }
+__host__ __device__ constexpr int tw_xplanes(int NA, bool XM) { return XM ? TW_MB / 8 : NA / 8; }
+__host__ __device__ constexpr int tw_gbytes(int NA, bool XM, int segw) { return tw_gplanes(NA, XM) * segw * 16; }
+__host__ __device__ constexpr int tw_xbytes(int NA, bool XM) { return tw_xplanes(NA, XM) * TC_HROW * 16; }
+__host__ __device__ constexpr int tw_stage_bytes(int NA, bool XM, int segw) {
+    return tw_gbytes(NA, XM, segw) + tw_xbytes(NA, XM);
 }
-__host__ __device__ constexpr size_t tw_smem_bytes(int NBW, int segw) {
-    return (size_t)tw_stages(NBW, segw) * tw_stage_bytes(NBW, segw) + 512 + 1024;
+__host__ __device__ constexpr int tw_stages(int NA, bool XM, int segw) {
+    return (int)((232448 - 1024 - 512) / tw_stage_bytes(NA, XM, segw)) > 6
+               ? 6
+               : (int)((232448 - 1024 - 512) / tw_stage_bytes(NA, XM, segw));
+}
+__host__ __device__ constexpr size_t tw_smem_bytes(int NA, bool XM, int segw) {
+    return (size_t)tw_stages(NA, XM, segw) * tw_stage_bytes(NA, XM, segw) + 512 + 1024;
 }
 // input-channel block of a layer (0: not for this kernel)
 __host__ __device__ constexpr int tw_block(int Cin) {
     return Cin % 128 == 0 ? 128 : (Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 0));
 }
 
-template <int NBW>
+template <int NA, bool XM>
 __global__ void __launch_bounds__(TW_THREADS, 1)
     k_wgrad_tc(WgradTcArgs a, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap xmap,
                int stages) {
-    constexpr int XG = NBW / 8;                 // input channel groups
-    constexpr int EDGES = 2 * XG;               // wrapped neighbours per stage
-    constexpr uint32_t COLS = 3 * NBW <= 128 ? 128u : (3 * NBW <= 256 ? 256u : 512u);
-    static_assert(EDGES <= 32, "one edge copy per producer lane");
+    // NA: N of the MMA (input-channel block; with XM the output channels)
+    constexpr int NBW = XM ? TW_MB : NA;            // input channels of a block
+    constexpr int XG = tw_xplanes(NA, XM);          // input channel groups staged
+    constexpr uint32_t COLS = 3 * NA <= 128 ? 128u : (3 * NA <= 256 ? 256u : 512u);
+    static_assert(2 * XG <= 32, "one edge copy per producer lane");
     extern __shared__ __align__(1024) uint8_t tw_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tw_raw) + 1023) & ~uintptr_t(1023));
     const int H = a.H, W = a.W;
     const int segw = tw_segw(W);
     const int segs = W / segw;
-    const int GB = tw_gbytes(segw);
-    const int SB = GB + tw_xbytes(NBW);
+    const int GB = tw_gbytes(NA, XM, segw);
+    const int SB = GB + tw_xbytes(NA, XM);
     uint8_t* sS = base;                                                     // [stages][SB]
     uint64_t* full = reinterpret_cast<uint64_t*>(sS + (size_t)stages * SB);  // [stages]
     uint64_t* empty = full + 6;                                             // [stages]
@@ -92,7 +105,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // unit: output block, input block, dy, split (split outermost: the CTAs
     // working on the same pixels run together)
-    const int ncob = (a.Cout + TW_MB - 1) / TW_MB, ncib = a.Cin / NBW;
+    const int ncob = XM ? 1 : (a.Cout + TW_MB - 1) / TW_MB;
+    const int ncib = (a.Cin + NBW - 1) / NBW;
     int u = blockIdx.x;
     const int cob = u % ncob;
     u /= ncob;
@@ -106,8 +120,10 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
     const int nitems = it1 > it0 ? it1 - it0 : 0;
     const bool do_bias = cib == 0 && dy == 1;
     const int cg0 = (a.goff + cob * TW_MB) / 8;         // first g channel group of the block
-    const int gvalid = min(TW_MB, a.Cout - cob * TW_MB) / 8;  // g groups that exist
+    const int gvalid = XM ? a.Cout / 8 : min(TW_MB, a.Cout - cob * TW_MB) / 8;  // g groups that exist
     const int xg0 = (a.xoff + cib * NBW) / 8;
+    const int xvalid = min(NBW, a.Cin - cib * NBW) / 8;  // x groups that exist
+    const int EDGES = 2 * xvalid;                        // wrapped neighbours per stage
 
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
             const uint32_t fb = smem_addr(&full[s]);
             {
                 // arm with every byte of the stage's tensor copies
-                const uint32_t bytes = (uint32_t)((gvalid + XG) * segw * 16);
+                const uint32_t bytes = (uint32_t)((gvalid + xvalid) * segw * 16);
                 asm volatile(
                     "{\n .reg .pred e;\n .reg .b32 el;\n elect.sync el|e, 0xffffffff;\n"
                     " @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}\n" ::"r"(fb),
@@ -162,8 +178,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
                     : "memory");
             }
             for (int k = 0; k < gvalid; ++k) ts_tma(&gmap, st + k * segw * 16, fb, x0 / 8, cg0 + k, row);
-#pragma unroll 4
-            for (int k = 0; k < XG; ++k)
+            for (int k = 0; k < xvalid; ++k)
                 ts_tma(&xmap, st + GB + (k * TC_HROW + TC_BODY) * 16, fb, x0 / 8, xg0 + k, xrow);
             if (edge) {
                 const int xx = eside ? wrap(x0 + segw, W) : wrap(x0 - 1, W);
@@ -185,14 +200,15 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
         // ------------------------------------------------ MMA issue
         // kind::f16, D FP32, A and B BF16, both MN-major (bits 15, 16)
         constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                                   ((uint32_t)(NBW >> 3) << 17) | ((uint32_t)(TW_MB >> 4) << 24);
+                                   ((uint32_t)(NA >> 3) << 17) | ((uint32_t)(TW_MB >> 4) << 24);
         // no-swizzle MN-major operands: the leading byte offset is the stride
         // between K groups (8 pixels: 128 bytes), the stride byte offset the
         // stride between MN groups (8 channels)
-        // A (g): channel groups segw * 16 bytes apart
-        const uint64_t da0 = tc_mdesc(smem_addr(sS), 128, (uint32_t)(segw * 16));
-        // B (x): channel groups one halo row (TC_HROW * 16 bytes) apart
-        const uint64_t db0 = tc_mdesc(smem_addr(sS) + (uint32_t)(GB + (TC_BODY - 1) * 16), 128, TC_HROW * 16);
+        // g: channel groups segw * 16 bytes apart
+        const uint64_t dg0 = tc_mdesc(smem_addr(sS), 128, (uint32_t)(segw * 16));
+        // x: channel groups one halo row (TC_HROW * 16 bytes) apart
+        const uint64_t dx0 = tc_mdesc(smem_addr(sS) + (uint32_t)(GB + (TC_BODY - 1) * 16), 128, TC_HROW * 16);
+        const uint64_t da0 = XM ? dx0 : dg0, db0 = XM ? dg0 : dx0;
         const uint32_t ahi = (uint32_t)(da0 >> 32), bhi = (uint32_t)(db0 >> 32);
         const int ksteps = segw / 16;
         int s = 0;
@@ -210,8 +226,9 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
             for (int k = 0; k < ksteps; ++k) {
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx)
-                    ts_mma1(tmem + (uint32_t)(dx * NBW), a_lo + (uint32_t)(k * 16), ahi,
-                            b_lo + (uint32_t)(dx + k * 16), bhi, IDESC, (i > 0 || k > 0) ? 1u : 0u);
+                    // the x view of tap dx starts dx slots further
+                    ts_mma1(tmem + (uint32_t)(dx * NA), a_lo + (uint32_t)((XM ? dx : 0) + k * 16), ahi,
+                            b_lo + (uint32_t)((XM ? 0 : dx) + k * 16), bhi, IDESC, (i > 0 || k > 0) ? 1u : 0u);
             }
             tc_commit_one(&empty[s]);
             if (++s == stages) {
@@ -274,21 +291,23 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
                 a.bpart[(long long)split * a.Cout + co] = v;
             }
         }
-        // wait for the last MMAs, then TMEM lane (32 q + lane) = output channel
+        // wait for the last MMAs, then TMEM lane (32 q + lane) = output
+        // channel (with XM: input channel)
         const bool done = __all_sync(0xffffffffu, tc_bar_wait(mdone, 0u));
         if (!done && lane == 0 && a.err) atomicOr(a.err, 1 << 6);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int col = 32 * q + lane;
         const int co = cob * TW_MB + col;
-        const bool valid = col < gvalid * 8 && nitems > 0 && done;
-        float* out = a.part + ((long long)split * a.Cout + co) * 9 * a.Cin;
+        const bool valid = col < (XM ? xvalid : gvalid) * 8 && nitems > 0 && done;
+        float* out = XM ? a.part + (long long)split * a.Cout * 9 * a.Cin + cib * NBW + col
+                        : a.part + ((long long)split * a.Cout + co) * 9 * a.Cin;
 #pragma unroll 1
         for (int dx = 0; dx < 3; ++dx) {
             const int tap = dy * 3 + dx;
 #pragma unroll 1
-            for (int cc = 0; cc < NBW; cc += 32) {
+            for (int cc = 0; cc < NA; cc += 32) {
                 uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(dx * NBW + cc);
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(dx * NA + cc);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -299,7 +318,12 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
                       "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (valid) {
+                if (valid && XM) {
+                    // column j = output channel cc + j: [co][tap][ci], this lane's ci
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        out[((long long)(cc + j) * 9 + tap) * a.Cin] = __uint_as_float(v[j]);
+                } else if (valid) {
                     float4* o4 = reinterpret_cast<float4*>(out + (long long)tap * a.Cin + cib * NBW + cc);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
