@@ -67,6 +67,12 @@ template <> struct Store<LB_PREC_FP16_DEV> {
     static constexpr int NPLANES = 20;
     static constexpr bool SPLIT = true;
     static __device__ __forceinline__ real dec(elem h) { return __half2float(h); }
+    // acc + dec(h) in one mixed-precision add (the widening is exact, so this
+    // rounds once, as the separate decode and FP32 add do)
+    static __device__ __forceinline__ real add_dec(elem h, real acc) {
+        asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc) : "h"(__half_as_ushort(h)));
+        return acc;
+    }
     static __device__ __forceinline__ elem enc(real d) { return __float2half_rn(d); }
     static __device__ __forceinline__ unsigned short bits(elem h) { return __half_as_ushort(h); }
     static __device__ __forceinline__ elem from_bits(unsigned short b) { return __ushort_as_half(b); }
@@ -79,6 +85,10 @@ template <> struct Store<LB_PREC_BF16_DEV> {
     static constexpr int NPLANES = 20;
     static constexpr bool SPLIT = true;
     static __device__ __forceinline__ real dec(elem h) { return __bfloat162float(h); }
+    static __device__ __forceinline__ real add_dec(elem h, real acc) {
+        asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc) : "h"(__bfloat16_as_ushort(h)));
+        return acc;
+    }
     static __device__ __forceinline__ elem enc(real d) { return __float2bfloat16_rn(d); }
     static __device__ __forceinline__ unsigned short bits(elem h) { return __bfloat16_as_ushort(h); }
     static __device__ __forceinline__ elem from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
@@ -102,6 +112,16 @@ __device__ __forceinline__ typename S::real dev_of(const typename S::elem* p, in
     } else {
         return *p;
     }
+}
+
+// acc + dev_of(p, ...) for a 16-bit mode (the moving populations through the
+// mixed-precision add).
+template <class S>
+__device__ __forceinline__ float acc_dev(const typename S::elem* p, int plane_idx, long long lo_off, float acc) {
+    static_assert(S::SPLIT, "deviation storage only");
+    if (is_rest_plane(plane_idx))
+        return acc + __uint_as_float(((unsigned)S::bits(p[0]) << 16) | (unsigned)S::bits(p[lo_off]));
+    return S::add_dec(*p, acc);
 }
 
 // Population of plane plane_idx (0..17) at p; `stride` is the distance
@@ -186,6 +206,15 @@ struct KParams {
         float omega_f, omega_g, guo_pre, corr_pre, G, two_over_G, beta, half_1mbeta;
         float T_hot, T_cold, g_grav, T_in, T_w, U_in, a, b, R, cv, inv_cv, T_psi;
     } f;
+    // factors of the deviation-variable collision (collide_dev) in FMA form,
+    // per weight class ([0] axis w = 1/9, [1] diagonal w = 1/36)
+    struct {
+        float omc_f, omc_g;        // 1 - omega_f, 1 - omega_g
+        float wo_f[2], wo_g[2];    // omega_f w, omega_g w
+        float ocw_f[2], ocw_g[2];  // omega_f cw_f, omega_g cw_g
+        float gw[2], gw9[2], gw3[2];  // guo w, 9 guo w, 3 guo w
+        float cw3[2];              // 3 corr w
+    } d;
 };
 
 // Set KParams::f from the double fields (call after they are final).
@@ -210,6 +239,19 @@ inline void kp_fill_float(KParams& k) {
     k.f.cv = (float)k.cv;
     k.f.inv_cv = (float)k.inv_cv;
     k.f.T_psi = (float)k.T_psi;
+    k.d.omc_f = (float)(1.0 - k.omega_f);
+    k.d.omc_g = (float)(1.0 - k.omega_g);
+    for (int c = 0; c < 2; ++c) {
+        const double w = c == 0 ? 1.0 / 9.0 : 1.0 / 36.0;
+        k.d.wo_f[c] = (float)(k.omega_f * w);
+        k.d.wo_g[c] = (float)(k.omega_g * w);
+        k.d.ocw_f[c] = (float)(k.omega_f * (double)k.cw_f[1 + c]);
+        k.d.ocw_g[c] = (float)(k.omega_g * (double)k.cw_g[1 + c]);
+        k.d.gw[c] = (float)(k.guo_pre * w);
+        k.d.gw9[c] = (float)(9.0 * k.guo_pre * w);
+        k.d.gw3[c] = (float)(3.0 * k.guo_pre * w);
+        k.d.cw3[c] = (float)(3.0 * k.corr_pre * w);
+    }
 }
 
 // a parameter in the arithmetic type `real`.  Translation units built with
@@ -290,13 +332,13 @@ __device__ __forceinline__ void put_pop_ghost(typename S::elem* p, long long str
 // Store one value per plane at d (plane stride `stride`) and, for the few
 // threads whose column has a periodic ghost copy, once more nx columns right
 // (ghost_lo) or left (ghost_hi): one branch per site, not one per plane.
+// The periodic ghost copies of a site's planes (columns within STRIP_GHOST of
+// either edge are also written nx columns further in, see put_planes).
 template <class S, typename IT>
-__device__ __forceinline__ void put_planes(typename S::elem* d, IT stride, int nx, const typename S::elem* v,
-                                           bool ghost_lo, bool ghost_hi) {
+__device__ __forceinline__ void put_ghost_copies(typename S::elem* d, IT stride, int nx, const typename S::elem* v,
+                                                 bool ghost_lo, bool ghost_hi) {
     // (the plane offset is formed in IT, the signed column shift by pointer
     // arithmetic: an unsigned IT must never absorb a negative shift)
-#pragma unroll
-    for (int p = 0; p < S::NPLANES; ++p) d[(IT)p * stride] = v[p];
     if (ghost_lo || ghost_hi) {
         const int sh = ghost_lo ? nx : -nx;
 #pragma unroll
@@ -312,6 +354,14 @@ __device__ __forceinline__ void put_planes(typename S::elem* d, IT stride, int n
             }
         }
     }
+}
+
+template <class S, typename IT>
+__device__ __forceinline__ void put_planes(typename S::elem* d, IT stride, int nx, const typename S::elem* v,
+                                           bool ghost_lo, bool ghost_hi) {
+#pragma unroll
+    for (int p = 0; p < S::NPLANES; ++p) d[(IT)p * stride] = v[p];
+    put_ghost_copies<S>(d, stride, nx, v, ghost_lo, ghost_hi);
 }
 
 // The post-collision populations of one site into storage; d points at the
@@ -634,7 +684,12 @@ __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9],
 //   f^eq_i - base_i = w_i (rho - rho0) + (w_i rho0 - base_i) + w_i rho (4.5 (e.u)^2 - 1.5 u^2) + 3 w_i rho e.u
 //   c_v T f^eq_i - base_g,i = w_i (e - e0) + (w_i e0 - base_g,i) + w_i e (4.5 (e.u)^2 - 1.5 u^2) + 3 w_i e e.u
 // so no base is added to or subtracted from a population (fewer operations,
-// and the small deviations keep their own FP32 precision).
+// and the small deviations keep their own FP32 precision).  The update
+//   h_i <- h_i + omega_f (f^eq_i - base_i - h_i) + F_i
+// is evaluated as (1 - omega_f) h_i + P +- Q, with P = omega_f (even part of
+// f^eq - base) + (even part of F_i) and Q = omega_f (odd part) + (odd part),
+// the same for q_i with C_i of Eq. (25) in its odd part: every term is a
+// fused multiply-add of per-site factors and the constants in kp.d.
 template <bool EQ24>
 __device__ __forceinline__ void collide_dev(const KParams& kp, float h[9], float q[9], float Hf, float Hg,
                                             float Fx, float Fy) {
@@ -646,63 +701,77 @@ __device__ __forceinline__ void collide_dev(const KParams& kp, float h[9], float
     const float ux = (mx + 0.5f * Fx) * inv_rho;
     const float uy = (my + 0.5f * Fy) * inv_rho;
     const float cvT = e * inv_rho;
-    const float om_f = kp.f.omega_f, om_g = kp.f.omega_g;
-    const float guo = kp.f.guo_pre, corr = kp.f.corr_pre;
-    const float m15u2 = -1.5f * (ux * ux + uy * uy);
-    const float uF3 = 3.0f * (ux * Fx + uy * Fy);
-    const float Aa = (float)(1.0 / 9.0) * drho + kp.cw_f[1], Ad = (float)(1.0 / 36.0) * drho + kp.cw_f[2];
-    const float Ba = (float)(1.0 / 9.0) * de + kp.cw_g[1], Bd = (float)(1.0 / 36.0) * de + kp.cw_g[2];
+    const float m15u2 = -1.5f * fmaf(ux, ux, uy * uy);
+    const float uF3 = 3.0f * fmaf(ux, Fx, uy * Fy);
+    // per weight class c (axis, diagonal):
+    //   P0 = omega_f (w drho + cw_f) + omega_f w rho (-1.5 u^2) - guo w 3 u.F
+    //   P  = P0 + 4.5 omega_f w rho (e.u)^2 + 9 guo w (e.u)(e.F)
+    //   Q  = 3 omega_f w rho (e.u) + 3 guo w (e.F)
+    //   G0 = omega_g (w de + cw_g) + omega_g w e (-1.5 u^2)
+    //   Pg = G0 + 4.5 omega_g w e (e.u)^2,   Qg = 3 omega_g w e (e.u) [+ 3 corr w c_v T (e.F)]
+    float P0[2], r45[2], r3[2], G0[2], e45[2], e3[2], c3[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float rwo = kp.d.wo_f[c] * rho, ewo = kp.d.wo_g[c] * e;
+        P0[c] = fmaf(-kp.d.gw[c], uF3, fmaf(rwo, m15u2, fmaf(kp.d.wo_f[c], drho, kp.d.ocw_f[c])));
+        r45[c] = 4.5f * rwo;
+        r3[c] = 3.0f * rwo;
+        G0[c] = fmaf(ewo, m15u2, fmaf(kp.d.wo_g[c], de, kp.d.ocw_g[c]));
+        e45[c] = 4.5f * ewo;
+        e3[c] = 3.0f * ewo;
+        c3[c] = EQ24 ? kp.d.cw3[c] * cvT : 0.0f;
+    }
+    const float omc_f = kp.d.omc_f, omc_g = kp.d.omc_g;
     // pairs of opposite directions (1,3), (2,4), (5,7), (8,6) share the even parts
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
         const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
-        const float w = (float)wd(i);
-        const float A = p < 2 ? Aa : Ad, B = p < 2 ? Ba : Bd;
-        const float eu = (float)ex(i) * ux + (float)ey(i) * uy;
-        const float eF = (float)ex(i) * Fx + (float)ey(i) * Fy;
-        const float sq = 4.5f * eu * eu + m15u2;
-        const float rw = rho * w, ew = e * w;
-        const float fe = A + rw * sq, fo = 3.0f * rw * eu;
-        const float ge = B + ew * sq, go = 3.0f * ew * eu;
-        const float Fe = guo * w * (9.0f * eu * eF - uF3), Fo = 3.0f * guo * w * eF;
-        h[i] = h[i] + om_f * ((fe + fo) - h[i]) + (Fe + Fo);
-        h[k] = h[k] + om_f * ((fe - fo) - h[k]) + (Fe - Fo);
-        float gi = q[i] + om_g * ((ge + go) - q[i]);
-        float gk = q[k] + om_g * ((ge - go) - q[k]);
-        if (EQ24) {
-            const float C = 3.0f * corr * w * cvT * eF;
-            gi += C;
-            gk -= C;
-        }
-        q[i] = gi;
-        q[k] = gk;
+        const int c = p < 2 ? 0 : 1;
+        const float eu = p == 0 ? ux : (p == 1 ? uy : (p == 2 ? ux + uy : ux - uy));
+        const float eF = p == 0 ? Fx : (p == 1 ? Fy : (p == 2 ? Fx + Fy : Fx - Fy));
+        const float eu2 = eu * eu;
+        const float P = fmaf(kp.d.gw9[c], eu * eF, fmaf(r45[c], eu2, P0[c]));
+        const float Q = fmaf(r3[c], eu, kp.d.gw3[c] * eF);
+        h[i] = fmaf(omc_f, h[i], P + Q);
+        h[k] = fmaf(omc_f, h[k], P - Q);
+        const float Pg = fmaf(e45[c], eu2, G0[c]);
+        const float Qg = EQ24 ? fmaf(c3[c], eF, e3[c] * eu) : e3[c] * eu;
+        q[i] = fmaf(omc_g, q[i], Pg + Qg);
+        q[k] = fmaf(omc_g, q[k], Pg - Qg);
     }
 }
 
-// store_site for deviations already computed by collide_dev (16-bit modes):
-// the moving populations are rounded to 16 bits, the rest populations close
-// the stored deviation sums (see store_site).
-template <class S, typename IT>
-__device__ __forceinline__ void store_site_dev(typename S::elem* d, IT stride, const KParams& kp,
-                                               const float h[9], const float q[9], float Hf, float Hg,
-                                               bool ghost_lo, bool ghost_hi) {
+// The stored form of a site whose deviations collide_dev computed (16-bit
+// modes): the moving populations rounded to 16 bits, the rest populations
+// closing the stored deviation sums (see store_site), as the NPLANES values of
+// the site's planes.
+template <class S>
+__device__ __forceinline__ void encode_site_dev(const float h[9], const float q[9], float Hf, float Hg,
+                                                typename S::elem v[S::NPLANES]) {
     static_assert(S::SPLIT, "deviation storage only");
-    using elem = typename S::elem;
-    elem v[S::NPLANES];
     float sf = 0.0f, sg = 0.0f;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         v[i] = S::enc(h[i]);
         v[9 + i] = S::enc(q[i]);
-        sf += S::dec(v[i]);
-        sg += S::dec(v[9 + i]);
+        sf = S::add_dec(v[i], sf);
+        sg = S::add_dec(v[9 + i], sg);
     }
     const unsigned bf = __float_as_uint(Hf - sf), bg = __float_as_uint(Hg - sg);
     v[0] = S::from_bits((unsigned short)(bf >> 16));
     v[18] = S::from_bits((unsigned short)(bf & 0xffffu));
     v[9] = S::from_bits((unsigned short)(bg >> 16));
     v[19] = S::from_bits((unsigned short)(bg & 0xffffu));
+}
+
+// store_site for deviations already computed by collide_dev (16-bit modes).
+template <class S, typename IT>
+__device__ __forceinline__ void store_site_dev(typename S::elem* d, IT stride, const KParams& kp,
+                                               const float h[9], const float q[9], float Hf, float Hg,
+                                               bool ghost_lo, bool ghost_hi) {
+    typename S::elem v[S::NPLANES];
+    encode_site_dev<S>(h, q, Hf, Hg, v);
     put_planes<S>(d, stride, kp.nx, v, ghost_lo, ghost_hi);
 }
 

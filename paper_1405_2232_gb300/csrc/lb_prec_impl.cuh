@@ -8,6 +8,7 @@
 #include "lb_fd_strip.cuh"
 #include "lb_launch.h"
 #include "lb_step_strip.cuh"
+#include "lb_step_strip_dev.cuh"
 
 namespace lbgb {
 
@@ -45,15 +46,27 @@ cudaError_t step_tile(const StepLaunch& L) {
 // pick one precision's launcher for all).
 
 // Stage count per strip width: the deepest ring that still lets two CTAs
-// share an SM (228 KB of shared memory).
+// share an SM (228 KB of shared memory).  The 16-bit kernel also holds
+// DEV_OUT_BUFS row buffers of the collided rows.
 template <int BX>
 constexpr int strip_stages() {
-    constexpr size_t stage = (size_t)Store<LBGB_PREC>::NPLANES * (BX + 2 * StripCfg<LBGB_PREC>::HALO) *
-                             StripCfg<LBGB_PREC>::ES;
-    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<LBGB_PREC>::real);
+    using C = StripCfg<LBGB_PREC>;
+    constexpr int NPL = Store<LBGB_PREC>::NPLANES;
+    constexpr size_t stage = (size_t)NPL * (BX + 2 * C::HALO) * C::ES;
+    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename C::real);
+    constexpr size_t out = Store<LBGB_PREC>::SPLIT ? (size_t)DEV_OUT_BUFS * NPL * BX * C::ES : 0;
     constexpr size_t budget = 110 * 1024 - 32;
-    constexpr size_t s = (budget - ring) / stage;
+    constexpr size_t s = (budget - ring - out) / stage;
     return s > 12 ? 12 : (int)s;
+}
+
+// 16-bit deviation storage: k_step_strip_dev; FP32 / FP64: k_step_strip.
+template <int BX, int ST, bool EQ24, int BM>
+auto strip_kernel() {
+    if constexpr (Store<LBGB_PREC>::SPLIT)
+        return k_step_strip_dev<LBGB_PREC, BX, ST, EQ24, BM>;
+    else
+        return k_step_strip<LBGB_PREC, BX, ST, EQ24, BM>;
 }
 
 template <int BX, bool EQ24, int BM>
@@ -61,8 +74,11 @@ cudaError_t strip_launch(const StepLaunch& L) {
     using E = typename Store<LBGB_PREC>::elem;
     constexpr int ST = strip_stages<BX>();
     static_assert(ST >= 3, "strip kernel needs at least three stages");
-    constexpr size_t smem = strip_smem_bytes<LBGB_PREC, BX, ST>();
-    auto kern = k_step_strip<LBGB_PREC, BX, ST, EQ24, BM>;
+    constexpr bool DEV = Store<LBGB_PREC>::SPLIT;
+    constexpr size_t smem =
+        DEV ? strip_dev_smem_bytes<LBGB_PREC, BX, ST>() : strip_smem_bytes<LBGB_PREC, BX, ST>();
+    static_assert(smem <= 110 * 1024, "two CTAs per SM");
+    auto kern = strip_kernel<BX, ST, EQ24, BM>();
     static unsigned long long configured = 0;  // per instantiation, one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -185,6 +185,58 @@ __host__ __device__ constexpr int strip_threads() {
     return BX + 64;
 }
 
+// The producer warp of a strip kernel: for every job j (pre-collision row
+// y_start - 1 + j) it waits until the job's stage is released, then lane 0
+// arms the stage's "full" mbarrier with the byte count and lanes
+// 0..NPLANES-1 each issue the copy of one plane-row segment (columns
+// x0 - HALO .. x0 + W + HALO - 1, ghost columns at the lattice edges).  (One
+// lane issuing all of them measured slower.)  On a
+// timeout of the release wait it records LB_ERR_TIMEOUT and stops issuing
+// (the consumers then time out on "full"); it returns only when every copy it
+// issued has landed (bounded).
+template <class S, int STAGES, int SEGW>
+__device__ __forceinline__ void strip_produce(const typename S::elem* __restrict__ src, typename S::elem* stage,
+                                              uint64_t* full, uint64_t* empty, const KParams& kp, int lane,
+                                              int njobs, int y_start, int x0, int W) {
+    using elem = typename S::elem;
+    constexpr int ES = (int)sizeof(elem);
+    constexpr int HALO = 16 / ES;
+    constexpr int NPL = S::NPLANES;
+    const int ny = kp.ny;
+    const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
+    const uint32_t cb = strip_copy_bytes<ES, HALO>(W);
+    int issued = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const int s = j % STAGES;
+        if (j >= STAGES) {
+            // the stage's previous job (j - STAGES) must have been released;
+            // the warp takes one decision (its lanes poll the barrier independently)
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1),
+                                                           kp.wait_cycles))) {
+                if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
+                break;
+            }
+        }
+        int y = y_start - 1 + j;
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)NPL * cb);
+        __syncwarp();
+        if (lane < NPL) {
+            const int i = lane;
+            // direction of the plane (planes 18, 19: low halves of the rest populations)
+            const int d = i < 9 ? i : (i < 18 ? i - 9 : 0);
+            int sy = y - ey(d);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
+            bulk_copy_g2s(stage + ((size_t)s * NPL + i) * SEGW, row + (x0 - HALO), cb, &full[s]);
+        }
+        issued = j + 1;
+    }
+    if (lane == 0)
+        for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
+            (void)mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+}
+
 // Block: BX column threads (BX/32 warps), one halo warp and one producer warp.
 //   producer: for every job (pre-collision row) waits until its stage is
 //     released, then lane 0 arms the stage's "full" mbarrier with the byte
@@ -244,42 +296,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     __syncthreads();
 
     if (t >= BX + 32) {
-        // ------------------------------------------------ producer warp
-        const int lane = t - BX - 32;
-        int issued = 0;
-        for (int j = 0; j < njobs; ++j) {
-            const int s = j % STAGES;
-            if (j >= STAGES) {
-                // the stage's previous job (j - STAGES) must have been released;
-                // on timeout stop issuing (the consumers then time out on "full")
-                // the warp takes one decision (its lanes poll the barrier independently)
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((j / STAGES) - 1) & 1),
-                                                               kp.wait_cycles))) {
-                    if (lane == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
-                    break;
-                }
-            }
-            int y = y_start - 1 + j;
-            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-            const uint32_t cb = strip_copy_bytes<ES, HALO>(W);
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)NPL * cb);
-            __syncwarp();
-            if (lane < NPL) {
-                const int i = lane;
-                // direction of the plane (planes 18, 19: low halves of the rest populations)
-                const int d = i < 9 ? i : (i < 18 ? i - 9 : 0);
-                int sy = y - ey(d);
-                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-                const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
-                // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
-                bulk_copy_g2s(stage + ((size_t)s * NPL + i) * SEGW, row + (x0 - HALO), cb, &full[s]);
-            }
-            issued = j + 1;
-        }
-        // leave only when every copy this CTA issued has landed (bounded)
-        if (lane == 0)
-            for (int j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
-                (void)mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+        strip_produce<S, STAGES, SEGW>(src, stage, full, empty, kp, t - BX - 32, njobs, y_start, x0, W);
         return;
     }
 

@@ -36,7 +36,8 @@ def test_no_symbol_shared_between_precision_objects():
 
 def test_every_strip_kernel_width_is_compiled():
     """The strip kernel exists at width 128 for every precision and at 256 for the
-    FP32 and 16-bit modes (the launcher returns cudaErrorInvalidValue otherwise)."""
+    FP32 and 16-bit modes (the launcher returns cudaErrorInvalidValue otherwise);
+    the 16-bit modes use their own strip kernel, k_step_strip_dev."""
     from paper_1405_2232_gb300 import build
     build.build()
     want = {"fp64": ["128"], "fp32": ["128", "256"], "fp16": ["128", "256"], "bf16": ["128", "256"]}
@@ -45,5 +46,6 @@ def test_every_strip_kernel_width_is_compiled():
         out = subprocess.run(["nm", "--defined-only", os.path.join(BUILD, f"lb_prec_{name}.o")],
                              capture_output=True, text=True, check=True).stdout
         for w in widths:
-            tag = f"k_step_stripILi{prec_id[name]}ELi{w}E"
+            kern = "k_step_strip_dev" if name in ("fp16", "bf16") else "k_step_strip"
+            tag = f"{kern}ILi{prec_id[name]}ELi{w}E"
             assert tag in out, f"{name}: no strip kernel of width {w}"
