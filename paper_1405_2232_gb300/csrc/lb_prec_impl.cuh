@@ -47,15 +47,16 @@ cudaError_t step_tile(const StepLaunch& L) {
 
 // Stage count per strip width: the deepest ring that still lets two CTAs
 // share an SM (228 KB of shared memory).  The 16-bit kernel also holds
-// DEV_OUT_BUFS row buffers of the collided rows.
+// DEV_OUT_BUFS row buffers of the collided rows and a six-row psi ring.
 template <int BX>
 constexpr int strip_stages() {
     using C = StripCfg<LBGB_PREC>;
     constexpr int NPL = Store<LBGB_PREC>::NPLANES;
     constexpr size_t stage = (size_t)NPL * (BX + 2 * C::HALO) * C::ES;
-    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename C::real);
-    constexpr size_t out = Store<LBGB_PREC>::SPLIT ? (size_t)DEV_OUT_BUFS * NPL * BX * C::ES : 0;
-    constexpr size_t budget = 110 * 1024 - 32;
+    constexpr bool DEV = Store<LBGB_PREC>::SPLIT;
+    constexpr size_t ring = (size_t)(DEV ? 2 * DEV_PSI_ROWS : 8) * (BX + 2) * sizeof(typename C::real);
+    constexpr size_t out = DEV ? (size_t)DEV_OUT_BUFS * NPL * BX * C::ES : 0;
+    constexpr size_t budget = 110 * 1024 - 32 - (DEV ? (2 * 12 + 2) * 8 : 0);
     constexpr size_t s = (budget - ring - out) / stage;
     return s > 12 ? 12 : (int)s;
 }
