@@ -15,6 +15,7 @@
 
 #include "lb.h"
 #include "lb_launch.h"
+#include "tensor_map.h"
 
 using namespace lbgb;
 
@@ -171,6 +172,8 @@ struct lb_ctx {
     int64_t ref_time = 0;
     int64_t t = 0;
     int nchunks = 1;            // strip kernel: row chunks per strip
+    bool have_out_map = false;  // 16-bit strip contexts: out_map[b] describes buf[b]
+    CUtensorMap out_map[2];
     long long pitch = 0, plane = 0;  // population layout (elements)
     // finite-difference temperature treatment (Eqs. 26-27)
     bool fd = false;
@@ -259,6 +262,7 @@ cudaError_t dispatch_step(const lb_ctx* c, const void* src, void* dst) {
     L.by = c->p.tile_y;
     L.nchunks = c->nchunks;
     L.stream = c->stream;
+    if (c->have_out_map) L.dst_map = &c->out_map[dst == c->buf[0] ? 0 : 1];
     if (c->p.walls == LB_WALLS_CHANNEL)
         return c->p.precision == LB_PREC_FP64 ? launch_step_channel_fp64(L) : launch_step_channel_fp32(L);
     if (c->kp.walls)
@@ -509,6 +513,31 @@ lb_status create(const lb_params* p, void* stream, lb_ctx** out) {
         int nch = (2 * sms) / strips;
         nch = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
         c->nchunks = nch;
+    }
+    if (strip && !c->fd && !c->kp.walls &&
+        (p->precision == LB_PREC_FP16_DEV || p->precision == LB_PREC_BF16_DEV)) {
+        // the 16-bit strip kernel stores each collided row of a strip with
+        // one tensor copy: dims (nx columns, ny rows, planes), box (strip
+        // width, 1 row, every plane); columns past nx are clipped by the copy
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) {
+            release(c);
+            return fail(LB_ERR_CUDA, "the driver provides no cuTensorMapEncodeTiled");
+        }
+        const int npl = pop_planes(p->precision);
+        const cuuint64_t dims[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)npl};
+        const cuuint64_t strides[2] = {(cuuint64_t)(pitch * (long long)es), (cuuint64_t)(plane * (long long)es)};
+        const cuuint32_t box[3] = {(cuuint32_t)c->p.tile_x, 1, (cuuint32_t)npl};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        for (int b = 0; b < 2; ++b) {
+            if (enc(&c->out_map[b], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, c->buf[b], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+                release(c);
+                return fail(LB_ERR_CUDA, "encoding the tensor map of population buffer %d", b);
+            }
+        }
+        c->have_out_map = true;
     }
     *out = c;
     return LB_OK;

@@ -2,6 +2,7 @@
 // per-precision kernel translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lb_device.cuh"
@@ -18,6 +19,10 @@ struct StepLaunch {
     int bx, by;     // CTA tile; by == 0: strip kernel of width bx
     int nchunks;    // strip kernel: row chunks per strip
     cudaStream_t stream;
+    // 16-bit strip kernel: tensor map of dst (x: nx columns, y: ny rows,
+    // z: the planes; box bx x 1 x NPLANES) that its collided rows are stored
+    // through; nullptr elsewhere
+    const CUtensorMap* dst_map = nullptr;
 };
 
 struct MomentsLaunch {

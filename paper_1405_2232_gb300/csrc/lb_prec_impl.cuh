@@ -90,8 +90,14 @@ cudaError_t strip_launch(const StepLaunch& L) {
         if (dev < 64) configured |= 1ULL << dev;
     }
     const dim3 grid((L.kp.nx + BX - 1) / BX, L.nchunks);
-    kern<<<grid, strip_threads<BX>(), smem, L.stream>>>(static_cast<const E*>(L.src),
-                                                         static_cast<E*>(L.dst), L.kp, L.nchunks);
+    if constexpr (DEV) {
+        if (!L.dst_map) return cudaErrorInvalidValue;  // the kernel stores through it
+        kern<<<grid, strip_threads<BX>(), smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
+                                                             L.kp, L.nchunks, *L.dst_map);
+    } else {
+        kern<<<grid, strip_threads<BX>(), smem, L.stream>>>(static_cast<const E*>(L.src), static_cast<E*>(L.dst),
+                                                             L.kp, L.nchunks);
+    }
     return cudaGetLastError();
 }
 

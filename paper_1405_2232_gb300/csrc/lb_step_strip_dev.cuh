@@ -11,23 +11,24 @@
 //     2k - 1 and 2k), so the per-row bookkeeping, waits and barrier are
 //     paid once per two sites;
 //   - the collided rows are written to shared-memory row buffers (job m
-//     into buffer m mod 3) and leave the CTA as one bulk copy per
-//     plane row (cp.async.bulk shared -> global), so no thread forms twenty
-//     64-bit store addresses per site; columns past the last whole 16-byte
-//     unit of the strip and the periodic ghost copies of the edge columns are
-//     stored by their threads directly.  Lanes 0..NPLANES-1 of the halo warp
-//     issue the copies (a copy's operands are uniform registers, so a warp
-//     issuing twenty of them steps through its lanes one by one: in a column
-//     warp this delayed every barrier; one lane issuing all twenty measured
-//     slower still): after the barrier of iteration k they copy the row
-//     collided second in iteration k - 1, then wait on an mbarrier on which
-//     the column warps arrive once the first row of iteration k is written
-//     (and fenced for the async proxy) and copy that one, and before the next
-//     barrier wait until both copies have read their buffers (waiting for
-//     the second row within the iteration put the halo warp, which also
-//     computes two psi sites per iteration, last at every barrier; two
-//     buffers with an mbarrier that frees the second before it is rewritten
-//     measured slower than three);
+//     into buffer m mod 3, laid out [plane][column]) and leave the CTA as
+//     one tensor copy each (cp.async.bulk.tensor.3d shared -> global through
+//     the map of the destination buffer: x the column, y the row, z the
+//     plane; the copy clips the columns past nx), so no thread forms twenty
+//     64-bit store addresses per site; the periodic ghost copies of the edge
+//     columns are stored by their threads directly.  Lane 0 of the halo warp
+//     issues the copies (twenty per-plane bulk copies, whose operands are
+//     uniform registers, made the issuing warp step through its lanes one by
+//     one, which loaded its SM sub-partition more than the others): after
+//     the barrier of iteration k it copies the row collided second in
+//     iteration k - 1, then waits on an mbarrier on which the column warps
+//     arrive once the first row of iteration k is written (and fenced for
+//     the async proxy) and copies that one, and before the next barrier
+//     waits until both copies have read their buffers (waiting for the
+//     second row within the iteration put the halo warp, which also computes
+//     two psi sites per iteration, last at every barrier; two buffers with an
+//     mbarrier that frees the second before it is rewritten measured slower
+//     than three);
 //   - the deviation sums Hf, Hg of a site, formed when psi of its row is
 //     computed, are kept in registers until the site collides (the same sums
 //     in the same order, so the result does not change);
@@ -39,15 +40,20 @@
 // loop at the same iteration.
 #pragma once
 
+#include <cuda.h>
+
 #include "lb_step_strip.cuh"
 
 namespace lbgb {
 
 constexpr int DEV_OUT_BUFS = 3;  // row buffers: job m collides into buffer m mod 3
 
-__device__ __forceinline__ void bulk_copy_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"(smem_u32(ssrc)), "r"(bytes)
+// 3D tensor copy shared -> global of the box at (x, y, z) (bulk async group
+// of the issuing thread)
+__device__ __forceinline__ void tensor_store_3d(const CUtensorMap* map, const void* ssrc, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(ssrc)), "r"(x), "r"(y), "r"(z)
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit_group() {
@@ -96,9 +102,9 @@ __device__ __forceinline__ void dev_psi_site(const KParams& kp, const typename S
     Hg = hg;
 }
 
-// Eq. (1) + F_i and Eq. (7) / (24) for one site, stored: into the row buffer
-// column o (then fenced for the bulk copy) or, for o == nullptr, straight to
-// its planes at d; the ghost copies of an edge column straight to memory.
+// Eq. (1) + F_i and Eq. (7) / (24) for one site: its stored form into row
+// buffer column o (fenced for the tensor copy), the ghost copies of an edge
+// column straight to its planes at d.
 template <class S, int SEGW, int BX, bool EQ24>
 __device__ __forceinline__ void dev_collide_site(const KParams& kp, const typename S::elem* st, int c, float Hf,
                                                  float Hg, float Fx, float Fy, typename S::elem* d,
@@ -114,20 +120,17 @@ __device__ __forceinline__ void dev_collide_site(const KParams& kp, const typena
     collide_dev<EQ24>(kp, h, q, Hf, Hg, Fx, Fy);
     typename S::elem v[NPL];
     encode_site_dev<S>(h, q, Hf, Hg, v);
-    if (o) {
 #pragma unroll
-        for (int p = 0; p < NPL; ++p) o[p * BX] = v[p];
-        fence_proxy_async_smem();
-        put_ghost_copies<S>(d, plane, kp.nx, v, ghost_lo, ghost_hi);
-    } else {
-        put_planes<S>(d, plane, kp.nx, v, ghost_lo, ghost_hi);
-    }
+    for (int p = 0; p < NPL; ++p) o[p * BX] = v[p];
+    fence_proxy_async_smem();
+    put_ghost_copies<S>(d, plane, kp.nx, v, ghost_lo, ghost_hi);
 }
 
 template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
 __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     k_step_strip_dev(const typename Store<PREC>::elem* __restrict__ src,
-                     typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks) {
+                     typename Store<PREC>::elem* __restrict__ dst, const KParams kp, int nchunks,
+                     const __grid_constant__ CUtensorMap dst_map) {
     using S = Store<PREC>;
     static_assert(S::SPLIT, "16-bit deviation storage only");
     using C = StripCfg<PREC>;
@@ -138,7 +141,6 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     constexpr int RW = BX + 2;
     constexpr int NPL = S::NPLANES;
     constexpr int ES = C::ES;
-    static_assert(NPL <= 32, "one issuing lane per plane in the halo warp");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     elem* stage = reinterpret_cast<elem*>(smem_raw);                 // [STAGES][NPL][SEGW]
@@ -190,9 +192,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     const int r_psi = halo ? (lane == 0 ? 0 : W + 1) : t + 1;
     const bool has_psi = halo ? lane < 2 : t < W;
     const int c_psi = r_psi - 1 + HALO;   // smem column of the psi site
-    const int Wb = W & ~(16 / ES - 1);    // columns leaving by bulk copy (whole 16-byte units)
-    const uint32_t out_bytes = (uint32_t)Wb * ES;
-    const bool issuer = halo && lane < NPL;  // halo lane p copies plane p of each collided row out
+    const bool issuer = halo && lane == 0;  // copies the collided rows out
     const int xg = x0 + t;
     const bool ghost_lo = xg < STRIP_GHOST, ghost_hi = xg >= nx - STRIP_GHOST;
     const int c = t + HALO;               // smem column of the collided site
@@ -236,18 +236,16 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             // the row collided second in the iteration before is complete
             // since the barrier (its writers fenced before arriving)
             const int mp = j0 - 2;
-            if (issuer && k >= 1 && mp >= 1 && mp <= njobs - 2 && out_bytes > 0) {
+            if (issuer && k >= 1 && mp >= 1 && mp <= njobs - 2) {
                 const int bP = b0 + 1 == DEV_OUT_BUFS ? 0 : b0 + 1;  // (2k - 2) mod 3
-                bulk_copy_s2g(dst + ((size_t)lane * plane + (size_t)(y_start - 1 + mp) * pitch + (size_t)x0),
-                              outb + ((size_t)bP * NPL + lane) * BX, out_bytes);
+                tensor_store_3d(&dst_map, outb + (size_t)bP * NPL * BX, x0, y_start - 1 + mp, 0);
                 bulk_commit_group();
             }
             // the first row of this iteration, once every column warp has written it
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(written, (uint32_t)(k & 1), kp.wait_cycles))) {
                 s_abort[(k + 1) & 1] = 1;  // every consumer leaves after the next barrier
-            } else if (issuer && c0 && out_bytes > 0) {
-                bulk_copy_s2g(dst + ((size_t)lane * plane + (size_t)(y_start - 1 + m0) * pitch + (size_t)x0),
-                              outb + ((size_t)bA * NPL + lane) * BX, out_bytes);
+            } else if (issuer && c0) {
+                tensor_store_3d(&dst_map, outb + (size_t)bA * NPL * BX, x0, y_start - 1 + m0, 0);
                 bulk_commit_group();
             }
             // both buffers copied here are written again from the next iteration on
@@ -269,7 +267,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     const int y = y_start - 1 + m0;
                     dev_collide_site<S, SEGW, BX, EQ24>(kp, stage + sm * (NPL * SEGW), c, Hf_p, Hg_p, FxA, FyA,
                                                         dst + ((size_t)y * pitch + (size_t)xg),
-                                                        t < Wb ? outb + (size_t)bA * NPL * BX + t : nullptr, plane,
+                                                        outb + (size_t)bA * NPL * BX + t, plane,
                                                         ghost_lo, ghost_hi);
                 }
                 __syncwarp();
@@ -278,7 +276,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     const int y = y_start - 1 + m1;
                     dev_collide_site<S, SEGW, BX, EQ24>(kp, stage + s0 * (NPL * SEGW), c, Hf_0, Hg_0, FxB, FyB,
                                                         dst + ((size_t)y * pitch + (size_t)xg),
-                                                        t < Wb ? outb + (size_t)b0 * NPL * BX + t : nullptr, plane,
+                                                        outb + (size_t)b0 * NPL * BX + t, plane,
                                                         ghost_lo, ghost_hi);
                 }
             } else {
@@ -304,10 +302,9 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         // the row collided second in the last iteration
         consumer_sync<BX + 32>();
         const int mp = 2 * iters - 2;
-        if (issuer && mp >= 1 && mp <= njobs - 2 && out_bytes > 0) {
+        if (issuer && mp >= 1 && mp <= njobs - 2) {
             const int bP = b0 + 1 == DEV_OUT_BUFS ? 0 : b0 + 1;  // mp mod 3
-            bulk_copy_s2g(dst + ((size_t)lane * plane + (size_t)(y_start - 1 + mp) * pitch + (size_t)x0),
-                          outb + ((size_t)bP * NPL + lane) * BX, out_bytes);
+            tensor_store_3d(&dst_map, outb + (size_t)bP * NPL * BX, x0, y_start - 1 + mp, 0);
             bulk_commit_group();
         }
     }

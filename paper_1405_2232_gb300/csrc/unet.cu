@@ -23,6 +23,7 @@
 #include <new>
 #include <vector>
 
+#include "tensor_map.h"
 #include "lb.h"
 #include "unet.h"
 #include "unet_kernels.cuh"
@@ -35,6 +36,7 @@ lb_status record_error(lb_status st, const char* msg);
 }
 
 using unk::bf16;
+using lbgb::tensor_map_encoder;
 
 namespace {
 
@@ -194,23 +196,6 @@ void wgrad_shape(const un_net* n, const Layer& L, long long M, int* MT, int* NT,
     const long long c = (nchunks + s - 1) / s;
     *cps = (int)c;
     *splits = (int)((nchunks + c - 1) / c);
-}
-
-// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
-// query (no link-time dependence on the driver library); host-only encoding
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
 }
 
 // Tensor map of a BF16 activation tensor (layout of act_at) for k_conv3_tc:
