@@ -395,6 +395,21 @@ def test_16bit_one_step_within_rounding_bound(lb, prec, u, shape, tile):
     """One step from a state the 16-bit mode represents exactly: every stored
     population within (half an ulp of its deviation) + (FP32 step error), on the
     strip kernel (any nx) and the tile kernel."""
+    check_16bit_one_step(lb, prec, u, shape, tile)
+
+
+# shapes of the 16-bit strip kernel's edge cases: strips narrower than one
+# 16-byte unit and than a warp (the row's tensor copy clips at nx), odd and
+# even job counts per row chunk (two rows per iteration), one- and
+# many-chunk strips, a ragged second strip
+@pytest.mark.parametrize("prec,u", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("shape,tile", [((5, 3), (256, 0)), ((3, 6), (256, 0)), ((7, 40), (256, 0)), ((50, 300), (256, 0)),
+                                        ((9, 257), (128, 0)), ((64, 136), (128, 0))])
+def test_16bit_strip_shapes_within_rounding_bound(lb, prec, u, shape, tile):
+    check_16bit_one_step(lb, prec, u, shape, tile)
+
+
+def check_16bit_one_step(lb, prec, u, shape, tile):
     rho0, T0 = 0.12, 0.75 * I.CS_TC
     ny, nx = shape
     rho, T = I.spinodal_fields(nx, ny)
