@@ -571,7 +571,11 @@ __device__ __forceinline__ void force_from_window(const KParams& kp, const real*
 //    any literal FP64 implementation;
 //  * FP32: multiplications by the constants 3, 4.5, 9 and one reciprocal of
 //    rho, contracted to FMAs.
-template <typename real, bool EQ24>
+// FMA (FP32 only): the update in fused multiply-add form from the factors in
+// kp.d, (1 - omega) f_i + P +- Q (see below); measured faster in the fused
+// finite-difference kernel (+2.6%), slower in the strip and batched steps
+// (-8% and -0.5%), which keep the direct form.
+template <typename real, bool EQ24, bool FMA = false>
 __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9], real rho,
                                         real Fx, real Fy, real& ux_out, real& uy_out,
                                         real& T_out) {
@@ -620,40 +624,87 @@ __device__ __forceinline__ void collide(const KParams& kp, real f[9], real g[9],
         const real uy = (my + (real)0.5 * Fy) * inv_rho;
         const real T = e / (rho * KPR(kp, cv));
         const real cvT = KPR(kp, cv) * T;
-        const real om_f = KPR(kp, omega_f), om_g = KPR(kp, omega_g);
-        const real guo = KPR(kp, guo_pre), corr = KPR(kp, corr_pre);
-        const real base = (real)1 - (real)1.5 * (ux * ux + uy * uy);
-        const real uF3 = (real)3 * (ux * Fx + uy * Fy);
-        // Opposite directions i and i' = opposite(i) share the even parts of
-        // f^eq and F_i; the odd parts change sign:
-        //   f^eq = rho w (1 - 1.5 u^2 + 4.5 (e.u)^2) +- 3 rho w (e.u)
-        //   F_i  = guo w (9 (e.u)(e.F) - 3 u.F)      +- 3 guo w (e.F)
-        //   C_i  =                                     +- 3 corr w c_v T (e.F)
-        // pairs (1,3), (2,4), (5,7), (8,6): e(i) = (dx, dy), e(i') = -(dx, dy)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
-            const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
-            const real w = (real)wd(i);
-            const real eu = (real)ex(i) * ux + (real)ey(i) * uy;
-            const real eF = (real)ex(i) * Fx + (real)ey(i) * Fy;
-            const real rw = rho * w;
-            const real feq_even = rw * (base + (real)4.5 * eu * eu);
-            const real feq_odd = (real)3 * rw * eu;
-            const real F_even = guo * w * ((real)9 * eu * eF - uF3);
-            const real F_odd = (real)3 * guo * w * eF;
-            const real feq_i = feq_even + feq_odd, feq_k = feq_even - feq_odd;
-            f[i] = f[i] + om_f * (feq_i - f[i]) + (F_even + F_odd);
-            f[k] = f[k] + om_f * (feq_k - f[k]) + (F_even - F_odd);
-            real gi = g[i] + om_g * (cvT * feq_i - g[i]);
-            real gk = g[k] + om_g * (cvT * feq_k - g[k]);
-            if (EQ24) {
-                const real C_odd = (real)3 * corr * w * cvT * eF;
-                gi += C_odd;
-                gk -= C_odd;
+        if constexpr (FMA) {
+            const real m15u2 = (real)-1.5 * fmaf(ux, ux, uy * uy);
+            const real uF3 = (real)3 * fmaf(ux, Fx, uy * Fy);
+            // Opposite directions i and i' = opposite(i) share the even parts of
+            // f^eq and F_i; the odd parts change sign:
+            //   f^eq = rho w (1 - 1.5 u^2 + 4.5 (e.u)^2) +- 3 rho w (e.u)
+            //   F_i  = guo w (9 (e.u)(e.F) - 3 u.F)      +- 3 guo w (e.F)
+            //   C_i  =                                     +- 3 corr w c_v T (e.F)
+            // and with c_v T rho = e, c_v T f^eq = e w (...).  The update
+            // f_i <- f_i + omega_f (f^eq_i - f_i) + F_i is evaluated as
+            // (1 - omega_f) f_i + P +- Q, P = omega_f (even part of f^eq) + (even
+            // part of F_i), Q the odd parts, the same for g with C_i: fused
+            // multiply-adds of per-site factors (per weight class c: axis, diagonal)
+            // and the constants in kp.d.
+            real A[2], r45[2], r3[2], B[2], e45[2], e3[2], c3[2];
+    #pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const real rwo = kp.d.wo_f[c] * rho, ewo = kp.d.wo_g[c] * e;
+                A[c] = fmaf(-kp.d.gw[c], uF3, fmaf(rwo, m15u2, rwo));
+                r45[c] = (real)4.5 * rwo;
+                r3[c] = (real)3 * rwo;
+                B[c] = fmaf(ewo, m15u2, ewo);
+                e45[c] = (real)4.5 * ewo;
+                e3[c] = (real)3 * ewo;
+                c3[c] = EQ24 ? kp.d.cw3[c] * cvT : (real)0;
             }
-            g[i] = gi;
-            g[k] = gk;
+            const real omc_f = kp.d.omc_f, omc_g = kp.d.omc_g;
+            // pairs (1,3), (2,4), (5,7), (8,6): e(i) = (dx, dy), e(i') = -(dx, dy)
+    #pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
+                const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
+                const int c = p < 2 ? 0 : 1;
+                const real eu = p == 0 ? ux : (p == 1 ? uy : (p == 2 ? ux + uy : ux - uy));
+                const real eF = p == 0 ? Fx : (p == 1 ? Fy : (p == 2 ? Fx + Fy : Fx - Fy));
+                const real eu2 = eu * eu;
+                const real P = fmaf(kp.d.gw9[c], eu * eF, fmaf(r45[c], eu2, A[c]));
+                const real Q = fmaf(r3[c], eu, kp.d.gw3[c] * eF);
+                f[i] = fmaf(omc_f, f[i], P + Q);
+                f[k] = fmaf(omc_f, f[k], P - Q);
+                const real Pg = fmaf(e45[c], eu2, B[c]);
+                const real Qg = EQ24 ? fmaf(c3[c], eF, e3[c] * eu) : e3[c] * eu;
+                g[i] = fmaf(omc_g, g[i], Pg + Qg);
+                g[k] = fmaf(omc_g, g[k], Pg - Qg);
+            }
+        } else {
+            const real om_f = KPR(kp, omega_f), om_g = KPR(kp, omega_g);
+            const real guo = KPR(kp, guo_pre), corr = KPR(kp, corr_pre);
+            const real base = (real)1 - (real)1.5 * (ux * ux + uy * uy);
+            const real uF3 = (real)3 * (ux * Fx + uy * Fy);
+            // Opposite directions i and i' = opposite(i) share the even parts of
+            // f^eq and F_i; the odd parts change sign:
+            //   f^eq = rho w (1 - 1.5 u^2 + 4.5 (e.u)^2) +- 3 rho w (e.u)
+            //   F_i  = guo w (9 (e.u)(e.F) - 3 u.F)      +- 3 guo w (e.F)
+            //   C_i  =                                     +- 3 corr w c_v T (e.F)
+            // pairs (1,3), (2,4), (5,7), (8,6): e(i) = (dx, dy), e(i') = -(dx, dy)
+    #pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int i = p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 8));
+                const int k = p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 6));
+                const real w = (real)wd(i);
+                const real eu = (real)ex(i) * ux + (real)ey(i) * uy;
+                const real eF = (real)ex(i) * Fx + (real)ey(i) * Fy;
+                const real rw = rho * w;
+                const real feq_even = rw * (base + (real)4.5 * eu * eu);
+                const real feq_odd = (real)3 * rw * eu;
+                const real F_even = guo * w * ((real)9 * eu * eF - uF3);
+                const real F_odd = (real)3 * guo * w * eF;
+                const real feq_i = feq_even + feq_odd, feq_k = feq_even - feq_odd;
+                f[i] = f[i] + om_f * (feq_i - f[i]) + (F_even + F_odd);
+                f[k] = f[k] + om_f * (feq_k - f[k]) + (F_even - F_odd);
+                real gi = g[i] + om_g * (cvT * feq_i - g[i]);
+                real gk = g[k] + om_g * (cvT * feq_k - g[k]);
+                if (EQ24) {
+                    const real C_odd = (real)3 * corr * w * cvT * eF;
+                    gi += C_odd;
+                    gk -= C_odd;
+                }
+                g[i] = gi;
+                g[k] = gk;
+            }
         }
         // The collision conserves mass and energy exactly: sum f^eq = rho,
         // sum F_i = 0, sum g^eq = rho c_v T = sum g, sum C_i = 0.  In FP32 the
