@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
     uint64_t* empty = full + STAGES;
-    __shared__ int s_abort;
+    __shared__ int s_abort[2];  // one slot per job parity (see the loop)
 
     const int t = threadIdx.x;
     // this CTA's work items (contiguous; the lists are read at launch, so a
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             mbar_init(&empty[s], NCW);
         }
         fence_mbar_init();
-        s_abort = 0;
+        s_abort[0] = 0;
+        s_abort[1] = 0;
     }
     __syncthreads();
 
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     // (ring column r holds strip column r - 1; see k_step_strip)
     const bool halo = t >= BX;
     long long jg = 0;
+    bool aborted = false;
     for (int it = it_begin; it < it_end; ++it) {
         const BatchItem item = items[it];
         const BatchDomain& D = doms[item.domain];
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         int flags = 0;
         for (int j = 0; j < njobs; ++j, ++jg) {
             const int s = (int)(jg % STAGES);
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort = 1;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort[jg & 1] = 1;
             if (has_psi) {
                 const elem* st = stage + (size_t)s * 18 * SEGW;
                 real* rp = ring_psi + (int)(jg & 3) * RW;
@@ -165,7 +167,12 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 }
             }
             consumer_sync<BX + 32>();
-            if (s_abort) break;
+            // (a thread that times out at the next job writes the other slot
+            // than the one read here, so every consumer leaves at the same job)
+            if (s_abort[jg & 1]) {
+                aborted = true;
+                break;
+            }
             if (halo) continue;
             if (j >= 2 && t < W) {
                 const int sp = (int)((jg - 1) % STAGES);
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 if ((t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
             }
         }
-        if (s_abort) break;
+        if (aborted) break;
         // the item's last job (a halo row, never collided) is released too, so
         // the producer may reuse its stage for the next item (column warps
         // only: the halo warp never releases)
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         if (!halo && (t & 31) == 0) mbar_arrive(&empty[(int)((jg - 1) % STAGES)]);
         if (flags) atomicOr(kp.err, flags);
     }
-    if (s_abort && t == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);
+    if (aborted && t == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);
 }
 
 // Per-domain partial sums over tiles of 256 sites: rho, rho c_v T (sum g),

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(r_Ts + 4 * RB) + 7) & ~uintptr_t(7));
     uint64_t* empty = full + STAGES;
-    __shared__ int s_abort;
+    __shared__ int s_abort[2];  // one slot per job parity (see the loop)
 
     const int t = threadIdx.x;
     const int nx = kp.nx, ny = kp.ny;
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             mbar_init(&empty[s], NCW);
         }
         fence_mbar_init();
-        s_abort = 0;
+        s_abort[0] = 0;
+        s_abort[1] = 0;
     }
     __syncthreads();
 
@@ -203,11 +204,12 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     const int colB = halo ? (hl == 0 ? -1 : (hl == 1 ? W : -99)) : (t < W ? t : -99);
     const bool own_col = !halo && t < W;
     int flags = 0;
+    bool aborted = false;
     for (int j = 0; j < njobs + 2; ++j) {
         // A(j)
         if (j < njobs) {
             const int s = j % STAGES;
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort = 1;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort[j & 1] = 1;
             if (colA != -99) {
                 const elem* st = stage + (size_t)s * NP * SEGW;
                 const int c = colA + HALO;
@@ -227,7 +229,12 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             }
         }
         consumer_sync<BX + 32>();
-        if (s_abort) break;
+        // (a thread that times out at job j + 1 writes the other slot than the
+        // one read here, so every consumer leaves at the same job)
+        if (s_abort[j & 1]) {
+            aborted = true;
+            break;
+        }
         // B(k), k = j - 1: force, u; own rows: f collision and store
         {
             const int k = j - 1;
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             if ((t & 31) == 0) mbar_arrive(&empty[(j - 1) % STAGES]);
         }
     }
-    if (s_abort) {
+    if (aborted) {
         if (t == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
         return;
     }

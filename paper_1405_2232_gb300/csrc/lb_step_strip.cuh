@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
     uint64_t* empty = full + STAGES;
-    __shared__ int s_abort;
+    __shared__ int s_abort[2];  // one slot per job parity (see the loop)
 
     const int t = threadIdx.x;
     const int nx = kp.nx, ny = kp.ny;
@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             mbar_init(&empty[s], NCW);
         }
         fence_mbar_init();
-        s_abort = 0;
+        s_abort[0] = 0;
+        s_abort[1] = 0;
     }
     __syncthreads();
 
@@ -307,9 +308,10 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     const int r_psi = halo ? ((t & 31) == 0 ? 0 : W + 1) : t + 1;
     const bool has_psi = halo ? (t & 31) < 2 : t < W;
     int flags = 0;
+    bool aborted = false;
     for (int j = 0; j < njobs; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort = 1;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1), kp.wait_cycles)) s_abort[j & 1] = 1;
         // 1. rho, T, psi of pre-collision row j at ring column r_psi
         if (has_psi) {
             const elem* st = stage + (size_t)s * NPL * SEGW;
@@ -344,7 +346,12 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             }
         }
         consumer_sync<BX + 32>();
-        if (s_abort) break;
+        // (a thread that times out at job j + 1 writes the other slot than the
+        // one read here, so every consumer leaves at the same job)
+        if (s_abort[j & 1]) {
+            aborted = true;
+            break;
+        }
         if (halo) continue;
         // 2. collide pre-collision row j-1 (its psi neighbourhood is complete)
         if (j >= 2 && t < W) {
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             if ((t & 31) == 0) mbar_arrive(&empty[(j - 1) % STAGES]);
         }
     }
-    if (s_abort) {
+    if (aborted) {
         if (t == 0) atomicOr(kp.err, 1 << LB_ERR_TIMEOUT);
         return;
     }
