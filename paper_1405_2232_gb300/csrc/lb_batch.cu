@@ -25,8 +25,8 @@ namespace lbgb {
 lb_status record_error(lb_status st, const char* msg);
 // FP64 batch step: its own translation unit, compiled without contraction
 cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain* doms,
-                                   const BatchItem* items, const int* cta_off, int eq24, int bmode,
-                                   int grid, cudaStream_t stream);
+                                   const BatchItem* items, const int* n_items, int* next_item, int eq24,
+                                   int bmode, int grid, cudaStream_t stream);
 }
 
 using namespace lbgb;
@@ -88,7 +88,7 @@ struct lb_batch {
     // work lists
     BatchItem* d_items = nullptr;
     int* d_counts = nullptr;      // [0] items, [1] tiles
-    int* d_cta_off = nullptr;     // [grid + 1]: work items of persistent CTA b are [off[b], off[b+1])
+    int* d_next = nullptr;        // the next work item to take (reset before every step)
     int max_items = 0;
     BatchTile* d_tiles = nullptr;
     int* d_tile_begin = nullptr;  // [n + 1]
@@ -118,7 +118,7 @@ cudaError_t launch_batch_step(lb_batch* b, const void* src, void* dst) {
         using E = float;
         constexpr int BX = BATCH_BX_FP32, ST = batch_stages<LB_PREC_FP32, BX>();
         constexpr size_t smem = strip_smem_bytes<LB_PREC_FP32, BX, ST>();
-        auto pick = [&]() -> void (*)(const E*, E*, const BatchDomain*, const BatchItem*, const int*) {
+        auto pick = [&]() -> void (*)(const E*, E*, const BatchDomain*, const BatchItem*, const int*, int*) {
             if (b->eq24) {
                 if (b->bmode == BETA_ZERO) return k_batch_step<LB_PREC_FP32, BX, ST, true, BETA_ZERO>;
                 if (b->bmode == BETA_ONE) return k_batch_step<LB_PREC_FP32, BX, ST, true, BETA_ONE>;
@@ -130,11 +130,17 @@ cudaError_t launch_batch_step(lb_batch* b, const void* src, void* dst) {
         };
         auto k = pick();
         if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) return e;
         k<<<grid, strip_threads<BX>(), smem, b->stream>>>(static_cast<const E*>(src), static_cast<E*>(dst),
-                                                           b->d_doms, b->d_items, b->d_cta_off);
+                                                           b->d_doms, b->d_items, b->d_counts, b->d_next);
         return cudaGetLastError();
     }
-    return launch_batch_step_fp64(src, dst, b->d_doms, b->d_items, b->d_cta_off, b->eq24, b->bmode,
+    if (src) {
+        cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_batch_step_fp64(src, dst, b->d_doms, b->d_items, b->d_counts, b->d_next, b->eq24, b->bmode,
                                   grid, b->stream);
 }
 
@@ -179,41 +185,20 @@ lb_status rebuild_lists(lb_batch* b) {
     begin[b->n] = (int)tiles.size();
     if ((int)items.size() > b->max_items || (int)tiles.size() > b->max_tiles)
         return err(LB_ERR_ARG, "batch work list larger than allocated");
-    // Longest item first to the least loaded persistent CTA.  Cost of an item:
+    // Longest item first: the persistent CTAs take items in this order from a
+    // global counter, so the short items fill in at the end.  Cost of an item:
     // its rows plus the two halo rows, times its columns plus a per-row
     // constant (a narrow strip still pays the row's barrier and latencies).
-    const int grid = 2 * b->sms;
     auto cost = [&](const BatchItem& a) {
         const long long w = std::min(b->bx, b->params[a.domain].nx - a.strip * b->bx);
         return (long long)(a.y1 - a.y0 + 2) * (w + 64);
     };
     std::stable_sort(items.begin(), items.end(),
                      [&](const BatchItem& a, const BatchItem& c) { return cost(a) > cost(c); });
-    std::vector<std::vector<int>> per(grid);
-    std::vector<std::pair<long long, int>> heap;  // (load, cta), min-heap
-    for (int g = 0; g < grid; ++g) heap.push_back({0, g});
-    auto greater = [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x > y; };
-    std::make_heap(heap.begin(), heap.end(), greater);
-    for (int i = 0; i < (int)items.size(); ++i) {
-        std::pop_heap(heap.begin(), heap.end(), greater);
-        per[heap.back().second].push_back(i);
-        heap.back().first += cost(items[i]);
-        std::push_heap(heap.begin(), heap.end(), greater);
-    }
-    std::vector<BatchItem> ordered;
-    std::vector<int> off(grid + 1, 0);
-    ordered.reserve(items.size());
-    for (int g = 0; g < grid; ++g) {
-        off[g] = (int)ordered.size();
-        for (int i : per[g]) ordered.push_back(items[i]);
-    }
-    off[grid] = (int)ordered.size();
     int counts[2] = {(int)items.size(), (int)tiles.size()};
-    if (!ordered.empty())
-        BCU(cudaMemcpyAsync(b->d_items, ordered.data(), sizeof(BatchItem) * ordered.size(),
+    if (!items.empty())
+        BCU(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
                             cudaMemcpyHostToDevice, b->stream), "work list upload");
-    BCU(cudaMemcpyAsync(b->d_cta_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, b->stream),
-        "work list offsets upload");
     if (!tiles.empty())
         BCU(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(),
                             cudaMemcpyHostToDevice, b->stream), "tile list upload");
@@ -236,7 +221,7 @@ void release(lb_batch* b) {
     cudaFree(b->d_err);
     cudaFree(b->d_items);
     cudaFree(b->d_counts);
-    cudaFree(b->d_cta_off);
+    cudaFree(b->d_next);
     cudaFree(b->d_tiles);
     cudaFree(b->d_tile_begin);
     cudaFree(b->d_part);
@@ -379,7 +364,7 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
     if (e == cudaSuccess) e = cudaMalloc(&b->d_doms, sizeof(BatchDomain) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (max_items > 0 ? max_items : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_cta_off, sizeof(int) * (2 * b->sms + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * (max_tiles > 0 ? max_tiles : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * 6 * (max_tiles > 0 ? max_tiles : 1));

@@ -3,13 +3,18 @@
 //
 // The fused step is the strip-marching kernel of lb_step_strip.cuh made
 // persistent: a fixed grid of CTAs walks a device-side list of work items
-// (domain, strip, row chunk), each CTA its own contiguous range of the list
-// (the host deals items longest first to the least loaded CTA).  The producer
-// warp and the consumer warps keep one job counter across items, so the
-// producer streams the next item's rows while the consumers still work on the
-// current one.  The ranges are read from device memory at launch, so a
-// captured CUDA graph stays valid while converged domains are taken off the
-// list.  As in the single-lattice kernel,
+// (domain, strip, row chunk) sorted longest first; each CTA's producer warp
+// takes the next item from a global counter when it starts one, so the CTAs
+// finish together (a static deal by estimated cost left the last CTA 14%
+// behind the mean).  The producer passes each item's index to the consumer
+// warps through a small shared-memory queue (written before it arms the
+// item's first stage, read after that stage's barrier), and after the last
+// item an end mark: a stage completed without data whose queue entry is -1.
+// The producer and the consumers keep one job counter across items, so the
+// producer streams the next item's rows while the consumers still work on
+// the current one.  The list and its length are read from device memory at
+// launch and the counter is reset before every launch, so a captured CUDA
+// graph stays valid while converged domains are taken off the list.  As in the single-lattice kernel,
 // every domain is stored in the ghost-column layout (one bulk copy per plane
 // row, ghost copies written with the row) and a halo warp computes the two
 // halo psi columns.
@@ -18,6 +23,10 @@
 #include "lb_step_strip.cuh"
 
 namespace lbgb {
+
+// Item indices the producer may run ahead of the consumers (it is at most
+// STAGES jobs ahead, and every item has at least three jobs).
+constexpr int BATCH_QN = 16;
 
 // One domain of a batch.
 struct BatchDomain {
@@ -47,7 +56,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     k_batch_step(const typename Store<PREC>::elem* __restrict__ src_base,
                  typename Store<PREC>::elem* __restrict__ dst_base,
                  const BatchDomain* __restrict__ doms, const BatchItem* __restrict__ items,
-                 const int* __restrict__ cta_off) {
+                 const int* __restrict__ n_items_ptr, int* __restrict__ next_item) {
     using S = Store<PREC>;
     using C = StripCfg<PREC>;
     using elem = typename C::elem;
@@ -66,11 +75,9 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         (reinterpret_cast<uintptr_t>(ring_psi2 + 4 * RW) + 7) & ~uintptr_t(7));
     uint64_t* empty = full + STAGES;
     __shared__ int s_abort[2];  // one slot per job parity (see the loop)
+    __shared__ int s_items[BATCH_QN];  // item index of the q-th item this CTA took (-1: no more)
 
     const int t = threadIdx.x;
-    // this CTA's work items (contiguous; the lists are read at launch, so a
-    // captured graph stays valid while the host rebuilds them)
-    const int it_begin = cta_off[blockIdx.x], it_end = cta_off[blockIdx.x + 1];
     if (t == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -85,8 +92,14 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     if (t >= BX + 32) {
         // ------------------------------------------------ producer warp
         const int lane = t - BX - 32;
+        const int n_items = *n_items_ptr;
         long long jg = 0;  // job counter across this CTA's items
-        for (int it = it_begin; it < it_end; ++it) {
+        int q = 0;         // items taken
+        for (;; ++q) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(next_item, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n_items) break;
             const BatchItem item = items[it];
             const BatchDomain& D = doms[item.domain];
             const int nx = D.kp.nx, ny = D.kp.ny;
@@ -106,7 +119,11 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 }
                 int y = item.y0 - 1 + j;
                 y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)18 * strip_copy_bytes<ES, HALO>(W));
+                if (lane == 0) {
+                    // the item's index, published by the arrive below
+                    if (j == 0) s_items[q % BATCH_QN] = it;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)18 * strip_copy_bytes<ES, HALO>(W));
+                }
                 __syncwarp();
                 if (lane < 18) {
                     const int i = lane;
@@ -120,10 +137,23 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 }
             }
         }
-        // leave only when every copy this CTA issued has landed (bounded)
+        // every copy this CTA issued has landed (bounded) before the end mark
+        // completes the next phase of a stage's barrier, and before the CTA exits
         if (lane == 0)
             for (long long j = (jg > STAGES ? jg - STAGES : 0); j < jg; ++j)
                 (void)mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+        __syncwarp();
+        // the end mark: the next stage completes without data, its queue entry -1
+        const int s = (int)(jg % STAGES);
+        if (jg >= STAGES &&
+            !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1)))) {
+            if (lane == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);
+            return;  // consumers then time out on "full" and leave
+        }
+        if (lane == 0) {
+            s_items[q % BATCH_QN] = -1;
+            mbar_arrive(&full[s]);
+        }
         return;
     }
 
@@ -132,7 +162,18 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     const bool halo = t >= BX;
     long long jg = 0;
     bool aborted = false;
-    for (int it = it_begin; it < it_end; ++it) {
+    for (int q = 0;; ++q) {
+        // the first stage of the q-th item this CTA's producer took (or its
+        // end mark); one barrier so that every consumer reads the same entry
+        // and abort flag
+        if (!mbar_wait_bounded(&full[(int)(jg % STAGES)], (uint32_t)((jg / STAGES) & 1))) s_abort[jg & 1] = 1;
+        consumer_sync<BX + 32>();
+        if (s_abort[jg & 1]) {
+            aborted = true;
+            break;
+        }
+        const int it = s_items[q % BATCH_QN];
+        if (it < 0) break;
         const BatchItem item = items[it];
         const BatchDomain& D = doms[item.domain];
         const KParams kp = D.kp;
@@ -147,7 +188,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         int flags = 0;
         for (int j = 0; j < njobs; ++j, ++jg) {
             const int s = (int)(jg % STAGES);
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort[jg & 1] = 1;
+            // (the first job's stage was waited for above)
+            if (j > 0 && !mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort[jg & 1] = 1;
             if (has_psi) {
                 const elem* st = stage + (size_t)s * 18 * SEGW;
                 real* rp = ring_psi + (int)(jg & 3) * RW;

@@ -9,12 +9,12 @@
 namespace lbgb {
 
 cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain* doms,
-                                   const BatchItem* items, const int* cta_off, int eq24, int bmode,
-                                   int grid, cudaStream_t stream) {
+                                   const BatchItem* items, const int* n_items, int* next_item, int eq24,
+                                   int bmode, int grid, cudaStream_t stream) {
     using E = double;
     constexpr int BX = 128, ST = batch_stages<LB_PREC_FP64, BX>();
     constexpr size_t smem = strip_smem_bytes<LB_PREC_FP64, BX, ST>();
-    void (*k)(const E*, E*, const BatchDomain*, const BatchItem*, const int*);
+    void (*k)(const E*, E*, const BatchDomain*, const BatchItem*, const int*, int*);
     if (eq24)
         k = bmode == BETA_ZERO  ? k_batch_step<LB_PREC_FP64, BX, ST, true, BETA_ZERO>
             : bmode == BETA_ONE ? k_batch_step<LB_PREC_FP64, BX, ST, true, BETA_ONE>
@@ -26,7 +26,7 @@ cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain
     // src == nullptr: set the shared-memory attribute only (once, outside capture)
     if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, strip_threads<BX>(), smem, stream>>>(static_cast<const E*>(src), static_cast<E*>(dst), doms,
-                                                   items, cta_off);
+                                                   items, n_items, next_item);
     return cudaGetLastError();
 }
 
