@@ -117,7 +117,8 @@ cudaError_t launch_batch_step(lb_batch* b, const void* src, void* dst) {
     if (b->prec == LB_PREC_FP32) {
         using E = float;
         constexpr int BX = BATCH_BX_FP32, ST = batch_stages<LB_PREC_FP32, BX>();
-        constexpr size_t smem = strip_smem_bytes<LB_PREC_FP32, BX, ST>();
+        constexpr size_t smem = batch_smem_bytes<LB_PREC_FP32, BX, ST>();
+        static_assert(smem <= 110 * 1024, "two CTAs per SM");
         auto pick = [&]() -> void (*)(const E*, E*, const BatchDomain*, const BatchItem*, const int*, int*) {
             if (b->eq24) {
                 if (b->bmode == BETA_ZERO) return k_batch_step<LB_PREC_FP32, BX, ST, true, BETA_ZERO>;
@@ -170,16 +171,23 @@ lb_status rebuild_lists(lb_batch* b) {
         if (b->frozen[d] >= 0) continue;
         const int nx = b->params[d].nx, ny = b->params[d].ny;
         const int strips = (nx + b->bx - 1) / b->bx;
-        const int chunks = (ny + b->chunk_rows - 1) / b->chunk_rows;
-        for (int s = 0; s < strips; ++s)
+        for (int s = 0; s < strips; ++s) {
+            // a strip at most half the kernel's width runs as half items: twice
+            // the rows of a chunk, split between the two halves of the CTA
+            const int w = std::min(b->bx, nx - s * b->bx);
+            const int half = 2 * w <= b->bx ? 1 : 0;
+            const int rows = half ? 2 * b->chunk_rows : b->chunk_rows;
+            const int chunks = (ny + rows - 1) / rows;
             for (int c = 0; c < chunks; ++c) {
                 BatchItem it;
                 it.domain = d;
                 it.strip = s;
                 it.y0 = (int)((long long)c * ny / chunks);
                 it.y1 = (int)((long long)(c + 1) * ny / chunks);
+                it.half = half;
                 items.push_back(it);
             }
+        }
         for (int first = 0; first < nx * ny; first += 256) tiles.push_back(BatchTile{d, first});
     }
     begin[b->n] = (int)tiles.size();
@@ -187,10 +195,13 @@ lb_status rebuild_lists(lb_batch* b) {
         return err(LB_ERR_ARG, "batch work list larger than allocated");
     // Longest item first: the persistent CTAs take items in this order from a
     // global counter, so the short items fill in at the end.  Cost of an item:
-    // its rows plus the two halo rows, times its columns plus a per-row
-    // constant (a narrow strip still pays the row's barrier and latencies).
+    // its jobs (rows plus the two halo rows; a half item's two halves march
+    // together, so the left half's rows) times the columns they keep busy
+    // plus a per-row constant (a narrow strip still pays the row's barrier
+    // and latencies).
     auto cost = [&](const BatchItem& a) {
         const long long w = std::min(b->bx, b->params[a.domain].nx - a.strip * b->bx);
+        if (a.half) return (long long)(batch_split(a.y0, a.y1) - a.y0 + 2) * (2 * w + 64);
         return (long long)(a.y1 - a.y0 + 2) * (w + 64);
     };
     std::stable_sort(items.begin(), items.end(),

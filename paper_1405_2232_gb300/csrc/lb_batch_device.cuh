@@ -14,7 +14,16 @@
 // producer streams the next item's rows while the consumers still work on
 // the current one.  The list and its length are read from device memory at
 // launch and the counter is reset before every launch, so a captured CUDA
-// graph stays valid while converged domains are taken off the list.  As in the single-lattice kernel,
+// graph stays valid while converged domains are taken off the list.
+//
+// Half items: a strip at most BX/2 columns wide (a narrow domain, or the
+// remainder strip of a wider one) would leave most column threads idle, so
+// its rows are split between the two halves of the CTA, which march them in
+// lockstep: column threads [0, BX/2) take rows [y0, ym) and [BX/2, BX) rows
+// [ym, y1).  The stage and psi-ring rows hold one segment per half, the
+// producer copies both halves' plane rows for a job, the halo warp's lanes
+// 0, 1 and 2, 3 compute the halo psi columns of the two halves; when the
+// right half has one row fewer it sits out the left half's last job.  As in the single-lattice kernel,
 // every domain is stored in the ghost-column layout (one bulk copy per plane
 // row, ghost copies written with the row) and a halo warp computes the two
 // halo psi columns.
@@ -40,15 +49,35 @@ struct BatchItem {
     int domain;
     int strip;    // column strip (width BX)
     int y0, y1;   // rows [y0, y1) collided by this item
+    int half;     // 1: strip at most BX/2 wide, rows split between the CTA's halves
 };
+
+// Rows of the left half of a half item: [y0, batch_split(y0, y1)).
+__host__ __device__ inline int batch_split(int y0, int y1) { return y0 + (y1 - y0 + 1) / 2; }
+
+// Row pitches of the batched step's stage and psi ring: room for one full
+// strip (BX + 2 HALO, BX + 2) or two half strips (2 (BX/2 + 2 HALO), 2 (BX/2 + 2)).
+template <int PREC, int BX>
+__host__ __device__ constexpr int batch_segw() {
+    return BX + 4 * StripCfg<PREC>::HALO;
+}
+template <int BX>
+__host__ __device__ constexpr int batch_rw() {
+    return BX + 4;
+}
 
 // Stage count of the batched step: the deepest ring that lets two CTAs share an SM.
 template <int PREC, int BX>
 constexpr int batch_stages() {
-    constexpr size_t stage = (size_t)18 * (BX + 2 * StripCfg<PREC>::HALO) * StripCfg<PREC>::ES;
-    constexpr size_t ring = (size_t)8 * (BX + 2) * sizeof(typename StripCfg<PREC>::real);
+    constexpr size_t stage = (size_t)18 * batch_segw<PREC, BX>() * StripCfg<PREC>::ES;
+    constexpr size_t ring = (size_t)8 * batch_rw<BX>() * sizeof(typename StripCfg<PREC>::real);
     constexpr size_t s = (110 * 1024 - 32 - ring) / stage;
     return s > 12 ? 12 : (int)s;
+}
+template <int PREC, int BX, int STAGES>
+constexpr size_t batch_smem_bytes() {
+    return (size_t)STAGES * 18 * batch_segw<PREC, BX>() * StripCfg<PREC>::ES +
+           (size_t)8 * batch_rw<BX>() * sizeof(typename StripCfg<PREC>::real) + (size_t)2 * STAGES * 8 + 16;
 }
 
 template <int PREC, int BX, int STAGES, bool EQ24, int BMODE>
@@ -62,10 +91,14 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
     using elem = typename C::elem;
     using real = typename C::real;
     constexpr int HALO = C::HALO;
-    constexpr int SEGW = BX + 2 * HALO;
-    constexpr int RW = BX + 2;
+    constexpr int SEGW = batch_segw<PREC, BX>();  // stage row pitch
+    constexpr int RW = batch_rw<BX>();            // psi ring row pitch
+    constexpr int HW = BX / 2;                    // columns of a half strip
+    constexpr int SEGW2 = HW + 2 * HALO;          // stage offset of the right half
+    constexpr int RW2 = HW + 2;                   // ring offset of the right half
     constexpr int ES = C::ES;
     constexpr int NCW = BX / 32;
+    static_assert(HW % 32 == 0, "a half strip is whole warps");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     elem* stage = reinterpret_cast<elem*>(smem_raw);  // [STAGES][18][SEGW]
@@ -106,8 +139,13 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             const uint32_t plane = (uint32_t)D.kp.plane, pitch = (uint32_t)D.kp.pitch;
             const int x0 = item.strip * BX;
             const int W = min(BX, nx - x0);
-            const int njobs = item.y1 - item.y0 + 2;
+            // a half item: the left half's rows set the job count, the right
+            // half (rows from ym) has as many or one fewer
+            const int ym = item.half ? batch_split(item.y0, item.y1) : item.y1;
+            const int njobs = ym - item.y0 + 2;
+            const int njobs1 = item.half ? item.y1 - ym + 2 : 0;
             const elem* src = src_base + D.off;
+            const uint32_t cb = strip_copy_bytes<ES, HALO>(W);
             for (int j = 0; j < njobs; ++j, ++jg) {
                 const int s = (int)(jg % STAGES);
                 if (jg >= STAGES) {
@@ -117,23 +155,26 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                         return;  // consumers then time out on "full" and leave
                     }
                 }
-                int y = item.y0 - 1 + j;
-                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                const bool two = j < njobs1;  // the right half of a half item has this job
                 if (lane == 0) {
                     // the item's index, published by the arrive below
                     if (j == 0) s_items[q % BATCH_QN] = it;
-                    mbar_arrive_expect_tx(&full[s], (uint32_t)18 * strip_copy_bytes<ES, HALO>(W));
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)(two ? 36 : 18) * cb);
                 }
                 __syncwarp();
                 if (lane < 18) {
                     const int i = lane;
                     const int d = i < 9 ? i : i - 9;
-                    int sy = y - ey(d);
-                    sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-                    const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
-                    // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
-                    bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW, row + (x0 - HALO),
-                                  strip_copy_bytes<ES, HALO>(W), &full[s]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !two) break;
+                        int sy = (h == 0 ? item.y0 : ym) - 1 + j - ey(d);
+                        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                        const elem* row = src + (size_t)((uint32_t)i * plane + (uint32_t)sy * pitch);
+                        // columns x0 - HALO .. x0 + W + HALO - 1 (ghost columns at the edges)
+                        bulk_copy_g2s(stage + ((size_t)s * 18 + i) * SEGW + h * SEGW2, row + (x0 - HALO), cb,
+                                      &full[s]);
+                    }
                 }
             }
         }
@@ -181,19 +222,29 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         const uint32_t plane = (uint32_t)kp.plane, pitch = (uint32_t)kp.pitch;
         const int x0 = item.strip * BX;
         const int W = min(BX, nx - x0);
-        const int njobs = item.y1 - item.y0 + 2;
+        // this thread's half: h = 1 for the right half of a half item (column
+        // threads from BX/2, halo lanes 2 and 3); its rows start at yh, its
+        // stage and ring segments at soff, roff, its column in the strip is tl
+        const int ym = item.half ? batch_split(item.y0, item.y1) : item.y1;
+        const int njobs = ym - item.y0 + 2;
+        const int lane = t & 31;
+        const int h = item.half ? (halo ? (lane >> 1) & 1 : (t >= HW ? 1 : 0)) : 0;
+        const int tl = t - h * HW;
+        const int yh = h ? ym : item.y0;
+        const int njobs_h = h ? item.y1 - ym + 2 : njobs;
+        const int soff = h * SEGW2, roff = h * RW2;
         elem* dst = dst_base + D.off;
-        const int r_psi = halo ? ((t & 31) == 0 ? 0 : W + 1) : t + 1;
-        const bool has_psi = halo ? (t & 31) < 2 : t < W;
+        const int r_psi = halo ? ((lane & 1) == 0 ? 0 : W + 1) : tl + 1;
+        const bool has_psi = halo ? lane < (item.half ? 4 : 2) : tl < W;
         int flags = 0;
         for (int j = 0; j < njobs; ++j, ++jg) {
             const int s = (int)(jg % STAGES);
             // (the first job's stage was waited for above)
             if (j > 0 && !mbar_wait_bounded(&full[s], (uint32_t)((jg / STAGES) & 1))) s_abort[jg & 1] = 1;
-            if (has_psi) {
-                const elem* st = stage + (size_t)s * 18 * SEGW;
-                real* rp = ring_psi + (int)(jg & 3) * RW;
-                real* rq = ring_psi2 + (int)(jg & 3) * RW;
+            if (has_psi && j < njobs_h) {
+                const elem* st = stage + (size_t)s * 18 * SEGW + soff;
+                real* rp = ring_psi + (int)(jg & 3) * RW + roff;
+                real* rq = ring_psi2 + (int)(jg & 3) * RW + roff;
                 {
                     const int r = r_psi;
                     const int c = r - 1 + HALO;
@@ -216,10 +267,10 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 break;
             }
             if (halo) continue;
-            if (j >= 2 && t < W) {
+            if (j >= 2 && j < njobs_h && tl < W) {
                 const int sp = (int)((jg - 1) % STAGES);
-                const elem* st = stage + (size_t)sp * 18 * SEGW;
-                const int c = t + HALO;
+                const elem* st = stage + (size_t)sp * 18 * SEGW + soff;
+                const int c = tl + HALO;
                 real f[9], g[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
@@ -229,15 +280,15 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 real rho = f[0];
 #pragma unroll
                 for (int i = 1; i < 9; ++i) rho += f[i];
-                const int r = t + 1;
+                const int r = roff + tl + 1;
                 real Fx, Fy, ux, uy, T;
                 force_from_rows<real, BMODE>(
                     kp, ring_psi + (int)((jg - 2) & 3) * RW + r, ring_psi + (int)((jg - 1) & 3) * RW + r,
                     ring_psi + (int)(jg & 3) * RW + r, ring_psi2 + (int)((jg - 2) & 3) * RW + r,
                     ring_psi2 + (int)((jg - 1) & 3) * RW + r, ring_psi2 + (int)(jg & 3) * RW + r, Fx, Fy);
                 collide<real, EQ24>(kp, f, g, rho, Fx, Fy, ux, uy, T);
-                const int y = item.y0 + j - 2;
-                const int xg = x0 + t;
+                const int y = yh + j - 2;
+                const int xg = x0 + tl;
                 const uint32_t off = (uint32_t)y * pitch + (uint32_t)xg;
                 // FP32 / FP64 storage, the values as computed; each plane's ghost
                 // copy right after its value (the one-branch-per-site form of

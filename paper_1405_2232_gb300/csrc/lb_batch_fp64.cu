@@ -13,7 +13,7 @@ cudaError_t launch_batch_step_fp64(const void* src, void* dst, const BatchDomain
                                    int bmode, int grid, cudaStream_t stream) {
     using E = double;
     constexpr int BX = 128, ST = batch_stages<LB_PREC_FP64, BX>();
-    constexpr size_t smem = strip_smem_bytes<LB_PREC_FP64, BX, ST>();
+    constexpr size_t smem = batch_smem_bytes<LB_PREC_FP64, BX, ST>();
     void (*k)(const E*, E*, const BatchDomain*, const BatchItem*, const int*, int*);
     if (eq24)
         k = bmode == BETA_ZERO  ? k_batch_step<LB_PREC_FP64, BX, ST, true, BETA_ZERO>
