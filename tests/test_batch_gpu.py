@@ -211,3 +211,42 @@ def test_batch_restart_domain(lb):
         assert steps2[0] == steps[0] + 20 and st2[0] in (lb.LB_ERR_NOT_CONVERGED, lb.LB_ERR_PSI_DOMAIN)
     with pytest.raises(lb.LbError):
         lb.lb_batch_restart(None, 0, rho, T)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_many_items_per_cta_match_lone_runs(lb, precision):
+    """More work items than persistent CTAs (each CTA takes several items from
+    the global counter through its shared-memory queue, then the end mark),
+    full and half items (strips at most half the kernel's width, rows split
+    over the two halves of the CTA, odd and even row counts): every domain
+    equals a lone single-lattice run of the same steps, FP64 bit for bit
+    (both compiled without contraction, both bit-identical to the oracle);
+    FP32 to a few FP32 roundings (the two kernels' units may contract
+    products into fused multiply-adds differently)."""
+    rng = np.random.default_rng(11)
+    specs = []
+    for k in range(48):
+        nx = int(rng.choice([37, 64, 100, 131, 260, 300, 333]))
+        ny = int(rng.integers(9, 70))
+        kind = "droplet" if k % 2 else "slab"
+        specs.append((nx, ny, float(rng.uniform(0.7, 1.2)), float(rng.uniform(-1.1, -0.9)), "cs",
+                      float(rng.uniform(0.8, 0.92)), kind))
+    setups = [domain_setup(s, O.THERMAL_EQ24) for s in specs]
+    params = [lb_params_from(lb, P, precision) for _, _, P, _ in setups]
+    with lb.Batch(params, [s[0] for s in setups], [s[1] for s in setups]) as B:
+        lb.lb_batch_set_chunk_rows(B.b, 16)
+        B.step(12)
+        for d, (rho0, T0, P, _) in enumerate(setups):
+            rho, T = B.fields(d)
+            with lb.Lattice(rho0, T0, nx=P.nx, ny=P.ny, precision=precision, tau_f=P.tau_f, G=P.G,
+                            thermal=P.thermal, beta=P.beta, psi_uses_local_T=P.psi_uses_local_T,
+                            T_psi=P.T_psi, eos=P.eos, tile_x=32, tile_y=8) as L:
+                L.step(12)
+                m = L.moments()
+            if precision == "fp64":
+                assert np.array_equal(rho, m[0]) and np.array_equal(T, m[3]), (d, specs[d][:2])
+            else:
+                e_rho = np.abs(rho - m[0]).max() / np.abs(m[0]).max()
+                e_T = np.abs(T - m[3]).max() / np.abs(m[3]).max()
+                assert e_rho < 1e-6 and e_T < 1e-6, (d, specs[d][:2], e_rho, e_T)
