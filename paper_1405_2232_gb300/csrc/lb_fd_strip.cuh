@@ -91,6 +91,44 @@ __device__ __forceinline__ real fd_K_rows(const real* Xs, const real* Xc, const 
         return -(ux * gTx + uy * gTy) + chi * (lap + __fdividef(grx * gTx + gry * gTy, Rc[0]));
 }
 
+// FP32: the same K with the terms that depend only on the site's density and
+// velocity folded into a = chi grad(rho) / rho - u, which both RK2 stages
+// share (formed once per site in the fused kernel's velocity phase):
+// K = a . grad(X) + chi lap(X), the stencil of X alone.
+__device__ __forceinline__ float fd_K_rows_a(const float* Xs, const float* Xc, const float* Xn, float ax,
+                                             float ay, float chi) {
+    float gTx = 0.0f, gTy = 0.0f, lap = 0.0f;
+    const float X0 = Xc[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const float w = (float)wd(i);
+        const float* xr = ey(i) == 1 ? Xn : (ey(i) == -1 ? Xs : Xc);
+        const float Xv = xr[ex(i)];
+        gTx += w * (float)ex(i) * Xv;
+        gTy += w * (float)ey(i) * Xv;
+        lap += w * (Xv - X0);
+    }
+    return fmaf(ax, 3.0f * gTx, fmaf(ay, 3.0f * gTy, chi * (6.0f * lap)));
+}
+
+// a = chi grad(rho) / rho - u at a site (FP32; see fd_K_rows_a), from the
+// density rows (south, centre, north, each at the site's column)
+__device__ __forceinline__ void fd_a_rows(const float* Rs, const float* Rc, const float* Rn, float ux, float uy,
+                                          float chi, float& ax, float& ay) {
+    float grx = 0.0f, gry = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const float w = (float)wd(i);
+        const float* rr = ey(i) == 1 ? Rn : (ey(i) == -1 ? Rs : Rc);
+        const float rn = rr[ex(i)];
+        grx += w * (float)ex(i) * rn;
+        gry += w * (float)ey(i) * rn;
+    }
+    const float cr = __fdividef(chi, Rc[0]);
+    ax = fmaf(cr, 3.0f * grx, -ux);
+    ay = fmaf(cr, 3.0f * gry, -uy);
+}
+
 // One whole FD step (Eqs. 1, 26, 27) on a strip context, one pass over HBM:
 // f and T^n in, f and T^{n+1} out (both in the ghost-column layout, row
 // pitch kp.pitch, kp.ghost = FD_GHOST).  Job k is pre-collision row
@@ -259,8 +297,18 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 // the f half of the collision; g (zero here) is not used
                 // (FP32: the fused multiply-add form, faster in this kernel)
                 collide<real, false, true>(kp, f, g, rho, Fx, Fy, ux, uy, Tg);
-                r_ux[(k & 3) * RB + colB + 1] = ux;
-                r_uy[(k & 3) * RB + colB + 1] = uy;
+                if constexpr (sizeof(real) == 4) {
+                    // FP32: the rings keep a = chi grad(rho) / rho - u, which
+                    // both stages' K share (fd_K_rows_a)
+                    real ax, ay;
+                    fd_a_rows(r_rho + ((k - 1) & 7) * RA + ia, r_rho + (k & 7) * RA + ia,
+                              r_rho + ((k + 1) & 7) * RA + ia, ux, uy, chi, ax, ay);
+                    r_ux[(k & 3) * RB + colB + 1] = ax;
+                    r_uy[(k & 3) * RB + colB + 1] = ay;
+                } else {
+                    r_ux[(k & 3) * RB + colB + 1] = ux;
+                    r_uy[(k & 3) * RB + colB + 1] = uy;
+                }
                 if (own_col && k >= 2 && k <= njobs - 3) {
                     int y = y_start - 2 + k;
                     y = y >= ny ? y - ny : y;
@@ -289,9 +337,13 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                 const real* Ts_ = r_T + ((k - 1) & 7) * RA + ia;
                 const real* Tc_ = r_T + (k & 7) * RA + ia;
                 const real* Tn_ = r_T + ((k + 1) & 7) * RA + ia;
-                const real K = fd_K_rows<real>(Ts_, Tc_, Tn_, r_rho + ((k - 1) & 7) * RA + ia,
-                                               r_rho + (k & 7) * RA + ia, r_rho + ((k + 1) & 7) * RA + ia,
-                                               r_ux[(k & 3) * RB + ib], r_uy[(k & 3) * RB + ib], chi);
+                real K;
+                if constexpr (sizeof(real) == 4)
+                    K = fd_K_rows_a(Ts_, Tc_, Tn_, r_ux[(k & 3) * RB + ib], r_uy[(k & 3) * RB + ib], chi);
+                else
+                    K = fd_K_rows<real>(Ts_, Tc_, Tn_, r_rho + ((k - 1) & 7) * RA + ia, r_rho + (k & 7) * RA + ia,
+                                        r_rho + ((k + 1) & 7) * RA + ia, r_ux[(k & 3) * RB + ib],
+                                        r_uy[(k & 3) * RB + ib], chi);
                 r_h1[(k & 3) * RB + ib] = K;
                 r_Ts[(k & 3) * RB + ib] = Tc_[0] + a * K;
             }
@@ -301,10 +353,16 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
             const int k = j - 4;
             if (k >= 2 && k <= njobs - 3 && own_col) {
                 const int ia = t + 2, ib = t + 1;
-                const real K = fd_K_rows<real>(r_Ts + ((k - 1) & 3) * RB + ib, r_Ts + (k & 3) * RB + ib,
-                                               r_Ts + ((k + 1) & 3) * RB + ib, r_rho + ((k - 1) & 7) * RA + ia,
-                                               r_rho + (k & 7) * RA + ia, r_rho + ((k + 1) & 7) * RA + ia,
-                                               r_ux[(k & 3) * RB + ib], r_uy[(k & 3) * RB + ib], chi);
+                real K;
+                if constexpr (sizeof(real) == 4)
+                    K = fd_K_rows_a(r_Ts + ((k - 1) & 3) * RB + ib, r_Ts + (k & 3) * RB + ib,
+                                    r_Ts + ((k + 1) & 3) * RB + ib, r_ux[(k & 3) * RB + ib], r_uy[(k & 3) * RB + ib],
+                                    chi);
+                else
+                    K = fd_K_rows<real>(r_Ts + ((k - 1) & 3) * RB + ib, r_Ts + (k & 3) * RB + ib,
+                                        r_Ts + ((k + 1) & 3) * RB + ib, r_rho + ((k - 1) & 7) * RA + ia,
+                                        r_rho + (k & 7) * RA + ia, r_rho + ((k + 1) & 7) * RA + ia,
+                                        r_ux[(k & 3) * RB + ib], r_uy[(k & 3) * RB + ib], chi);
                 const real v = r_T[(k & 7) * RA + ia] + (real)0.5 * (r_h1[(k & 3) * RB + ib] + K);
                 int y = y_start - 2 + k;
                 y = y >= ny ? y - ny : y;
