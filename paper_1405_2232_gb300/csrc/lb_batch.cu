@@ -171,13 +171,14 @@ lb_status rebuild_lists(lb_batch* b) {
         if (b->frozen[d] >= 0) continue;
         const int nx = b->params[d].nx, ny = b->params[d].ny;
         const int strips = (nx + b->bx - 1) / b->bx;
+        const int chunks = (ny + b->chunk_rows - 1) / b->chunk_rows;
         for (int s = 0; s < strips; ++s) {
-            // a strip at most half the kernel's width runs as half items: twice
-            // the rows of a chunk, split between the two halves of the CTA
+            // a strip at most half the kernel's width runs as half items: the
+            // chunk's rows split between the two halves of the CTA, so the item
+            // takes half the jobs (twice the chunk's rows per item measured
+            // slower: fewer items than CTAs on batches of small domains)
             const int w = std::min(b->bx, nx - s * b->bx);
             const int half = 2 * w <= b->bx ? 1 : 0;
-            const int rows = half ? 2 * b->chunk_rows : b->chunk_rows;
-            const int chunks = (ny + rows - 1) / rows;
             for (int c = 0; c < chunks; ++c) {
                 BatchItem it;
                 it.domain = d;
