@@ -88,7 +88,7 @@ struct lb_batch {
     // work lists
     BatchItem* d_items = nullptr;
     int* d_counts = nullptr;      // [0] items, [1] tiles
-    int* d_next = nullptr;        // the next work item to take (reset before every step)
+    int* d_next = nullptr;        // takes from the work counter in the current step (the step resets it)
     int max_items = 0;
     BatchTile* d_tiles = nullptr;
     int* d_tile_begin = nullptr;  // [n + 1]
@@ -131,15 +131,9 @@ cudaError_t launch_batch_step(lb_batch* b, const void* src, void* dst) {
         };
         auto k = pick();
         if (!src) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
-        if (e != cudaSuccess) return e;
         k<<<grid, strip_threads<BX>(), smem, b->stream>>>(static_cast<const E*>(src), static_cast<E*>(dst),
                                                            b->d_doms, b->d_items, b->d_counts, b->d_next);
         return cudaGetLastError();
-    }
-    if (src) {
-        cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
-        if (e != cudaSuccess) return e;
     }
     return launch_batch_step_fp64(src, dst, b->d_doms, b->d_items, b->d_counts, b->d_next, b->eq24, b->bmode,
                                   grid, b->stream);
@@ -218,6 +212,9 @@ lb_status rebuild_lists(lb_batch* b) {
                         cudaMemcpyHostToDevice, b->stream), "tile index upload");
     BCU(cudaMemcpyAsync(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, b->stream),
         "list length upload");
+    // (each step leaves the work counter at zero; reset it here as well, so a
+    // step that stopped on an error cannot leave it behind)
+    BCU(cudaMemsetAsync(b->d_next, 0, sizeof(int) * 2, b->stream), "work counter reset");
     BCU(cudaStreamSynchronize(b->stream), "synchronize");
     return LB_OK;
 }
@@ -376,7 +373,8 @@ lb_status lb_batch_init(const lb_params* params, int32_t n, const double* const*
     if (e == cudaSuccess) e = cudaMalloc(&b->d_doms, sizeof(BatchDomain) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (max_items > 0 ? max_items : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(int) * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(int) * 2, b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * (max_tiles > 0 ? max_tiles : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_part, sizeof(double) * 6 * (max_tiles > 0 ? max_tiles : 1));

@@ -3,18 +3,22 @@
 //
 // The fused step is the strip-marching kernel of lb_step_strip.cuh made
 // persistent: a fixed grid of CTAs walks a device-side list of work items
-// (domain, strip, row chunk) sorted longest first; each CTA's producer warp
-// takes the next item from a global counter when it starts one, so the CTAs
-// finish together (a static deal by estimated cost left the last CTA 14%
-// behind the mean).  The producer passes each item's index to the consumer
+// (domain, strip, row chunk) sorted longest first; CTA b starts with item b
+// and its producer warp takes every further item from a global counter, so
+// the CTAs finish together (a static deal by estimated cost left the last CTA
+// 14% behind the mean).  The producer passes each item's index to the consumer
 // warps through a small shared-memory queue (written before it arms the
 // item's first stage, read after that stage's barrier), and after the last
 // item an end mark: a stage completed without data whose queue entry is -1.
 // The producer and the consumers keep one job counter across items, so the
 // producer streams the next item's rows while the consumers still work on
 // the current one.  The list and its length are read from device memory at
-// launch and the counter is reset before every launch, so a captured CUDA
-// graph stays valid while converged domains are taken off the list.
+// launch.  A launch over n items and G CTAs takes from the counter exactly
+// max(0, n - G) + min(G, n) times (every further item, and one failed take
+// per CTA that had an item), so the take that returns the last of those
+// values resets the counter for the next launch: a captured CUDA graph
+// replays the step with no reset node, CTAs without an item touch no atomic,
+// and the graph stays valid while converged domains are taken off the list.
 //
 // Half items: a strip at most BX/2 columns wide (a narrow domain, or the
 // remainder strip of a wider one) would leave most column threads idle, so
@@ -86,6 +90,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                  typename Store<PREC>::elem* __restrict__ dst_base,
                  const BatchDomain* __restrict__ doms, const BatchItem* __restrict__ items,
                  const int* __restrict__ n_items_ptr, int* __restrict__ next_item) {
+    // next_item[0]: takes from the counter so far (item G + value)
     using S = Store<PREC>;
     using C = StripCfg<PREC>;
     using elem = typename C::elem;
@@ -128,10 +133,19 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         const int n_items = *n_items_ptr;
         long long jg = 0;  // job counter across this CTA's items
         int q = 0;         // items taken
+        bool timed_out = false;
+        const int G = (int)gridDim.x;
+        const int takes = max(0, n_items - G) + min(G, n_items);
         for (;; ++q) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(next_item, 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
+            int it = (int)blockIdx.x;  // the first item: no counter
+            if (q > 0) {
+                int x = 0;
+                if (lane == 0) {
+                    x = atomicAdd(next_item, 1);
+                    if (x == takes - 1) *next_item = 0;  // the launch's last take
+                }
+                it = G + __shfl_sync(0xffffffffu, x, 0);
+            }
             if (it >= n_items) break;
             const BatchItem item = items[it];
             const BatchDomain& D = doms[item.domain];
@@ -152,7 +166,8 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     // the warp takes one decision (its lanes poll the barrier independently)
                     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1)))) {
                         if (lane == 0) atomicOr(D.kp.err, 1 << LB_ERR_TIMEOUT);
-                        return;  // consumers then time out on "full" and leave
+                        timed_out = true;  // consumers then time out on "full" and leave
+                        break;
                     }
                 }
                 const bool two = j < njobs1;  // the right half of a half item has this job
@@ -177,6 +192,7 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
                     }
                 }
             }
+            if (timed_out) break;
         }
         // every copy this CTA issued has landed (bounded) before the end mark
         // completes the next phase of a stage's barrier, and before the CTA exits
@@ -186,12 +202,12 @@ __global__ void __launch_bounds__(strip_threads<BX>(), 2)
         __syncwarp();
         // the end mark: the next stage completes without data, its queue entry -1
         const int s = (int)(jg % STAGES);
-        if (jg >= STAGES &&
+        if (!timed_out && jg >= STAGES &&
             !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (uint32_t)(((jg / STAGES) - 1) & 1)))) {
             if (lane == 0) atomicOr(doms[0].kp.err, 1 << LB_ERR_TIMEOUT);
-            return;  // consumers then time out on "full" and leave
+            timed_out = true;  // consumers then time out on "full" and leave
         }
-        if (lane == 0) {
+        if (lane == 0 && !timed_out) {
             s_items[q % BATCH_QN] = -1;
             mbar_arrive(&full[s]);
         }
