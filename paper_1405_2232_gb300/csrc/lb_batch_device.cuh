@@ -27,10 +27,11 @@
 // [ym, y1).  The stage and psi-ring rows hold one segment per half, the
 // producer copies both halves' plane rows for a job, the halo warp's lanes
 // 0, 1 and 2, 3 compute the halo psi columns of the two halves; when the
-// right half has one row fewer it sits out the left half's last job.  As in the single-lattice kernel,
-// every domain is stored in the ghost-column layout (one bulk copy per plane
-// row, ghost copies written with the row) and a halo warp computes the two
-// halo psi columns.
+// right half has one row fewer it sits out the left half's last job.
+//
+// As in the single-lattice kernel, every domain is stored in the ghost-column
+// layout (one bulk copy per plane row, ghost copies written with the row) and
+// a halo warp computes the halo psi columns.
 #pragma once
 
 #include "lb_step_strip.cuh"
